@@ -1,0 +1,371 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these re-types the oracle's formula: each checks a closed form, an
+invariant, a library routine, a second independent route, or brute force
+from the definitions on tiny inputs, so that a dropped term, a wrong sign or
+index, or a transposed operand in oracle/fg21_oracle.c fails at least one of
+them (tests/test_oracle_mutations.py plants such mistakes and checks that).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.stats
+
+import oracle as O
+from paper_2603_13196_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json")
+
+
+def small_case(npix=3072, F=21, T=3, window=6.0, seed=11, **kw):
+    sky = I.make_sky(npix, seed, **{k: v for k, v in kw.items() if k in ("beta_const", "t230_const")})
+    obs = I.make_obs(F, T, window, lst0_h=kw.get("lst0_h", 17.0), achromatic_p=kw.get("achromatic_p"),
+                     lo=kw.get("lo", 50.0), hi=kw.get("hi", 200.0))
+    return sky, obs
+
+
+# ----------------------------------------------------------------- constants
+
+def test_paper_constants_fixture_matches_inputs():
+    g = json.load(open(GOLDEN))
+    assert I.FIDUCIAL_T21 == (g["t21_fiducial"]["A21_K"], g["t21_fiducial"]["nu21_MHz"],
+                              g["t21_fiducial"]["sigma21_MHz"])
+    assert I.NOISE_K == g["noise_K"]["value"]
+    assert I.NU0_MHZ == g["nu0_MHz"]["value"]
+
+
+def test_t21_special_values():
+    """eq. t21model at the fiducial trough: peak A21 at nu21, e^-1/2 one width
+    away, e^-2 two widths away, symmetric about nu21."""
+    g = json.load(open(GOLDEN))["t21_fiducial"]
+    a, c, s = g["A21_K"], g["nu21_MHz"], g["sigma21_MHz"]
+    v = O.t21([c, c + s, c - s, c + 2 * s, c - 2 * s], a, c, s)
+    np.testing.assert_allclose(v, [a, a * math.exp(-0.5), a * math.exp(-0.5), a * math.exp(-2),
+                                   a * math.exp(-2)], rtol=1e-15)
+    # a negative width is the same trough; zero amplitude is flat zero
+    np.testing.assert_allclose(O.t21([70.0], a, c, -s), O.t21([70.0], a, c, s), rtol=0)
+    assert O.t21([70.0], 0.0, c, s)[0] == 0.0
+
+
+# ---------------------------------------------------------------------- beam
+
+@pytest.mark.parametrize("p", [0.0, 1.2, 1.8])
+def test_beam_is_a_directivity(p):
+    """(1/4pi) integral D dOmega = 1 for D = 2(p+1)cos^p above the horizon
+    (hemisphere integral of cos^p is 2pi/(p+1)); on the Fibonacci sphere the
+    discrete B[f,t] converges to 1 as Npix grows."""
+    errs = []
+    for npix in (768, 3072, 12288):
+        sky, obs = small_case(npix=npix, F=3, T=4, achromatic_p=p)
+        labels = np.zeros(npix, dtype=np.int32)
+        _, B = O.precompute(sky, obs, labels, 1)
+        errs.append(np.max(np.abs(B - 1.0)))
+    # the flat beam (p = 0) has a step at the horizon, so pixel counting converges slowly
+    assert errs[1] < (1e-2 if p == 0.0 else 1e-4)
+    assert errs[2] < errs[0]
+
+
+def test_flat_beam_counts_pixels_above_horizon():
+    """p = 0: D = 2 on the visible hemisphere, so A = (T0 - T_CMB) * 2 n_up / Npix and
+    B = 2 n_up / Npix for a constant sky, n_up = pixels with z.v > 0."""
+    T0 = 500.0
+    sky, obs = small_case(npix=3072, F=4, T=3, achromatic_p=0.0, t230_const=T0)
+    labels = np.zeros(sky.npix, dtype=np.int32)
+    A, B = O.precompute(sky, obs, labels, 1)
+    for t in range(obs.T):
+        n_up = int(np.sum(sky.dirs @ obs.zenith[t] > 0))
+        np.testing.assert_allclose(B[:, t], 2.0 * n_up / sky.npix, rtol=1e-13)
+        np.testing.assert_allclose(A[0, :, t], (T0 - I.T_CMB) * 2.0 * n_up / sky.npix, rtol=1e-13)
+
+
+# ----------------------------------------------------- forward model routes
+
+@pytest.mark.parametrize("scheme,N", [("recursive", 5), ("hierarchical", 6), ("linear", 4)])
+def test_fast_model_equals_pixel_model(scheme, N):
+    """eq. fast_forward_model with precomputed A equals eq. forward_model integrated
+    per pixel (linearity of the beam integral), for arbitrary per-region beta."""
+    sky, obs = small_case(npix=1536, F=9, T=3)
+    m = O.build_model(sky, obs, N, scheme)
+    th = I.prior_draws(4, N, seed=5)
+    M1 = O.fast_model(m.A, m.B, obs, th)
+    M2 = O.pixel_model(sky, obs, m.labels, N, th)
+    np.testing.assert_allclose(M1, M2, rtol=1e-11)
+
+
+def test_single_region_is_a_power_law():
+    """N = 1, achromatic beam, T = 1: M - T_CMB B - T21 = S (nu/nu0)^-beta, so
+    ln of it is linear in ln nu with slope -beta and equals S at nu = nu0,
+    where S is the beam-weighted template; with a flat beam (p = 0) and a
+    constant template T0, S = (T0 - T_CMB) 2 n_up / Npix."""
+    T0 = 700.0
+    sky, obs = small_case(npix=3072, F=16, T=1, achromatic_p=0.0, t230_const=T0, lo=50.0, hi=230.0)
+    m = O.build_model(sky, obs, 1, "recursive")
+    beta = 2.71
+    th = np.array([[beta, 0.0, 100.0, 10.0, 0.01]])
+    M = O.fast_model(m.A, m.B, obs, th)[0, :, 0]
+    y = np.log(M - I.T_CMB * m.B[:, 0])
+    slope, icpt = np.polyfit(np.log(obs.nu), y, 1)
+    assert abs(slope + beta) < 1e-11
+    n_up = int(np.sum(sky.dirs @ obs.zenith[0] > 0))
+    S = (T0 - I.T_CMB) * 2.0 * n_up / sky.npix
+    assert obs.nu[-1] == 230.0
+    np.testing.assert_allclose(M[-1] - I.T_CMB * m.B[-1, 0], S, rtol=1e-12)
+
+
+@pytest.mark.parametrize("scheme,N", [("recursive", 7), ("hierarchical", 5), ("linear", 4),
+                                      ("percentile", 3)])
+def test_equal_beta_collapse(scheme, N):
+    """All beta_i equal: sum_i A_i (nu/nu0)^-beta collapses to one power law of the
+    summed beam-weighted sky, independent of the partition (the A_i partition
+    the template)."""
+    sky, obs = small_case(npix=2048, F=7, T=2)
+    ref = O.build_model(sky, obs, 1, "recursive")
+    m = O.build_model(sky, obs, N, scheme)
+    np.testing.assert_allclose(m.A.sum(axis=0), ref.A[0], rtol=1e-12)
+    th1 = np.array([[2.6, 0.1, 80.0, 12.0, 0.02]])
+    thN = np.concatenate([[2.6] * N, [0.1, 80.0, 12.0, 0.02]])[None, :]
+    np.testing.assert_allclose(O.fast_model(m.A, m.B, obs, thN), O.fast_model(ref.A, ref.B, obs, th1),
+                               rtol=1e-12)
+
+
+def test_constant_beta_sky_reproduces_simulated_data():
+    """A sky with one spectral index everywhere is exactly an N-region model at
+    beta_i = beta0: eq. simantenna (noise-free) equals eq. fast_forward_model + T21."""
+    beta0 = 2.63
+    sky, obs = small_case(npix=2048, F=11, T=3, beta_const=beta0)
+    m = O.build_model(sky, obs, 3, "percentile")
+    t21p = np.array(I.FIDUCIAL_T21)
+    data = O.simulate_data(sky, obs, t21p)
+    th = np.concatenate([[beta0] * 3, t21p, [0.025]])[None, :]
+    np.testing.assert_allclose(O.fast_model(m.A, m.B, obs, th)[0], data, rtol=1e-12)
+
+
+def test_simulated_data_closed_form():
+    """Flat beam, constant template T0, constant beta: the antenna temperature is
+    (2 n_up/Npix) [(T0 - T_CMB)(nu/nu0)^-beta + T_CMB] + T21 + sigma * noise."""
+    T0, beta0 = 400.0, 2.5
+    sky, obs = small_case(npix=1024, F=6, T=2, achromatic_p=0.0, t230_const=T0, beta_const=beta0)
+    t21p = np.array([0.2, 120.0, 20.0])
+    noise = I.noise_draws(obs.F, obs.T, 3)
+    data = O.simulate_data(sky, obs, t21p, 0.025, noise)
+    for t in range(obs.T):
+        frac = 2.0 * np.sum(sky.dirs @ obs.zenith[t] > 0) / sky.npix
+        sky_t = frac * ((T0 - I.T_CMB) * (obs.nu / I.NU0_MHZ) ** (-beta0) + I.T_CMB)
+        trough = 0.2 * np.exp(-0.5 * ((obs.nu - 120.0) / 20.0) ** 2)
+        np.testing.assert_allclose(data[:, t], sky_t + trough + 0.025 * noise[:, t], rtol=1e-12)
+
+
+# ----------------------------------------------------------------- likelihood
+
+def test_noiseless_identity():
+    """Data equal to the model at theta*: lnL(theta*) = -1/2 F T ln(2 pi sigma^2)."""
+    sky, obs = small_case(npix=1024, F=13, T=4)
+    m = O.build_model(sky, obs, 4, "recursive")
+    th = np.concatenate([O.region_truth(sky, m.labels, 4), [0.155, 85.0, 15.0, 0.025]])[None, :]
+    data = O.fast_model(m.A, m.B, obs, th)[0]
+    L = O.loglike(m.A, m.B, data, obs, th)[0]
+    expect = -0.5 * obs.F * obs.T * math.log(2 * math.pi * 0.025 ** 2)
+    assert abs(L - expect) <= 1e-12 * abs(expect)
+
+
+def test_loglike_is_a_sum_of_gaussian_logpdfs():
+    """eq. likelihood equals the sum of scipy's normal log-densities of the data
+    about the model with scale sigma_n."""
+    sky, obs = small_case(npix=512, F=5, T=2)
+    m = O.build_model(sky, obs, 2, "recursive")
+    data = O.simulate_data(sky, obs, np.array(I.FIDUCIAL_T21), 0.025, I.noise_draws(5, 2, 1))
+    th = I.prior_draws(5, 2, seed=3)
+    th[:, :2] = O.region_truth(sky, m.labels, 2) + 1e-4
+    L = O.loglike(m.A, m.B, data, obs, th)
+    M = O.fast_model(m.A, m.B, obs, th)
+    for p in range(5):
+        ref = scipy.stats.norm.logpdf(data, loc=M[p], scale=th[p, -1]).sum()
+        assert abs(L[p] - ref) <= 1e-10 * abs(ref)
+    c2 = O.chi2(m.A, m.B, data, obs, th)
+    np.testing.assert_allclose(c2, ((data[None] - M) ** 2).sum(axis=(1, 2)), rtol=1e-12)
+
+
+# ------------------------------------------------------------------ weighting
+
+def test_weights_special_cases():
+    """Each importance map reduces to the simpler one when its extra factor is
+    constant: uniform = 1/Npix; horizon with T = 1 = H / n_up; sky weighting of a
+    constant sky = horizon weighting; beam weighting with a flat beam (p = 0) =
+    sky weighting.  All sum to one."""
+    sky, obs = small_case(npix=1024, F=5, T=1)
+    w_u = O.weights(sky, obs, "uniform")
+    np.testing.assert_allclose(w_u, 1.0 / sky.npix, rtol=1e-14)
+    up = (sky.dirs @ obs.zenith[0] > 0)
+    w_h = O.weights(sky, obs, "horizon")
+    np.testing.assert_allclose(w_h, up / up.sum(), rtol=1e-14, atol=0)
+    csky, cobs = small_case(npix=1024, F=5, T=3, t230_const=300.0, beta_const=2.6)
+    np.testing.assert_allclose(O.weights(csky, cobs, "sky"), O.weights(csky, cobs, "horizon"),
+                               rtol=1e-12)
+    fsky, fobs = small_case(npix=1024, F=5, T=3, achromatic_p=0.0)
+    np.testing.assert_allclose(O.weights(fsky, fobs, "beam"), O.weights(fsky, fobs, "sky"),
+                               rtol=1e-12)
+    for wt in ("beam", "sky", "horizon", "uniform"):
+        assert abs(O.weights(sky, obs, wt).sum() - 1.0) < 1e-12
+
+
+def test_beam_weighting_tracks_the_beam():
+    """With a constant sky the beam weight of a pixel at time t is proportional to
+    D(pix); with T = 1 this is cos^p of the zenith angle, normalised."""
+    sky, obs = small_case(npix=1024, F=1, T=1, t230_const=300.0, beta_const=2.6, achromatic_p=1.5,
+                          lo=100.0, hi=100.0)
+    w = O.weights(sky, obs, "beam")
+    c = np.maximum(sky.dirs @ obs.zenith[0], 0.0) ** 1.5
+    np.testing.assert_allclose(w, c / c.sum(), rtol=1e-12, atol=1e-300)
+
+
+# ------------------------------------------------------------------ partition
+
+def _brute_cdf(beta, w, x):
+    return sum(wi for bi, wi in zip(beta, w) if bi <= x)
+
+
+def _brute_cinv(beta, w, c):
+    cands = [b for b in sorted(set(beta)) if _brute_cdf(beta, w, b) >= c]
+    return cands[0] if cands else max(beta)
+
+
+def _brute_partition(beta, w, N, scheme):
+    """Algorithms 1 and 2 and the Sec. 4.1 splits, straight from the definitions
+    (Algorithm 1 refines only base regions, the nested reading):
+    C(beta') = sum of w over pixels with beta <= beta' (eq. weighted_cdf), region
+    mass = C(b) - C(a) (lowest region: C(b)), intervals kept as python lists."""
+    bmin, bmax = min(beta), max(beta)
+    if scheme == "recursive":
+        R = [(bmin, bmax, True)]
+        while len(R) < N:
+            def mass(r):
+                a, b, low = r
+                return _brute_cdf(beta, w, b) - (0.0 if low else _brute_cdf(beta, w, a))
+            best = max(range(len(R)), key=lambda k: (mass(R[k]), -R[k][0]))
+            a, b, low = R.pop(best)
+            mid = 0.5 * (a + b)
+            R += [(a, mid, low), (mid, b, False)]
+        edges = [bmin] + sorted(r[1] for r in R)
+    elif scheme == "hierarchical":
+        nb = 2 ** int(math.floor(math.log2(N)))
+        cs = [j / nb for j in range(nb + 1)]
+        bs = [bmin] + [_brute_cinv(beta, w, c) for c in cs[1:-1]] + [bmax]
+        R = [(bs[j], bs[j + 1], cs[j], cs[j + 1], True) for j in range(nb)]
+        while len(R) < N:
+            cand = [k for k in range(len(R)) if R[k][4]]
+            best = max(cand, key=lambda k: (R[k][1] - R[k][0], -R[k][0]))
+            a, b, ca, cb, _ = R.pop(best)
+            cm = 0.5 * (ca + cb)
+            bm = _brute_cinv(beta, w, cm)
+            R += [(a, bm, ca, cm, False), (bm, b, cm, cb, False)]
+        edges = [bmin] + sorted(r[1] for r in R)
+    elif scheme == "linear":
+        edges = [bmin] + [bmin + (bmax - bmin) * j / N for j in range(1, N)] + [bmax]
+    else:
+        sb = sorted(beta)
+        n = len(beta)
+        edges = [bmin] + [sb[math.ceil(j * n / N) - 1] for j in range(1, N)] + [bmax]
+    labels = [sum(1 for e in edges[1:-1] if b > e) for b in beta]
+    return edges, labels
+
+
+@pytest.mark.parametrize("scheme", ["recursive", "hierarchical", "linear", "percentile"])
+@pytest.mark.parametrize("seed", range(6))
+def test_partition_matches_brute_force(scheme, seed):
+    """Tiny maps (<= 16 pixels, tied betas, zero weights, dyadic weights so every
+    sum is exact): the sorted-prefix oracle equals the definitions label for label."""
+    g = np.random.default_rng(100 + seed)
+    npix = int(g.integers(5, 17))
+    beta = np.round(g.uniform(2.4, 3.2, npix), 2)            # ties likely
+    w = g.integers(0, 9, npix).astype(np.float64)
+    w[0] = max(w[0], 1.0)
+    w = w / 2.0 ** math.ceil(math.log2(w.sum()))                # dyadic, sum <= 1
+    w[np.argmax(w)] += 1.0 - w.sum()                            # exact sum 1
+    for N in range(1, 9):
+        e_o, l_o, _ = O.partition(beta, w, N, scheme)
+        e_b, l_b = _brute_partition(list(beta), list(w), N, scheme)
+        assert list(l_o) == l_b, (N, e_o, e_b)
+        np.testing.assert_array_equal(e_o, e_b)
+
+
+@pytest.mark.parametrize("scheme", ["recursive", "hierarchical"])
+@pytest.mark.parametrize("weighting", ["beam", "sky", "horizon"])
+def test_partitions_are_nested(scheme, weighting):
+    """Sec. 4.3: every region at level N is a union of regions at level N+1
+    (edge sets grow by inclusion, labels at N are a function of labels at N+1)."""
+    sky, obs = small_case(npix=3072, F=9, T=3)
+    w = O.weights(sky, obs, weighting)
+    prev = None
+    for N in range(1, 18):
+        edges, labels, _ = O.partition(sky.beta, w, N, scheme)
+        assert np.all(np.diff(edges) >= 0)
+        if prev is not None:
+            pe, pl = prev
+            assert set(pe.tolist()) <= set(edges.tolist())
+            for j in range(N):
+                sel = labels == j
+                if sel.any():
+                    assert len(np.unique(pl[sel])) == 1
+        prev = (edges, labels)
+
+
+def test_linear_split_is_not_nested():
+    """Sec. 4.1: equal-width splits redefine all boundaries (3 -> 4 regions)."""
+    sky, obs = small_case(npix=3072, F=3, T=1)
+    w = O.weights(sky, obs, "uniform")
+    e3, _, _ = O.partition(sky.beta, w, 3, "linear")
+    e4, _, _ = O.partition(sky.beta, w, 4, "linear")
+    assert not set(e3.tolist()) <= set(e4.tolist())
+
+
+@pytest.mark.parametrize("N", [2, 4, 8, 16])
+def test_hierarchical_base_regions_have_equal_mass(N):
+    """Sec. 4.3.1: the N_base regions each hold 1/N_base of the importance, to
+    within the largest single pixel weight."""
+    sky, obs = small_case(npix=3072, F=9, T=3)
+    w = O.weights(sky, obs, "beam")
+    _, labels, _ = O.partition(sky.beta, w, N, "hierarchical")
+    mass = np.bincount(labels, weights=w, minlength=N)
+    assert np.all(np.abs(mass - 1.0 / N) <= w.max() + 1e-15)
+
+
+def test_recursive_edges_are_dyadic_midpoints():
+    """Alg. 2 bisects at beta midpoints: every edge is beta_min + k (beta_max - beta_min)/2^j."""
+    sky, obs = small_case(npix=3072, F=9, T=3)
+    w = O.weights(sky, obs, "beam")
+    edges, _, _ = O.partition(sky.beta, w, 12, "recursive")
+    lo, hi = sky.beta.min(), sky.beta.max()
+    x = (edges - lo) / (hi - lo) * 2 ** 12
+    np.testing.assert_allclose(x, np.round(x), atol=1e-6)
+
+
+@pytest.mark.parametrize("scheme", ["recursive", "hierarchical"])
+def test_embedding_identity(scheme):
+    """Nesting makes level N a special case of level N+1: giving both children of
+    the split region the parent's beta reproduces T_model and lnL exactly, so
+    L_max can only grow with N (Sec. 4.1 and Sec. 6.1)."""
+    sky, obs = small_case(npix=2048, F=9, T=3)
+    t21p = np.array(I.FIDUCIAL_T21)
+    data = O.simulate_data(sky, obs, t21p, 0.025, I.noise_draws(obs.F, obs.T, 9))
+    for N in (3, 6, 9):
+        mN = O.build_model(sky, obs, N, scheme)
+        mN1 = O.build_model(sky, obs, N + 1, scheme)
+        thN = I.prior_draws(6, N, seed=N)
+        # region j at N+1 is (e'_j, e'_{j+1}]; its parent is the level-N region holding e'_{j+1}
+        parent_of = np.array([int(np.sum(mN.edges[1:-1] < mN1.edges[j + 1])) for j in range(N + 1)])
+        thN1 = np.concatenate([thN[:, parent_of], thN[:, N:]], axis=1)
+        np.testing.assert_allclose(O.fast_model(mN1.A, mN1.B, obs, thN1), O.fast_model(mN.A, mN.B, obs, thN),
+                                   rtol=1e-12)
+        np.testing.assert_allclose(O.loglike(mN1.A, mN1.B, data, obs, thN1),
+                                   O.loglike(mN.A, mN.B, data, obs, thN), rtol=1e-12)
+
+
+def test_partition_margin_reported():
+    """The oracle reports how close its deciding comparisons came to a tie; on
+    the synthetic workloads it stays far above FP64 rounding."""
+    wl = I.workload(1)
+    m = O.build_model(wl.sky(), wl.obs(), wl.N, wl.scheme)
+    assert 1e-9 < m.margin <= 1.0
