@@ -1,0 +1,340 @@
+#!/usr/bin/env python3
+"""Benchmark of the batched region-model likelihood on one GB300 (or N replicas).
+
+Workload: Npix = 49152, N = 24 regions, F = 301 channels (50-200 MHz, 0.5 MHz),
+T = 100 LST bins over 12 h, P = 16384 prior draws per batch (seeded synthetic
+sky/beam/data, see paper_2603_13196_gb300/inputs.py).  One step = the whole hot
+path over one batch: per-request reference (a1), weights, tensor-core
+contraction, trough, residual and square (a2-a5), per-point reduction and logL
+(a6).
+
+  value        logL evals/s of the split-FP16 tensor-core path, params and
+               logL device-resident (CUDA events on the launch stream, L2
+               flushed by a 256 MiB write between timed steps)
+  e2e          the same through the host-buffer C-ABI call (params H2D and
+               logL D2H inside the timed region)
+  fp32_direct  the plain FP32 SIMT kernel on the same device and protocol
+  roofline     dominant kernel (tcgen05 likelihood kernel): algorithmic flops
+               (2 N F T per point) / its mean launch time, against the measured
+               dense 16-bit tensor peak
+  cpu_baseline the FP64 oracle on the host cores, on a bounded sample
+
+`--impl reference` times the oracle alone (the reference arm of this build).
+Multi-GPU: one process per GPU under torchrun, each rank an independent
+replica with its own batch (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "logL evals/s at N=24,T=100 vs plain FP32 (|ΔlogL|≤1e-2); serve p50/p99 ms"
+WORKLOAD = "c3_npix49152_N24_F301_T100_P16384"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp16x3")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample budget")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ts, line in self.lines:
+            if ts < t0 - 0.06 or ts > t1 + 0.06:
+                continue
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(sky, obs, N, params, seconds):
+    """Time the FP64 oracle's likelihood on a bounded sample of the batch."""
+    import numpy as np
+    import oracle as O
+
+    m = O.build_model(sky, obs, N, "recursive")
+    from paper_2603_13196_gb300 import inputs as I
+    data = O.simulate_data(sky, obs, np.array(I.FIDUCIAL_T21), I.NOISE_K, I.noise_draws(obs.F, obs.T, 7))
+    t = time.perf_counter()
+    O.loglike(m.A, m.B, data, obs, params[:32])
+    per = (time.perf_counter() - t) / 32
+    n = int(max(32, min(params.shape[0], seconds / max(per, 1e-9))))
+    t = time.perf_counter()
+    O.loglike(m.A, m.B, data, obs, params[:n])
+    dt = time.perf_counter() - t
+    return {"value": n / dt, "unit": "logL evals/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{n} of the {params.shape[0]} points of one batch (same workload), FP64, "
+                      f"OpenMP over points, {dt:.1f} s"}, m, data
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle as it stands, on the bench workload."""
+    import numpy as np
+    from paper_2603_13196_gb300 import inputs as I
+    import oracle as O
+    from oracle import build as ob
+
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    ob.build()
+    wl = I.workload(3)
+    sky, obs = wl.sky(), wl.obs()
+    params = wl.params()
+    m = O.build_model(sky, obs, wl.N, wl.scheme)
+    data = O.simulate_data(sky, obs, np.array(I.FIDUCIAL_T21), I.NOISE_K, wl.noise())
+    t = time.perf_counter()
+    O.loglike(m.A, m.B, data, obs, params[:32])
+    per = (time.perf_counter() - t) / 32
+    budget = 150.0 / max(1, args.steps + args.warmup)       # whole run within a few minutes
+    n = int(max(16, min(wl.P, budget / max(per, 1e-9))))
+    for k in range(args.warmup):
+        O.loglike(m.A, m.B, data, obs, params[:n])
+    times = []
+    for k in range(args.steps):
+        sl = params[(k * n) % (wl.P - n + 1):][:n]
+        t = time.perf_counter()
+        O.loglike(m.A, m.B, data, obs, sl)
+        times.append(time.perf_counter() - t)
+    step = sum(times) / len(times)
+    v = n / step
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "logL evals/s", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_points_per_step": n},
+            "cpu_baseline": {"value": v, "unit": "logL evals/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{n} points of the {wl.P}-point batch per step"},
+            "e2e": {"value": v, "unit": "logL evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2603_13196_gb300 import fg21, inputs as I
+
+    wl = I.workload(3)
+    sky, obs = wl.sky(), wl.obs()
+    t0 = time.time()
+    model = fg21.fg21_build_regions(sky, obs, wl.N, wl.scheme, wl.weighting)
+    build_s = time.time() - t0
+    data = fg21.fg21_simulate_data(sky, obs, I.FIDUCIAL_T21, I.NOISE_K, wl.noise())
+    fg21.fg21_model_set_data(model, data)
+    params = wl.params(extra=rank)                     # each replica its own batch
+    P = params.shape[0]
+    N, F, T = wl.N, wl.F, wl.T
+    d_params = torch.from_numpy(params).to(dev)
+    d_logL = torch.empty(P, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step(prec):
+        fg21.fg21_loglike_batch_device(model, d_params.data_ptr(), P, d_logL.data_ptr(), prec, sptr)
+
+    def timed(prec, K, W):
+        for _ in range(W):
+            flush.zero_()
+            step(prec)
+        torch.cuda.synchronize()
+        fg21.fg21_model_timing(model, True)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        w0 = time.time()
+        for k in range(K):
+            flush.zero_()
+            evs[k][0].record(stream)
+            step(prec)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        w1 = time.time()
+        dev_ms = sum(a.elapsed_time(b) for a, b in evs)
+        calls, prep_ms, main_ms, red_ms = fg21.fg21_model_timing_totals(model)
+        fg21.fg21_model_timing(model, False)
+        inv = fg21.fg21_model_sync_status(model, sptr)
+        return dict(ms_per_step=dev_ms / K, main_ms=main_ms / calls, prep_ms=prep_ms / calls,
+                    reduce_ms=red_ms / calls, wall=(w0, w1), invalid=inv)
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    res = timed(args.precision, args.steps, max(3, args.warmup))
+    clk = clocks.summary(*res["wall"])
+    direct = timed("fp32_direct", max(3, args.steps // 4), 3)
+    clocks.stop()
+
+    # the max over ranks of the per-step device time
+    step_ms = res["ms_per_step"]
+    if ws > 1:
+        t = torch.tensor([step_ms, direct["ms_per_step"]], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        step_ms, direct_ms = float(t[0]), float(t[1])
+    else:
+        direct_ms = direct["ms_per_step"]
+    value = P * ws / (step_ms * 1e-3)
+
+    # end to end through the host-buffer C-ABI call
+    e2e_K = max(5, args.steps // 4)
+    for _ in range(3):
+        fg21.fg21_loglike_batch(model, params, args.precision)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    t = time.perf_counter()
+    for _ in range(e2e_K):
+        out = fg21.fg21_loglike_batch(model, params, args.precision)
+    e2e_s = (time.perf_counter() - t) / e2e_K
+    if ws > 1:
+        tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(tt[0])
+    assert np.all(np.isfinite(out))
+
+    pk, pk_kind = peaks()
+    alg_flops = 2.0 * N * F * T * P
+    achieved = alg_flops / (res["main_ms"] * 1e-3) / 1e12
+    peak = pk["bf16_tflops"]
+    kp, tcp = ((N + 2 + 15) // 16) * 16, ((T + 15) // 16) * 16
+    issued = 2.0 * 3 * kp * tcp * F * (math.ceil(P / 128) * 128)
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "tc_loglike_traffic.json")
+    if os.path.exists(tf):
+        try:
+            traffic = json.load(open(tf)).get("bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "logL evals/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f16x3 (split FP16 tensor, FP32 accumulate, FP64 logL)",
+        "data": "synthetic (seeded sky, beam, data and prior draws; random-init equivalent)",
+        "config": {"workload": WORKLOAD, "N": N, "F": F, "T": T, "P_per_gpu": P, "npix": wl.npix,
+                   "precision": args.precision, "parallelism": f"replicas x{ws}",
+                   "l2": "flushed by a 256 MiB write between timed steps (not timed)",
+                   "build_regions_s": round(build_s, 3)},
+        "fp32_direct": {"value": P * ws / (direct_ms * 1e-3), "unit": "logL evals/s", "ms_per_step": direct_ms,
+                        "speedup_of_value": (P * ws / (step_ms * 1e-3)) / (P * ws / (direct_ms * 1e-3))},
+        "kernels_ms": {"prep": res["prep_ms"], "tc_loglike": res["main_ms"], "reduce": res["reduce_ms"]},
+        "e2e": {"value": P * ws / e2e_s, "unit": "logL evals/s", "h2d_bytes_per_step": int(params.nbytes),
+                "d2h_bytes_per_step": int(P * 8)},
+        "gpu_launches": 4 * args.steps,
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_kind": f"{pk_kind} dense bf16 burst (fp16 same nominal rate)",
+                     "issued_mma_tflops": issued / (res["main_ms"] * 1e-3) / 1e12,
+                     "issued_frac": issued / (res["main_ms"] * 1e-3) / 1e12 / peak},
+        "clocks": clk,
+        "macs_per_s": N * F * T * P * ws / (step_ms * 1e-3),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        cb, _, _ = cpu_baseline(sky, obs, N, params, args.cpu_seconds)
+        line["cpu_baseline"] = cb
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    model.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,285 @@
+/*
+ * fg21.h -- C ABI of the GB300 library for the batched likelihood of the
+ * region-partitioned global-21cm foreground model (arXiv 2603.13196).
+ *
+ * Conventions for every call below:
+ *  - All functions are `extern "C"`, never throw, and return an int status:
+ *    FG21_OK (0) or a negative FG21_E_* code.  fg21_last_error() returns a
+ *    thread-local message describing the last failure of the calling thread.
+ *  - Arrays are row-major (C order) FP64 in HOST memory unless a name says
+ *    `d_` (device memory of the current CUDA device).
+ *  - Parameter rows follow the paper's parameter vector (Sec. 2.3, eq.
+ *    likelihood and the table of priors):
+ *        theta_p = [beta_1 .. beta_N, A21 (K), nu21 (MHz), sigma21 (MHz), sigma_n (K)]
+ *    with regions in ascending spectral-index order, so params is P x (N+4).
+ *  - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *    stream.
+ *  - The library owns the device memory of a model; handles are not
+ *    thread-safe: one call at a time per model (the serving loop, below, is the
+ *    concurrent interface).
+ *  - There is no CPU fallback: without a usable CUDA device every compute call
+ *    returns FG21_E_CUDA.
+ */
+#ifndef FG21_H
+#define FG21_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define FG21_OK            0
+#define FG21_E_ARG        -1   /* invalid argument (NULL, size out of range, bad enum, non-unit vector) */
+#define FG21_E_NOMEM      -2   /* host or device allocation failed */
+#define FG21_E_CUDA       -3   /* CUDA runtime / driver error, or no usable device */
+#define FG21_E_TIMEOUT    -4   /* a wait ran past its limit (serving tickets) */
+#define FG21_E_BUSY       -5   /* admission deferred: not enough memory budget yet */
+#define FG21_E_STATE      -6   /* call not valid in the object's current state */
+#define FG21_E_NOTFOUND   -7   /* unknown run id or ticket */
+#define FG21_E_CANCELLED  -8   /* the request was cancelled before it ran */
+#define FG21_E_DEVICE     -9   /* a kernel reported an internal failure (bounded wait expired) */
+#define FG21_E_RANGE     -10   /* problem size above a documented limit */
+
+/* ------------------------------------------------------------------ enums */
+/* Partition schemes (Sec. 4.1 and Sec. 4.3). */
+#define FG21_SCHEME_RECURSIVE     0  /* Algorithm 2: bisect the largest-mass region at its beta midpoint */
+#define FG21_SCHEME_HIERARCHICAL  1  /* Algorithm 1: 2^floor(log2 N) equal-mass regions, then bisect
+                                        the widest unsplit base region at its importance midpoint */
+#define FG21_SCHEME_LINEAR        2  /* equal-width beta intervals (Sec. 4.1 (i), not nested) */
+#define FG21_SCHEME_PERCENTILE    3  /* equal pixel-count intervals (Sec. 4.1 (ii), not nested) */
+
+/* Importance weightings (Sec. 4.2). */
+#define FG21_WEIGHT_BEAM     0  /* T_sky D H / integral (eq. w_beam_dynamic), the default */
+#define FG21_WEIGHT_SKY      1  /* T_sky H / integral */
+#define FG21_WEIGHT_HORIZON  2  /* H / integral */
+#define FG21_WEIGHT_UNIFORM  3  /* 1/Npix (observation independent) */
+
+/* Arithmetic of the likelihood kernels (all produce FP64 logL). */
+#define FG21_PREC_FP16X3      0  /* tcgen05, reference-subtracted contraction in split FP16 (hi*hi + hi*mid +
+                                    mid*hi), FP32 accumulation in tensor memory; the default */
+#define FG21_PREC_BF16X3      1  /* as FP16X3 with BF16 operands (wider range, 8-bit significands) */
+#define FG21_PREC_FP32_DELTA  2  /* SIMT FP32, reference-subtracted */
+#define FG21_PREC_FP32_DIRECT 3  /* SIMT FP32, the plain eq. fast_forward_model in FP32 (comparator) */
+
+/* Limits. */
+#define FG21_MAX_REGIONS_TC  62      /* N <= 62 on the tensor-core path (K = N + 2 padded to <= 64) */
+#define FG21_MAX_REGIONS    126      /* N limit of region building and of the SIMT paths */
+
+/* ------------------------------------------------------------------ types */
+typedef struct fg21_model fg21_model;     /* opaque: resident A, B, data of one observation + partition */
+typedef struct fg21_server fg21_server;   /* opaque: serving loop */
+
+/* Pixelised sky (Sec. 2.1).  dirs: unit vectors in the frame of `zenith`;
+ * t230: the 230 MHz template [K]; beta: per-pixel spectral index. */
+typedef struct {
+    int64_t npix;
+    const double *dirs;   /* [npix][3] */
+    const double *t230;   /* [npix] */
+    const double *beta;   /* [npix] */
+} fg21_sky;
+
+/* Observation: channels, LST bins and the chromatic beam of eq. simantenna.
+ * The beam is D = 2(p_f + 1) max(0, z_t . v)^p_f, zero below the horizon, which
+ * integrates to 4 pi over the sphere (a directivity). */
+typedef struct {
+    int32_t F;               /* channels */
+    const double *nu;        /* [F] MHz, > 0 */
+    double nu0;              /* reference frequency of the template, MHz (230 in the paper, Sec. 2.1) */
+    int32_t T;               /* LST bins */
+    const double *zenith;    /* [T][3] unit zenith vectors */
+    const double *beam_p;    /* [F] beam exponent p(nu) >= 0 */
+    double t_cmb;            /* K */
+} fg21_obs;
+
+typedef struct {
+    int32_t n_regions;       /* N >= 1 */
+    int32_t scheme;          /* FG21_SCHEME_* */
+    int32_t weighting;       /* FG21_WEIGHT_* */
+} fg21_partition_opts;
+
+/* --------------------------------------------------------------- errors */
+/* Message of the calling thread's last failure ("" if none).  The pointer stays
+ * valid until the thread's next fg21 call. */
+const char *fg21_last_error(void);
+
+/* Number of points the calling thread's last likelihood call marked invalid
+ * (non-finite parameter, sigma_n <= 0 or sigma21 == 0; their logL is -inf). */
+int64_t fg21_last_invalid_count(void);
+
+/* Library version string. */
+const char *fg21_version(void);
+
+/* Number of CUDA devices visible (0 on a machine without a GPU; never fails). */
+int fg21_device_count(void);
+
+/* ---------------------------------------------------------------- build */
+/* Partition the sky into nested regions by importance-weighted spectral index
+ * and precompute the chromatic response functions, for one observation.
+ *   Sec. 4.2 (importance maps, eq. w_beam_dynamic; CDF eq. weighted_cdf),
+ *   Sec. 4.3 (Algorithms 1 and 2), Sec. 2.2 (eq. chromatic_function):
+ *     w[pix]   = (1/(F T)) sum_{f,t} W(pix,f,t),  W = num / sum_pix num
+ *     A[i,f,t] = (1/Npix) sum_{pix in region i} (T230 - T_CMB) D(pix,f,t)
+ *     B[f,t]   = (1/Npix) sum_pix D(pix,f,t)       (multiplies T_CMB)
+ * Regions are (edge_i, edge_{i+1}], the lowest closed below, in ascending
+ * beta; labels are assigned by comparing beta with the edges.  Empty regions
+ * are allowed (their A rows are zero) and counted by fg21_model_info.
+ * On success *out is a new model owned by the caller (fg21_model_destroy);
+ * its data vector is zero until fg21_model_set_data.  labels_out [npix] and
+ * edges_out [N+1] are optional (may be NULL).  The library copies what it
+ * needs; inputs may be freed on return.
+ * Errors: FG21_E_ARG (NULL input, N < 1 or N > npix or N > FG21_MAX_REGIONS,
+ * F, T, npix <= 0, nu <= 0, beam_p < 0, |v| or |z| not within 1e-6 of 1,
+ * unknown scheme/weighting), FG21_E_NOMEM, FG21_E_CUDA. */
+int fg21_build_regions(const fg21_sky *sky, const fg21_obs *obs, const fg21_partition_opts *opt,
+                       fg21_model **out, int32_t *labels_out, double *edges_out);
+
+/* The host half of fg21_build_regions without any device work: the same
+ * partition and precompute, written to caller buffers labels_out [npix],
+ * edges_out [N+1], A_out [N][F][T], B_out [F][T] (each may be NULL).  For
+ * machines without a GPU and for checking the host logic. */
+int fg21_build_regions_host(const fg21_sky *sky, const fg21_obs *obs, const fg21_partition_opts *opt,
+                            int32_t *labels_out, double *edges_out, double *A_out, double *B_out);
+
+/* Release a model and its device memory (NULL is allowed). */
+int fg21_model_destroy(fg21_model *m);
+
+/* Replace the model's data vector D(nu_f, t_l) (eq. likelihood), [F][T] host
+ * FP64, copied to the device; e.g. a signal-free validation set (Sec. 5.2.1). */
+int fg21_model_set_data(fg21_model *m, const double *data);
+
+/* Copy the model's FP64 arrays to host memory: A [N][F][T], B [F][T]
+ * (either may be NULL).  For parity checks against an independent oracle. */
+int fg21_model_get_arrays(const fg21_model *m, double *A, double *B);
+
+/* Sizes of a model; any output pointer may be NULL.  device_bytes counts the
+ * model's resident device memory (A, B, data, tables, workspace). */
+int fg21_model_info(const fg21_model *m, int32_t *N, int32_t *F, int32_t *T, int32_t *n_empty,
+                    size_t *device_bytes);
+
+/* Simulated antenna temperature of eq. simantenna (Sec. 2.1), per pixel with the
+ * sky's own spectral index:
+ *   data[f,t] = (1/Npix) sum_pix D(pix,f,t) T_sky(pix,f) + T21(nu_f; t21)
+ *               + sigma_noise * noise[f,t]
+ * with T_sky of eq. skyapproximation and T21 of eq. t21model.  t21 = {A21, nu21,
+ * sigma21}; noise [F][T] standard-normal draws or NULL (noise-free).
+ * data_out [F][T] is written.  Host FP64 computation; no device needed. */
+int fg21_simulate_data(const fg21_sky *sky, const fg21_obs *obs, const double *t21,
+                       double sigma_noise, const double *noise, double *data_out);
+
+/* ----------------------------------------------------------- likelihood */
+/* Batched Gaussian log-likelihood of the fast forward model (Sec. 2.2 eq.
+ * fast_forward_model plus the trough of eq. t21model; Sec. 2.3.1 eq.
+ * likelihood):
+ *   M[p,f,t] = sum_i A[i,f,t] (nu_f/nu0)^-beta_{p,i} + T_CMB B[f,t] + T21(nu_f; theta_p)
+ *   logL[p]  = -1/2 sum_{f,t} [ ln(2 pi sigma_n^2) + (D[f,t] - M[p,f,t])^2 / sigma_n^2 ]
+ * params [P][N+4] and logL [P] are HOST buffers; the call copies params to the
+ * device, evaluates on `stream`, copies logL back and returns when done.
+ * precision: FG21_PREC_*.  Points with a non-finite parameter, sigma_n <= 0 or
+ * sigma21 == 0 get logL = -inf and are counted (fg21_last_invalid_count); the
+ * call still succeeds.  Prior bounds are not enforced.  P = 0 is a no-op.
+ * Errors: FG21_E_ARG, FG21_E_RANGE (N above the precision's limit),
+ * FG21_E_NOMEM, FG21_E_CUDA, FG21_E_DEVICE. */
+int fg21_loglike_batch(fg21_model *m, const double *params, int64_t P, double *logL,
+                       int precision, void *stream);
+
+/* As fg21_loglike_batch with DEVICE buffers d_params [P][N+4] and d_logL [P],
+ * enqueued asynchronously on `stream` (nothing is copied to or from the host;
+ * the call returns before the kernels finish).  The model's workspace is
+ * reused by the next call on the same model, which must be ordered after this
+ * one (same stream, or synchronised).  The device-side invalid count and any
+ * kernel failure are read by fg21_model_sync_status. */
+int fg21_loglike_batch_device(fg21_model *m, const double *d_params, int64_t P, double *d_logL,
+                              int precision, void *stream);
+
+/* Wait for the model's outstanding work on `stream`, then report the invalid
+ * count of its last device call (may be NULL) and FG21_E_DEVICE if a kernel
+ * reported an internal failure. */
+int fg21_model_sync_status(fg21_model *m, void *stream, int64_t *invalid_count);
+
+/* Kernel timing of a model's calls: with enable != 0 (which also clears the
+ * record), every later likelihood call on m records CUDA events on its launch
+ * stream around the per-request preparation (a1), the main likelihood kernel
+ * (a2-a5) and the reduction (a6), for up to the last 8192 calls.
+ * fg21_model_timing_totals waits for the last recorded call and returns the
+ * number of calls recorded and the summed durations in milliseconds (any
+ * pointer may be NULL); FG21_E_STATE if timing is off or nothing was recorded. */
+int fg21_model_timing(fg21_model *m, int enable);
+int fg21_model_timing_totals(fg21_model *m, int64_t *calls, double *prep_ms, double *main_ms, double *reduce_ms);
+
+/* Model temperatures for a batch (the quantity compared per channel against
+ * the oracle): T_model[p][f][t] = M[p,f,t] above, written to HOST memory,
+ * evaluated with the same arithmetic as `precision` uses inside the likelihood
+ * (the reference-subtracted forms return D - r with r their residual).
+ * Meant for validation at small P (P*F*T*8 bytes of output). */
+int fg21_model_eval(fg21_model *m, const double *params, int64_t P, double *T_model,
+                    int precision, void *stream);
+
+/* Uneven batch: several models (different N, T, P and data) evaluated in ONE
+ * persistent kernel launch.  params[k] [P[k]][N_k+4] and logL[k] [P[k]] are host
+ * buffers.  precision as above (FP16X3 or BF16X3 run as one tensor-core launch;
+ * the SIMT precisions run per model).  Same invalid-point rules. */
+int fg21_loglike_multi(fg21_model *const *models, const double *const *params, const int64_t *P,
+                       double *const *logL, int n_models, int precision, void *stream);
+
+/* ---------------------------------------------------------------- serving */
+/* Continuous-batching likelihood server for many concurrent nested-sampling
+ * runs (Sec. 3: batched replacement of live points, many independent runs).
+ * Runs are registered with a model (device-resident A, B, data), admitted
+ * while their resident bytes fit `mem_budget_bytes`, and submit requests of P
+ * points; a batcher thread packs pending requests into persistent launches
+ * on up to `max_inflight` streams, so new requests are admitted while earlier
+ * batches run.  Each request's result is independent of what it was batched
+ * with (per-request reference, fixed-order reductions). */
+typedef struct {
+    size_t mem_budget_bytes;   /* admission budget over registered runs' resident bytes */
+    int64_t max_batch_points;  /* points per launch (>= the largest single request) */
+    int32_t max_wait_us;       /* how long the batcher waits to fill a launch once work is pending */
+    int32_t max_inflight;      /* launches in flight (1..8) */
+    int32_t precision;         /* FG21_PREC_FP16X3 or FG21_PREC_BF16X3 */
+    int32_t device;            /* CUDA device ordinal */
+} fg21_serve_opts;
+
+typedef struct {
+    double p50_ms, p99_ms, mean_ms;   /* submit -> completion latency of finished requests */
+    double evals_per_s;               /* points evaluated / wall time since create */
+    double macs_per_s;                /* algorithmic N*F*T multiply-adds per second */
+    int64_t requests_done, points_done, launches;
+    int64_t queue_depth;              /* requests waiting for a launch */
+    size_t admitted_bytes;            /* resident bytes of admitted runs */
+    int32_t runs_admitted, runs_waiting;
+} fg21_stats;
+
+typedef int64_t fg21_ticket;
+
+int fg21_serve_create(const fg21_serve_opts *opts, fg21_server **out);
+/* Stop the batcher after in-flight launches finish; pending tickets complete
+ * with FG21_E_CANCELLED.  NULL is allowed. */
+int fg21_serve_destroy(fg21_server *s);
+/* Register a run that evaluates against `m` (not owned; must outlive the run).
+ * Returns FG21_OK if admitted now, FG21_E_BUSY if queued for admission (it is
+ * admitted in order once budget frees up; submits to it wait for admission).
+ * A run whose bytes exceed the whole budget is rejected with FG21_E_RANGE. */
+int fg21_serve_register_run(fg21_server *s, fg21_model *m, int32_t *run_id);
+/* Remove a run; its pending requests complete with FG21_E_CANCELLED. */
+int fg21_serve_unregister_run(fg21_server *s, int32_t run_id);
+/* Queue P points (params copied now).  logL_out [P] must stay valid until the
+ * ticket completes or is cancelled. */
+int fg21_serve_submit(fg21_server *s, int32_t run_id, const double *params, int64_t P,
+                      double *logL_out, fg21_ticket *ticket);
+/* Wait up to timeout_ms (< 0: no limit) for a ticket; returns the request's
+ * status (FG21_OK, FG21_E_CANCELLED, FG21_E_DEVICE ...) or FG21_E_TIMEOUT.
+ * A completed ticket is released by the first wait/poll that reports it. */
+int fg21_serve_wait(fg21_server *s, fg21_ticket t, int32_t timeout_ms);
+/* Non-blocking: FG21_E_BUSY while pending, else as fg21_serve_wait. */
+int fg21_serve_poll(fg21_server *s, fg21_ticket t);
+/* Cancel a pending ticket (no effect once its launch started). */
+int fg21_serve_cancel(fg21_server *s, fg21_ticket t);
+int fg21_serve_stats(fg21_server *s, fg21_stats *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FG21_H */

@@ -1,0 +1,122 @@
+// Internal declarations shared by the host code and the CUDA kernels of libfg21.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fg21.h"
+
+namespace fg21 {
+
+// ------------------------------------------------------------------ errors
+int set_error(int code, const char *fmt, ...);
+void set_invalid_count(int64_t n);
+int cuda_error(cudaError_t e, const char *what);
+#define FG21_CUDA_TRY(expr)                                            \
+    do {                                                               \
+        cudaError_t e__ = (expr);                                      \
+        if (e__ != cudaSuccess) return ::fg21::cuda_error(e__, #expr); \
+    } while (0)
+
+// Device status word bits (written by kernels with atomicOr).
+enum : unsigned {
+    STATUS_TIMEOUT_TMA = 1u,
+    STATUS_TIMEOUT_MMA = 2u,
+    STATUS_TIMEOUT_GEN = 4u,
+    STATUS_TIMEOUT_EPI = 8u,
+    STATUS_TIMEOUT_DRAIN = 16u,
+    STATUS_BAD_SHAPE = 32u,
+};
+
+constexpr int TILE_M = 128;         // points per MMA tile (tcgen05 M)
+constexpr int TC_MAX = 256;         // max t-columns per MMA (tcgen05 N)
+constexpr int STAT_BLOCK = 256;     // points per statistics block of the per-request prep
+constexpr int KP_MAX = 64;          // max padded K on the tensor path
+
+// Per-request descriptor, laid out identically on host and device.
+struct ReqDesc {
+    // model arrays (device)
+    const double *A;       // [N][F][T]
+    const double *B;       // [F][T]
+    const double *data;    // [F][T]
+    const double *L;       // [F] ln(nu_f / nu0)
+    const double *nu;      // [F] MHz
+    const float *A32;      // [N][F][T]   (direct FP32 form)
+    const float *B32;      // [F][T]
+    const float *data32;   // [F][T]
+    // request I/O (device)
+    const double *params;  // [P][N+4]
+    double *logL;          // [P]
+    double t_cmb;
+    double Lmax;           // max_f |ln(nu_f / nu0)|
+    int64_t P;
+    int N, F, T;
+    int Kp;                // K = N + 2 padded to a multiple of 16 (tensor path)
+    int Tc, Tc_pad, n_tchunks;   // t-chunks: Tc columns each (last may be shorter), padded to 16
+    int G, ch_per_group;         // channel groups per 128-point tile
+    int n_tiles;                 // ceil(P / 128)
+    int n_stat_blocks;           // ceil(P / STAT_BLOCK)
+    int64_t item_begin;          // first global work-item id of this request
+    int64_t tile_row0;           // first 128-byte row of this request's operand tiles in the arena
+    int64_t tile_rows;           // rows per (channel, t-chunk) tile
+    int64_t pt_begin;            // first global point index of this request (reduction)
+    char *tiles;                 // this request's operand tiles (arena + tile_row0 * 128)
+    // workspace (device)
+    double *stat_part;     // [n_stat_blocks][3N + 2]: sum, min, max per region, n_valid, max|A21|
+    double *beta_bar;      // [N]
+    double *req_stats;     // [4]: n_valid, max|dev|*max|L| (x), max|A21|, reserved
+    float *nL32;           // [F] -ln(nu_f/nu0)
+    float *nu32;           // [F]
+    int *scaleB;           // [F * n_tchunks] power-of-two exponent of each operand tile
+    int *scaleW;           // [1] power-of-two exponent of the weight operand
+    float *Bp32;           // [N][F][T] wbar_i A (FP32, SIMT delta form)
+    float *dref32;         // [F][T]    reference residual (FP32, SIMT delta form)
+    float2 *partials;      // [P][G] compensated partial chi^2 (hi, lo)
+    unsigned *status;      // device status word (shared by a launch)
+    unsigned long long *invalid;  // invalid-point counter
+};
+
+// Sizes of one request's workspace pieces (bytes, each 256-aligned).
+struct ReqLayout {
+    size_t stat_part, beta_bar, req_stats, nL32, nu32, scaleB, scaleW, Bp32, dref32, partials, tiles;
+    size_t total() const {
+        return stat_part + beta_bar + req_stats + nL32 + nu32 + scaleB + scaleW + Bp32 + dref32 +
+               partials + tiles;
+    }
+};
+
+// Shape decisions for one request (autotuned channel grouping).
+void plan_request(ReqDesc &r, int precision, int num_sms, int64_t total_tiles_in_launch);
+ReqLayout request_layout(const ReqDesc &r, int precision);
+
+// ------------------------------------------------------- kernel launchers
+// All enqueue on `stream` and return cudaError_t of the launch.
+cudaError_t launch_prep(const ReqDesc *h_reqs, const ReqDesc *d_reqs, int n_reqs, int precision,
+                        int max_stat_blocks, int max_F_chunks, cudaStream_t stream);
+cudaError_t launch_simt(const ReqDesc *h_reqs, const ReqDesc *d_reqs, int n_reqs, int precision,
+                        cudaStream_t stream);
+cudaError_t launch_reduce(const ReqDesc *h_reqs, const ReqDesc *d_reqs, int n_reqs,
+                          cudaStream_t stream);
+cudaError_t launch_model_eval(const ReqDesc *h_req, const ReqDesc *d_req, int precision,
+                              double *d_out, cudaStream_t stream);
+// Tensor kernel in validation mode: writes the residual D - M of every (p, f, t)
+// of one request to resid [P][F][T] instead of reducing it.
+cudaError_t launch_tc_residuals(const ReqDesc *h_req, const ReqDesc *d_req, int precision, float *resid,
+                                cudaStream_t stream);
+
+// Tensor-core path: one persistent launch over all requests' work items.
+struct TcLaunch {
+    const ReqDesc *d_reqs;
+    int n_reqs;
+    int64_t n_items;
+    int kp_max;              // max padded K over requests
+    int tc_pad_max;          // max padded t-chunk over requests
+    int precision;           // FG21_PREC_FP16X3 / BF16X3
+    void *arena;             // operand tile arena (device), 128-byte rows
+    int64_t arena_rows;
+    unsigned *status;
+};
+cudaError_t launch_tc(const TcLaunch &L, int num_sms, cudaStream_t stream);
+int tc_map_init();  // resolves cuTensorMapEncodeTiled; FG21_OK or error
+
+}  // namespace fg21

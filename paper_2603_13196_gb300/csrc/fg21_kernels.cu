@@ -1,0 +1,527 @@
+// Per-request preparation, SIMT likelihood kernels and the fixed-order
+// reduction of libfg21 (sm_103a).
+//
+// The likelihood of eq. likelihood (Sec. 2.3.1) over the fast forward model of
+// eq. fast_forward_model (Sec. 2.2) is evaluated in a reference-subtracted form:
+// with a per-request reference spectral index bbar_i (mean over the request's
+// valid points) and wbar_{i,f} = (nu_f/nu0)^-bbar_i,
+//
+//   D - M = dref[f,t] - sum_i (wbar_{i,f} A[i,f,t]) expm1(-(beta_{p,i} - bbar_i) L_f) - T21(nu_f)
+//   dref[f,t] = D[f,t] - sum_i wbar_{i,f} A[i,f,t] - T_CMB B[f,t]          (FP64, once per request)
+//
+// which is an exact rearrangement of D - M.  The large foreground cancels in
+// FP64 inside dref, so the per-point arithmetic only carries the (small)
+// departure of each point from the reference.  The plain FP32 form
+// (FG21_PREC_FP32_DIRECT) evaluates M directly and is kept as the comparator.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fg21_internal.h"
+
+namespace fg21 {
+
+namespace {
+
+constexpr int PREP_THREADS = 256;
+
+__device__ __forceinline__ bool point_valid(const double *th, int N) {
+    bool ok = true;
+    for (int k = 0; k < N + 4; ++k) ok &= isfinite(th[k]);
+    ok &= th[N + 3] > 0.0;      // sigma_n > 0
+    ok &= th[N + 2] != 0.0;     // sigma21 != 0
+    return ok;
+}
+
+// Deterministic block reductions (fixed shuffle tree, then warps in order).
+template <typename Op>
+__device__ double block_reduce(double v, Op op, double *sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double r = sh[0];
+    for (int w = 1; w < nw; ++w) r = op(r, sh[w]);
+    __syncthreads();
+    return r;
+}
+
+struct OpSum { __device__ double operator()(double a, double b) const { return a + b; } };
+struct OpMin { __device__ double operator()(double a, double b) const { return fmin(a, b); } };
+struct OpMax { __device__ double operator()(double a, double b) const { return fmax(a, b); } };
+
+// a1, pass 1: per block of STAT_BLOCK points, the sum / min / max of each
+// region's beta over valid points, the valid count and max |A21|.
+__global__ void __launch_bounds__(PREP_THREADS) prep_stats_kernel(const ReqDesc *__restrict__ reqs) {
+    __shared__ double sh[32];
+    const ReqDesc &r = reqs[blockIdx.y];
+    if ((int)blockIdx.x >= r.n_stat_blocks) return;
+    const int N = r.N;
+    const int64_t p = (int64_t)blockIdx.x * STAT_BLOCK + threadIdx.x;
+    const double *th = r.params + p * (N + 4);
+    const bool valid = p < r.P && point_valid(th, N);
+    double *out = r.stat_part + (size_t)blockIdx.x * (3 * N + 2);
+    for (int i = 0; i < N; ++i) {
+        double b = valid ? th[i] : 0.0;
+        double s = block_reduce(b, OpSum(), sh);
+        double mn = block_reduce(valid ? b : INFINITY, OpMin(), sh);
+        double mx = block_reduce(valid ? b : -INFINITY, OpMax(), sh);
+        if (threadIdx.x == 0) {
+            out[3 * i] = s;
+            out[3 * i + 1] = mn;
+            out[3 * i + 2] = mx;
+        }
+    }
+    double nv = block_reduce(valid ? 1.0 : 0.0, OpSum(), sh);
+    double ma = block_reduce(valid ? fabs(th[N]) : 0.0, OpMax(), sh);
+    if (threadIdx.x == 0) {
+        out[3 * N] = nv;
+        out[3 * N + 1] = ma;
+    }
+}
+
+__device__ __forceinline__ int pow2_exponent_for(double maxabs) {
+    // largest s with 2^s * maxabs <= 2^15 (half the FP16 range), clamped
+    if (!(maxabs > 0.0)) return 0;
+    int e = (int)floor(log2(32768.0 / maxabs));
+    return max(-40, min(40, e));
+}
+
+// a1, pass 2: one block per (channel, t-chunk).  Every block finalises the
+// request statistics in the same fixed order (so all agree bit for bit), then
+// builds its channel's reference: wbar, wbar*A, dref; and writes either the
+// FP32 arrays of the SIMT delta form or the split-precision operand tile of
+// the tensor-core form.
+//
+// Operand tile layout (one per channel and t-chunk, 2 x Kp x Tc_pad 16-bit
+// values): [split s in {hi, mid}][k-chunk kc = k/8][t][8 values k%8], i.e. the
+// K-major core-matrix layout (8 rows of 16 bytes) the tensor cores read; row k
+// < N holds wbar_k A[k,f,t] 2^sB, row N holds 2^sB (multiplies the trough
+// column of the weights), row N+1 holds dref 2^sB (multiplies -1), other rows
+// and columns t >= Tc are zero.
+template <bool BF16>
+__device__ __forceinline__ uint16_t to_bits(double v) {
+    if (BF16) {
+        __nv_bfloat16 h = __double2bfloat16(v);
+        return *reinterpret_cast<uint16_t *>(&h);
+    } else {
+        __half h = __double2half(v);
+        return *reinterpret_cast<uint16_t *>(&h);
+    }
+}
+template <bool BF16>
+__device__ __forceinline__ double from_bits(uint16_t b) {
+    if (BF16) {
+        __nv_bfloat16 h = *reinterpret_cast<__nv_bfloat16 *>(&b);
+        return (double)__bfloat162float(h);
+    } else {
+        __half h = *reinterpret_cast<__half *>(&b);
+        return (double)__half2float(h);
+    }
+}
+
+// a1, pass 2 (one block per request): the reference point bbar_i = mean of
+// the valid points' beta_i (stat blocks summed in a fixed order), the largest
+// weight argument x = max_i |beta - bbar_i| * max_f |L_f| (which sets the
+// weight polynomial and the power-of-two scale sW of the weight operand), the
+// valid count and max |A21|.
+__global__ void __launch_bounds__(PREP_THREADS) prep_finalize_kernel(const ReqDesc *__restrict__ reqs) {
+    __shared__ double sh[32];
+    const ReqDesc &r = reqs[blockIdx.x];
+    const int N = r.N, nb = r.n_stat_blocks, stride = 3 * N + 2;
+    double nv = 0.0, ma = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        nv += r.stat_part[(size_t)b * stride + 3 * N];
+        ma = fmax(ma, r.stat_part[(size_t)b * stride + 3 * N + 1]);
+    }
+    // fixed-order: per-thread strided partials, then the deterministic tree
+    nv = block_reduce(nv, OpSum(), sh);
+    ma = block_reduce(ma, OpMax(), sh);
+    double dmax = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        double s = 0.0, mn = INFINITY, mx = -INFINITY;
+        for (int b = 0; b < nb; ++b) {
+            const double *q = r.stat_part + (size_t)b * stride + 3 * i;
+            s += q[0];
+            mn = fmin(mn, q[1]);
+            mx = fmax(mx, q[2]);
+        }
+        const double bb = nv > 0.0 ? s / nv : 0.0;
+        r.beta_bar[i] = bb;
+        if (nv > 0.0) dmax = fmax(dmax, fmax(mx - bb, bb - mn));
+    }
+    dmax = block_reduce(dmax, OpMax(), sh);
+    if (threadIdx.x == 0) {
+        const double x = dmax * r.Lmax;
+        r.req_stats[0] = nv;
+        r.req_stats[1] = x;
+        r.req_stats[2] = ma;
+        *r.scaleW = pow2_exponent_for(fmax(fmax(expm1(x), ma), 1.0));
+    }
+}
+
+// a1, pass 3: one block per (channel, t-chunk) builds that channel's
+// reference: wbar_i = (nu_f/nu0)^-bbar_i, wbar_i A[i,f,t] and
+// dref = D - sum_i wbar_i A_i - T_CMB B (FP64), then writes either the FP32
+// arrays of the SIMT delta form or the split-precision operand tile of the
+// tensor-core form.
+//
+// Operand tile layout (one per channel and t-chunk, 2 x Kp x Tc_pad 16-bit
+// values): [split s in {hi, mid}][k-chunk kc = k/8][t][8 values k%8], i.e. the
+// K-major core-matrix layout (8 rows of 16 bytes) the tensor cores read; row k
+// < N holds wbar_k A[k,f,t] 2^sB, row N holds 2^sB (multiplies the trough
+// column of the weights), row N+1 holds dref 2^sB (multiplies -1), other rows
+// and columns t >= Tc are zero.
+template <int MODE>  // 0 = tensor FP16, 1 = tensor BF16, 2 = SIMT delta, 3 = SIMT direct
+__global__ void __launch_bounds__(PREP_THREADS) prep_tiles_kernel(const ReqDesc *__restrict__ reqs) {
+    extern __shared__ double smem_d[];
+    __shared__ double sh[32];
+    __shared__ int s_scaleB;
+    const ReqDesc &r = reqs[blockIdx.y];
+    const int fc = blockIdx.x;
+    if (fc >= r.F * r.n_tchunks) return;
+    const int f = fc / r.n_tchunks, c = fc % r.n_tchunks;
+    const int N = r.N, T = r.T;
+    const int t0 = c * r.Tc, tn = min(r.Tc, T - t0);
+    double *wbar = smem_d;              // [N]
+    double *dref = smem_d + N;          // [Tc]
+    const double L = r.L[f];
+    for (int i = threadIdx.x; i < N; i += blockDim.x) wbar[i] = exp(-r.beta_bar[i] * L);
+    if (c == 0 && threadIdx.x == 0) {
+        r.nL32[f] = (float)(-L);
+        r.nu32[f] = (float)r.nu[f];
+    }
+    __syncthreads();
+    // --- reference residual dref[t] = D - sum_i wbar_i A_i - T_CMB B ---
+    double vmax = 1.0;
+    for (int t = threadIdx.x; t < tn; t += blockDim.x) {
+        const size_t ft = (size_t)f * T + t0 + t;
+        double s = 0.0;
+        for (int i = 0; i < N; ++i) {
+            double bw = wbar[i] * r.A[(size_t)i * r.F * T + ft];
+            s += bw;
+            vmax = fmax(vmax, fabs(bw));
+            if (MODE == 2) r.Bp32[(size_t)i * r.F * T + ft] = (float)bw;
+        }
+        double d = r.data[ft] - s - r.t_cmb * r.B[ft];
+        dref[t] = d;
+        vmax = fmax(vmax, fabs(d));
+        if (MODE == 2) r.dref32[ft] = (float)d;
+    }
+    if (MODE >= 2) return;
+    vmax = block_reduce(vmax, OpMax(), sh);
+    if (threadIdx.x == 0) {
+        s_scaleB = pow2_exponent_for(vmax);
+        r.scaleB[fc] = s_scaleB;
+    }
+    __syncthreads();
+    const double sB = ldexp(1.0, s_scaleB);
+    // --- operand tile: one 16-byte chunk (8 values of k) per (split, kc, t) ---
+    const int Kp = r.Kp, Tcp = r.Tc_pad, nkc = Kp / 8;
+    uint4 *tile = reinterpret_cast<uint4 *>(r.tiles + (size_t)fc * r.tile_rows * 128);
+    for (int j = threadIdx.x; j < nkc * Tcp; j += blockDim.x) {
+        const int kc = j / Tcp, t = j % Tcp;
+        uint16_t hi[8], mid[8];
+        for (int e = 0; e < 8; ++e) {
+            const int k = kc * 8 + e;
+            double v = 0.0;
+            if (t < tn) {
+                if (k < N) v = wbar[k] * r.A[(size_t)k * r.F * T + (size_t)f * T + t0 + t];
+                else if (k == N) v = 1.0;
+                else if (k == N + 1) v = dref[t];
+            }
+            v *= sB;
+            hi[e] = to_bits<MODE == 1>(v);
+            mid[e] = to_bits<MODE == 1>(v - from_bits<MODE == 1>(hi[e]));
+        }
+        uint4 H, M;
+        H.x = hi[0] | ((uint32_t)hi[1] << 16); H.y = hi[2] | ((uint32_t)hi[3] << 16);
+        H.z = hi[4] | ((uint32_t)hi[5] << 16); H.w = hi[6] | ((uint32_t)hi[7] << 16);
+        M.x = mid[0] | ((uint32_t)mid[1] << 16); M.y = mid[2] | ((uint32_t)mid[3] << 16);
+        M.z = mid[4] | ((uint32_t)mid[5] << 16); M.w = mid[6] | ((uint32_t)mid[7] << 16);
+        tile[(size_t)kc * Tcp + t] = H;                      // split 0 (hi)
+        tile[(size_t)(nkc + kc) * Tcp + t] = M;              // split 1 (mid)
+    }
+}
+
+// ------------------------------------------------------------- SIMT paths
+// One block = 128 points of one request x one channel group.  Each thread owns
+// a point: its weights for the channel go to a private shared-memory column,
+// the channel's model slice is staged in shared memory (broadcast reads), and
+// the residual of each (f, t) is squared and summed in FP32 per channel, the
+// channels folded into a compensated (hi, lo) FP32 pair.
+constexpr int SIMT_THREADS = 128;
+constexpr int SIMT_TCH = 64;
+
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
+    float y = x - c;
+    float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+__device__ __forceinline__ int find_req_by_item(const ReqDesc *__restrict__ reqs, int n_reqs, int64_t item) {
+    int lo = 0, hi = n_reqs - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (reqs[mid].item_begin <= item) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int find_req_by_point(const ReqDesc *__restrict__ reqs, int n_reqs, int64_t pt) {
+    int lo = 0, hi = n_reqs - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (reqs[mid].pt_begin <= pt) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int TCH, bool DIRECT>
+__device__ __forceinline__ float simt_chunk(const float *__restrict__ As, const float *__restrict__ ds,
+                                            const float *__restrict__ wcol, int N, int nvalid, float s21) {
+    float acc[TCH];
+#pragma unroll
+    for (int j = 0; j < TCH; ++j) acc[j] = 0.0f;
+    for (int i = 0; i < N; ++i) {
+        const float w = wcol[i * SIMT_THREADS];
+        const float4 *a4 = reinterpret_cast<const float4 *>(As + i * SIMT_TCH);
+#pragma unroll
+        for (int j = 0; j < TCH / 4; ++j) {
+            float4 a = a4[j];
+            acc[4 * j] = fmaf(a.x, w, acc[4 * j]);
+            acc[4 * j + 1] = fmaf(a.y, w, acc[4 * j + 1]);
+            acc[4 * j + 2] = fmaf(a.z, w, acc[4 * j + 2]);
+            acc[4 * j + 3] = fmaf(a.w, w, acc[4 * j + 3]);
+        }
+    }
+    float q = 0.0f;
+#pragma unroll
+    for (int j = 0; j < TCH; ++j) {
+        if (j < nvalid) {
+            float rr = (ds[j] - s21) - acc[j];
+            q = fmaf(rr, rr, q);
+        }
+    }
+    return q;
+}
+
+template <bool DIRECT>
+__global__ void __launch_bounds__(SIMT_THREADS) simt_kernel(const ReqDesc *__restrict__ reqs, int n_reqs) {
+    extern __shared__ float smem_f[];
+    const int64_t item = blockIdx.x;
+    const ReqDesc &r = reqs[find_req_by_item(reqs, n_reqs, item)];
+    const int64_t lid = item - r.item_begin;
+    const int tile = (int)(lid / r.G), g = (int)(lid % r.G);
+    const int N = r.N, F = r.F, T = r.T;
+    const int f0 = g * r.ch_per_group, f1 = min(F, f0 + r.ch_per_group);
+    float *wcol_all = smem_f;                          // [N][128]
+    float *As = smem_f + N * SIMT_THREADS;             // [N][64]
+    float *ds = As + N * SIMT_TCH;                     // [64]
+    const int64_t p = (int64_t)tile * TILE_M + threadIdx.x;
+    const bool inb = p < r.P;
+    const double *th = r.params + (inb ? p : 0) * (N + 4);
+    const float a21 = (float)th[N], nu21 = (float)th[N + 1];
+    const float inv2s2 = (float)(1.0 / (2.0 * th[N + 2] * th[N + 2]));
+    float qs = 0.0f, qc = 0.0f;
+    float *wcol = wcol_all + threadIdx.x;
+    for (int f = f0; f < f1; ++f) {
+        const float nuf = (float)r.nu[f];
+        const float dnu = nuf - nu21;
+        const float s21 = a21 * expf(-dnu * dnu * inv2s2);
+        if (DIRECT) {
+            const float l2 = (float)(r.L[f] * 1.4426950408889634);   // log2(nu/nu0)
+            for (int i = 0; i < N; ++i) wcol[i * SIMT_THREADS] = exp2f(-(float)th[i] * l2);
+        } else {
+            const float nL = (float)(-r.L[f]);
+            for (int i = 0; i < N; ++i)
+                wcol[i * SIMT_THREADS] = expm1f((float)(th[i] - r.beta_bar[i]) * nL);
+        }
+        float qf = 0.0f;
+        for (int tb = 0; tb < T; tb += SIMT_TCH) {
+            const int nvalid = min(SIMT_TCH, T - tb);
+            __syncthreads();
+            for (int k = threadIdx.x; k < N * SIMT_TCH; k += SIMT_THREADS) {
+                const int i = k / SIMT_TCH, j = k % SIMT_TCH;
+                float v = 0.0f;
+                if (j < nvalid) {
+                    const size_t idx = ((size_t)i * F + f) * T + tb + j;
+                    v = DIRECT ? r.A32[idx] : r.Bp32[idx];
+                }
+                As[k] = v;
+            }
+            for (int j = threadIdx.x; j < SIMT_TCH; j += SIMT_THREADS) {
+                float v = 0.0f;
+                if (j < nvalid) {
+                    const size_t ft = (size_t)f * T + tb + j;
+                    v = DIRECT ? r.data32[ft] - (float)r.t_cmb * r.B32[ft] : r.dref32[ft];
+                }
+                ds[j] = v;
+            }
+            __syncthreads();
+            if (nvalid > 32)
+                qf += simt_chunk<64, DIRECT>(As, ds, wcol, N, nvalid, s21);
+            else if (nvalid > 16)
+                qf += simt_chunk<32, DIRECT>(As, ds, wcol, N, nvalid, s21);
+            else
+                qf += simt_chunk<16, DIRECT>(As, ds, wcol, N, nvalid, s21);
+        }
+        kahan_add(qs, qc, qf);
+    }
+    if (inb) r.partials[(size_t)p * r.G + g] = make_float2(qs, -qc);
+}
+
+// a6: per point, sum the channel-group partials in fixed order (FP64) and form
+// lnL = -1/2 (F T ln(2 pi sigma_n^2) + chi2 / sigma_n^2) (eq. likelihood).
+__global__ void reduce_kernel(const ReqDesc *__restrict__ reqs, int n_reqs) {
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const ReqDesc &r = reqs[find_req_by_point(reqs, n_reqs, gid)];
+    const int64_t p = gid - r.pt_begin;
+    if (p < 0 || p >= r.P) return;
+    const int N = r.N;
+    const double *th = r.params + p * (N + 4);
+    if (!point_valid(th, N)) {
+        r.logL[p] = -INFINITY;
+        atomicAdd(r.invalid, 1ull);
+        return;
+    }
+    double chi2 = 0.0;
+    for (int g = 0; g < r.G; ++g) {
+        float2 v = r.partials[(size_t)p * r.G + g];
+        chi2 += (double)v.x + (double)v.y;
+    }
+    const double sig = th[N + 3];
+    const double n = (double)r.F * (double)r.T;
+    r.logL[p] = -0.5 * (n * log(2.0 * 3.141592653589793 * sig * sig) + chi2 / (sig * sig));
+}
+
+// Validation helper: T_model[p,f,t] with the arithmetic of the SIMT forms.
+template <bool DIRECT>
+__global__ void model_eval_simt_kernel(const ReqDesc *__restrict__ req, double *__restrict__ out) {
+    const ReqDesc &r = *req;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t total = r.P * r.F * r.T;
+    if (gid >= total) return;
+    const int64_t p = gid / ((int64_t)r.F * r.T);
+    const int f = (int)((gid / r.T) % r.F), t = (int)(gid % r.T);
+    const int N = r.N;
+    const double *th = r.params + p * (N + 4);
+    const size_t ft = (size_t)f * r.T + t;
+    const float nuf = (float)r.nu[f], dnu = nuf - (float)th[N + 1];
+    const float s21 = (float)th[N] * expf(-dnu * dnu * (float)(1.0 / (2.0 * th[N + 2] * th[N + 2])));
+    if (DIRECT) {
+        const float l2 = (float)(r.L[f] * 1.4426950408889634);
+        float acc = 0.0f;
+        for (int i = 0; i < N; ++i) acc = fmaf(r.A32[(size_t)i * r.F * r.T + ft], exp2f(-(float)th[i] * l2), acc);
+        out[gid] = (double)(acc + (float)r.t_cmb * r.B32[ft] + s21);
+    } else {
+        const float nL = (float)(-r.L[f]);
+        float acc = 0.0f;
+        for (int i = 0; i < N; ++i)
+            acc = fmaf(r.Bp32[(size_t)i * r.F * r.T + ft], expm1f((float)(th[i] - r.beta_bar[i]) * nL), acc);
+        const float rr = (r.dref32[ft] - s21) - acc;
+        out[gid] = r.data[ft] - (double)rr;
+    }
+}
+
+__global__ void resid_to_model_kernel(const ReqDesc *__restrict__ req, const float *__restrict__ resid,
+                                      double *__restrict__ out) {
+    const ReqDesc &r = *req;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t total = r.P * r.F * r.T;
+    if (gid >= total) return;
+    const size_t ft = (size_t)(gid % ((int64_t)r.F * r.T));
+    out[gid] = r.data[ft] - (double)resid[gid];
+}
+
+}  // namespace
+
+cudaError_t launch_prep(const ReqDesc *h_reqs, const ReqDesc *d_reqs, int n_reqs, int precision,
+                        int max_stat_blocks, int max_F_chunks, cudaStream_t stream) {
+    dim3 g1(max_stat_blocks, n_reqs);
+    prep_stats_kernel<<<g1, PREP_THREADS, 0, stream>>>(d_reqs);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    prep_finalize_kernel<<<n_reqs, PREP_THREADS, 0, stream>>>(d_reqs);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int maxN = 0, maxTcp = 0;
+    for (int k = 0; k < n_reqs; ++k) {
+        maxN = maxN > h_reqs[k].N ? maxN : h_reqs[k].N;
+        maxTcp = maxTcp > h_reqs[k].Tc_pad ? maxTcp : h_reqs[k].Tc_pad;
+    }
+    const size_t sm = sizeof(double) * ((size_t)maxN + maxTcp);
+    dim3 g2(max_F_chunks, n_reqs);
+    switch (precision) {
+        case FG21_PREC_FP16X3: prep_tiles_kernel<0><<<g2, PREP_THREADS, sm, stream>>>(d_reqs); break;
+        case FG21_PREC_BF16X3: prep_tiles_kernel<1><<<g2, PREP_THREADS, sm, stream>>>(d_reqs); break;
+        case FG21_PREC_FP32_DELTA: prep_tiles_kernel<2><<<g2, PREP_THREADS, sm, stream>>>(d_reqs); break;
+        default: prep_tiles_kernel<3><<<g2, PREP_THREADS, sm, stream>>>(d_reqs); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_simt(const ReqDesc *h_reqs, const ReqDesc *d_reqs, int n_reqs, int precision,
+                        cudaStream_t stream) {
+    int64_t items = 0;
+    int maxN = 0;
+    for (int k = 0; k < n_reqs; ++k) {
+        items += (int64_t)h_reqs[k].n_tiles * h_reqs[k].G;
+        maxN = maxN > h_reqs[k].N ? maxN : h_reqs[k].N;
+    }
+    if (items == 0) return cudaSuccess;
+    const size_t sm = sizeof(float) * ((size_t)maxN * (SIMT_THREADS + SIMT_TCH) + SIMT_TCH);
+    static bool attr_done[2] = {false, false};
+    const bool direct = precision == FG21_PREC_FP32_DIRECT;
+    if (!attr_done[direct]) {
+        cudaError_t e = direct ? cudaFuncSetAttribute(simt_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)
+                               : cudaFuncSetAttribute(simt_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_done[direct] = true;
+    }
+    if (direct)
+        simt_kernel<true><<<(unsigned)items, SIMT_THREADS, sm, stream>>>(d_reqs, n_reqs);
+    else
+        simt_kernel<false><<<(unsigned)items, SIMT_THREADS, sm, stream>>>(d_reqs, n_reqs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const ReqDesc *h_reqs, const ReqDesc *d_reqs, int n_reqs, cudaStream_t stream) {
+    int64_t pts = 0;
+    for (int k = 0; k < n_reqs; ++k) pts += h_reqs[k].P;
+    if (pts == 0) return cudaSuccess;
+    const int th = 256;
+    reduce_kernel<<<(unsigned)((pts + th - 1) / th), th, 0, stream>>>(d_reqs, n_reqs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_model_eval(const ReqDesc *h_req, const ReqDesc *d_req, int precision, double *d_out,
+                              cudaStream_t stream) {
+    const int64_t total = h_req->P * h_req->F * h_req->T;
+    const int th = 256;
+    const unsigned blocks = (unsigned)((total + th - 1) / th);
+    if (precision == FG21_PREC_FP32_DIRECT) {
+        model_eval_simt_kernel<true><<<blocks, th, 0, stream>>>(d_req, d_out);
+        return cudaGetLastError();
+    }
+    if (precision == FG21_PREC_FP32_DELTA) {
+        model_eval_simt_kernel<false><<<blocks, th, 0, stream>>>(d_req, d_out);
+        return cudaGetLastError();
+    }
+    // tensor-core forms: rerun the tensor kernel writing its residuals, then D - r
+    float *resid = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&resid, sizeof(float) * total, stream);
+    if (e != cudaSuccess) return e;
+    e = launch_tc_residuals(h_req, d_req, precision, resid, stream);
+    if (e == cudaSuccess) {
+        resid_to_model_kernel<<<blocks, th, 0, stream>>>(d_req, resid, d_out);
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(resid, stream);
+    return e;
+}
+
+}  // namespace fg21

@@ -1,0 +1,645 @@
+// Model handles, device workspaces, shape planning and the likelihood entry
+// points of fg21.h.  Every likelihood is evaluated by the kernels in
+// fg21_kernels.cu (prep, SIMT, reduce) and fg21_tc.cu (tensor cores).
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "fg21_internal.h"
+#include "fg21_model.h"
+
+namespace fg21 {
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+static int round16(int x) { return (x + 15) & ~15; }
+
+int num_sms_of(int device) {
+    static std::mutex mu;
+    static std::vector<int> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    if ((int)cache.size() <= device) cache.resize(device + 1, 0);
+    if (!cache[device]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+            cudaGetLastError();
+            n = 1;
+        }
+        cache[device] = n;
+    }
+    return cache[device];
+}
+
+// ------------------------------------------------------------- workspace
+int Workspace::ensure(size_t dev_need, size_t arena_need, size_t pinned_need, int n_reqs) {
+    if (device < 0) FG21_CUDA_TRY(cudaGetDevice(&device));
+    if (!done) FG21_CUDA_TRY(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+    // staging and scratch may still be in use by the previous call on this workspace
+    FG21_CUDA_TRY(cudaEventSynchronize(done));
+    if (!d_status) {
+        void *p = nullptr;
+        FG21_CUDA_TRY(cudaMalloc(&p, 256));
+        d_status = (unsigned *)p;
+        d_invalid = (unsigned long long *)((char *)p + 16);
+    }
+    if (dev_need > dev_bytes) {
+        if (dev) cudaFree(dev);
+        dev = nullptr;
+        dev_bytes = 0;
+        size_t want = std::max(dev_need, dev_need + dev_need / 4);
+        if (cudaMalloc((void **)&dev, want) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(FG21_E_NOMEM, "cudaMalloc of %zu workspace bytes failed", want);
+        }
+        dev_bytes = want;
+    }
+    if (arena_need > arena_bytes) {
+        if (arena) cudaFree(arena);
+        arena = nullptr;
+        arena_bytes = 0;
+        size_t want = std::max(arena_need, arena_need + arena_need / 4);
+        if (cudaMalloc((void **)&arena, want) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(FG21_E_NOMEM, "cudaMalloc of %zu operand-tile bytes failed", want);
+        }
+        arena_bytes = want;
+    }
+    if (pinned_need > pinned_bytes) {
+        if (pinned) cudaFreeHost(pinned);
+        pinned = nullptr;
+        pinned_bytes = 0;
+        size_t want = std::max(pinned_need, (size_t)4096);
+        if (cudaMallocHost((void **)&pinned, want) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(FG21_E_NOMEM, "cudaMallocHost of %zu bytes failed", want);
+        }
+        pinned_bytes = want;
+    }
+    if (n_reqs > reqs_cap) {
+        if (d_reqs) cudaFree(d_reqs);
+        d_reqs = nullptr;
+        reqs_cap = 0;
+        int want = std::max(n_reqs, 8);
+        FG21_CUDA_TRY(cudaMalloc((void **)&d_reqs, sizeof(ReqDesc) * want));
+        reqs_cap = want;
+    }
+    return FG21_OK;
+}
+
+cudaEvent_t *Workspace::timing_slot() {
+    if (!timing) return nullptr;
+    if (tev.empty()) {
+        tev.assign((size_t)TIMING_CAP * 4, nullptr);
+        for (auto &e : tev)
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                cudaGetLastError();
+                timing = false;
+                return nullptr;
+            }
+    }
+    cudaEvent_t *slot = &tev[(size_t)(tcalls % TIMING_CAP) * 4];
+    ++tcalls;
+    return slot;
+}
+
+void Workspace::release() {
+    if (done) cudaEventSynchronize(done);
+    if (dev) cudaFree(dev);
+    if (arena) cudaFree(arena);
+    if (pinned) cudaFreeHost(pinned);
+    if (d_reqs) cudaFree(d_reqs);
+    if (d_status) cudaFree(d_status);
+    if (done) cudaEventDestroy(done);
+    for (auto &e : tev)
+        if (e) cudaEventDestroy(e);
+    tev.clear();
+    tcalls = 0;
+    dev = arena = pinned = nullptr;
+    d_reqs = nullptr;
+    d_status = nullptr;
+    d_invalid = nullptr;
+    done = nullptr;
+    dev_bytes = arena_bytes = pinned_bytes = 0;
+    reqs_cap = 0;
+}
+
+// --------------------------------------------------------------- planning
+static int g_cpg_override() {
+    static int v = [] {
+        const char *e = std::getenv("FG21_CHANNELS_PER_GROUP");
+        return e ? std::atoi(e) : 0;
+    }();
+    return v;
+}
+
+// Channels per work item: minimise (waves of items over the SMs) x (channels
+// per item + a per-item overhead of about one channel).
+static int choose_channels_per_group(int64_t total_tiles, int F, int num_sms) {
+    if (g_cpg_override() > 0) return std::min(F, g_cpg_override());
+    double best = 1e300;
+    int best_cpg = F;
+    for (int cpg = 1; cpg <= F; ++cpg) {
+        int G = (F + cpg - 1) / cpg;
+        double waves = std::ceil((double)total_tiles * G / num_sms);
+        double cost = waves * (cpg + 1.0);
+        if (cost < best - 1e-9) {
+            best = cost;
+            best_cpg = cpg;
+        }
+    }
+    return best_cpg;
+}
+
+void plan_request(ReqDesc &r, int precision, int num_sms, int64_t total_tiles) {
+    r.Kp = round16(r.N + 2);
+    // one operand tile (2 x Kp x Tc_pad x 2 bytes) stays <= 32 KB so that four
+    // pipeline stages fit in shared memory next to the weight stages
+    const int tc_cap = r.Kp <= 32 ? TC_MAX : TC_MAX / 2;
+    r.n_tchunks = (r.T + tc_cap - 1) / tc_cap;
+    r.Tc = (r.T + r.n_tchunks - 1) / r.n_tchunks;
+    r.Tc_pad = round16(r.Tc);
+    r.n_tiles = (int)((r.P + TILE_M - 1) / TILE_M);
+    r.n_stat_blocks = (int)((r.P + STAT_BLOCK - 1) / STAT_BLOCK);
+    int cpg = choose_channels_per_group(total_tiles, r.F, num_sms);
+    r.G = (r.F + cpg - 1) / cpg;
+    r.ch_per_group = (r.F + r.G - 1) / r.G;
+    r.tile_rows = (int64_t)r.Kp * r.Tc_pad / 32;   // 2 splits x Kp x Tc_pad x 2 bytes / 128
+    (void)precision;
+}
+
+ReqLayout request_layout(const ReqDesc &r, int precision) {
+    ReqLayout L{};
+    const bool tc = precision == FG21_PREC_FP16X3 || precision == FG21_PREC_BF16X3;
+    L.stat_part = align256(sizeof(double) * (size_t)r.n_stat_blocks * (3 * r.N + 2));
+    L.beta_bar = align256(sizeof(double) * r.N);
+    L.req_stats = align256(sizeof(double) * 4);
+    L.nL32 = align256(sizeof(float) * r.F);
+    L.nu32 = align256(sizeof(float) * r.F);
+    L.scaleB = align256(sizeof(int) * (size_t)r.F * r.n_tchunks);
+    L.scaleW = align256(sizeof(int));
+    const bool delta = precision == FG21_PREC_FP32_DELTA;
+    L.Bp32 = delta ? align256(sizeof(float) * (size_t)r.N * r.F * r.T) : 0;
+    L.dref32 = delta ? align256(sizeof(float) * (size_t)r.F * r.T) : 0;
+    L.partials = align256(sizeof(float2) * (size_t)r.P * r.G);
+    L.tiles = tc ? (size_t)r.F * r.n_tchunks * r.tile_rows * 128 : 0;
+    return L;
+}
+
+int enqueue_requests(Workspace &ws, std::vector<ReqDesc> &reqs, int precision, cudaStream_t stream) {
+    const int n = (int)reqs.size();
+    if (n == 0) return FG21_OK;
+    const bool tc = precision == FG21_PREC_FP16X3 || precision == FG21_PREC_BF16X3;
+    int dev = 0;
+    FG21_CUDA_TRY(cudaGetDevice(&dev));
+    const int num_sms = num_sms_of(dev);
+    size_t dev_need = 0, arena_need = 0;
+    std::vector<ReqLayout> lay(n);
+    for (int k = 0; k < n; ++k) {
+        // each request is planned as if alone, so its work split (and with it
+        // every rounding) does not depend on what it is batched with
+        plan_request(reqs[k], precision, num_sms, (reqs[k].P + TILE_M - 1) / TILE_M);
+        lay[k] = request_layout(reqs[k], precision);
+        arena_need += lay[k].tiles;
+        dev_need += lay[k].total() - lay[k].tiles;
+    }
+    int rc = ws.ensure(dev_need, arena_need, sizeof(ReqDesc) * n, n);
+    if (rc) return rc;
+    char *p = ws.dev;
+    int64_t item = 0, row = 0, pts = 0;
+    int kp_max = 16, tc_max = 16, max_blocks = 1, max_fchunks = 1;
+    for (int k = 0; k < n; ++k) {
+        ReqDesc &r = reqs[k];
+        const ReqLayout &L = lay[k];
+        r.stat_part = (double *)p; p += L.stat_part;
+        r.beta_bar = (double *)p; p += L.beta_bar;
+        r.req_stats = (double *)p; p += L.req_stats;
+        r.nL32 = (float *)p; p += L.nL32;
+        r.nu32 = (float *)p; p += L.nu32;
+        r.scaleB = (int *)p; p += L.scaleB;
+        r.scaleW = (int *)p; p += L.scaleW;
+        r.Bp32 = L.Bp32 ? (float *)p : nullptr; p += L.Bp32;
+        r.dref32 = L.dref32 ? (float *)p : nullptr; p += L.dref32;
+        r.partials = (float2 *)p; p += L.partials;
+        r.item_begin = item;
+        item += (int64_t)r.n_tiles * r.G;
+        r.pt_begin = pts;
+        pts += r.P;
+        r.tile_row0 = row;
+        r.tiles = ws.arena + row * 128;
+        row += (int64_t)(L.tiles / 128);
+        r.status = ws.d_status;
+        r.invalid = ws.d_invalid;
+        kp_max = std::max(kp_max, r.Kp);
+        tc_max = std::max(tc_max, r.Tc_pad);
+        max_blocks = std::max(max_blocks, r.n_stat_blocks);
+        max_fchunks = std::max(max_fchunks, r.F * r.n_tchunks);
+    }
+    if (tc && kp_max > KP_MAX)
+        return set_error(FG21_E_RANGE, "N = %d regions exceeds the tensor-core limit %d", kp_max - 2,
+                         FG21_MAX_REGIONS_TC);
+    std::memcpy(ws.pinned, reqs.data(), sizeof(ReqDesc) * n);
+    FG21_CUDA_TRY(cudaMemsetAsync(ws.d_status, 0, 32, stream));
+    FG21_CUDA_TRY(cudaMemcpyAsync(ws.d_reqs, ws.pinned, sizeof(ReqDesc) * n, cudaMemcpyHostToDevice, stream));
+    cudaEvent_t *ev = ws.timing_slot();
+    if (ev) FG21_CUDA_TRY(cudaEventRecord(ev[0], stream));
+    FG21_CUDA_TRY(launch_prep(reqs.data(), ws.d_reqs, n, precision, max_blocks, max_fchunks, stream));
+    if (ev) FG21_CUDA_TRY(cudaEventRecord(ev[1], stream));
+    if (tc) {
+        TcLaunch L;
+        L.d_reqs = ws.d_reqs;
+        L.n_reqs = n;
+        L.n_items = item;
+        L.kp_max = kp_max;
+        L.tc_pad_max = tc_max;
+        L.precision = precision;
+        L.arena = ws.arena;
+        L.arena_rows = row;
+        L.status = ws.d_status;
+        cudaError_t e = launch_tc(L, num_sms, stream);
+        if (e != cudaSuccess) return cuda_error(e, "tensor-core likelihood launch");
+    } else {
+        FG21_CUDA_TRY(launch_simt(reqs.data(), ws.d_reqs, n, precision, stream));
+    }
+    if (ev) FG21_CUDA_TRY(cudaEventRecord(ev[2], stream));
+    FG21_CUDA_TRY(launch_reduce(reqs.data(), ws.d_reqs, n, stream));
+    if (ev) FG21_CUDA_TRY(cudaEventRecord(ev[3], stream));
+    FG21_CUDA_TRY(cudaEventRecord(ws.done, stream));
+    return FG21_OK;
+}
+
+// ------------------------------------------------------------------ model
+int model_upload(fg21_model *m) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(FG21_E_CUDA, "no usable CUDA device");
+    }
+    m->device = dev;
+    const size_t NFT = (size_t)m->N * m->F * m->T, FT = (size_t)m->F * m->T;
+    std::vector<double> L(m->F);
+    m->Lmax = 0.0;
+    for (int f = 0; f < m->F; ++f) {
+        L[f] = std::log(m->nu[f] / m->nu0);
+        m->Lmax = std::max(m->Lmax, std::fabs(L[f]));
+    }
+    std::vector<float> A32(NFT), B32(FT), zero32(FT, 0.0f);
+    for (size_t k = 0; k < NFT; ++k) A32[k] = (float)m->A[k];
+    for (size_t k = 0; k < FT; ++k) B32[k] = (float)m->B[k];
+    struct Item { void **dst; const void *src; size_t bytes; };
+    std::vector<double> zero(FT, 0.0);
+    Item items[] = {
+        {(void **)&m->d_A, m->A.data(), sizeof(double) * NFT},
+        {(void **)&m->d_B, m->B.data(), sizeof(double) * FT},
+        {(void **)&m->d_data, zero.data(), sizeof(double) * FT},
+        {(void **)&m->d_L, L.data(), sizeof(double) * m->F},
+        {(void **)&m->d_nu, m->nu.data(), sizeof(double) * m->F},
+        {(void **)&m->d_A32, A32.data(), sizeof(float) * NFT},
+        {(void **)&m->d_B32, B32.data(), sizeof(float) * FT},
+        {(void **)&m->d_data32, zero32.data(), sizeof(float) * FT},
+    };
+    m->resident_bytes = 0;
+    for (auto &it : items) {
+        if (cudaMalloc(it.dst, it.bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(FG21_E_NOMEM, "cudaMalloc of %zu model bytes failed", it.bytes);
+        }
+        FG21_CUDA_TRY(cudaMemcpy(*it.dst, it.src, it.bytes, cudaMemcpyHostToDevice));
+        m->resident_bytes += it.bytes;
+    }
+    return FG21_OK;
+}
+
+ReqDesc model_request(const fg21_model *m, const double *d_params, int64_t P, double *d_logL) {
+    ReqDesc r;
+    std::memset(&r, 0, sizeof r);
+    r.A = m->d_A;
+    r.B = m->d_B;
+    r.data = m->d_data;
+    r.L = m->d_L;
+    r.nu = m->d_nu;
+    r.A32 = m->d_A32;
+    r.B32 = m->d_B32;
+    r.data32 = m->d_data32;
+    r.params = d_params;
+    r.logL = d_logL;
+    r.t_cmb = m->t_cmb;
+    r.Lmax = m->Lmax;
+    r.P = P;
+    r.N = m->N;
+    r.F = m->F;
+    r.T = m->T;
+    return r;
+}
+
+static int check_precision(const fg21_model *m, int precision) {
+    if (precision < 0 || precision > 3) return set_error(FG21_E_ARG, "unknown precision %d", precision);
+    if ((precision == FG21_PREC_FP16X3 || precision == FG21_PREC_BF16X3) && m->N > FG21_MAX_REGIONS_TC)
+        return set_error(FG21_E_RANGE, "N = %d exceeds the tensor-core limit %d (use FG21_PREC_FP32_DELTA)",
+                         m->N, FG21_MAX_REGIONS_TC);
+    return FG21_OK;
+}
+
+static int device_guard(const fg21_model *m) {
+    int cur = -1;
+    FG21_CUDA_TRY(cudaGetDevice(&cur));
+    if (cur != m->device) FG21_CUDA_TRY(cudaSetDevice(m->device));
+    return FG21_OK;
+}
+
+// Host-buffer evaluation: params are staged through the model's pinned I/O
+// buffers, evaluated on the device, and logL copied back.
+static int run_host(fg21_model *m, const double *params, int64_t P, double *logL, int precision,
+                    cudaStream_t stream) {
+    const size_t pbytes = sizeof(double) * (size_t)P * (m->N + 4), lbytes = sizeof(double) * (size_t)P;
+    const size_t need = align256(pbytes) + align256(lbytes) + 64;
+    if (m->io_cap < need) {
+        if (m->ws.done) FG21_CUDA_TRY(cudaEventSynchronize(m->ws.done));
+        if (m->io_d) cudaFree(m->io_d);
+        if (m->io_h) cudaFreeHost(m->io_h);
+        m->io_d = nullptr;
+        m->io_h = nullptr;
+        m->io_cap = 0;
+        if (cudaMalloc((void **)&m->io_d, need) != cudaSuccess ||
+            cudaMallocHost((void **)&m->io_h, need) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(FG21_E_NOMEM, "I/O buffers of %zu bytes", need);
+        }
+        m->io_cap = need;
+    }
+    struct { double *d_params, *d_logL; char *h; } iob{(double *)m->io_d, (double *)(m->io_d + align256(pbytes)), m->io_h};
+    auto *io = &iob;
+    std::memcpy(io->h, params, pbytes);
+    FG21_CUDA_TRY(cudaMemcpyAsync(io->d_params, io->h, pbytes, cudaMemcpyHostToDevice, stream));
+    std::vector<ReqDesc> reqs{model_request(m, io->d_params, P, io->d_logL)};
+    int rc = enqueue_requests(m->ws, reqs, precision, stream);
+    if (rc) return rc;
+    char *h_log = io->h + align256(pbytes);
+    FG21_CUDA_TRY(cudaMemcpyAsync(h_log, io->d_logL, lbytes, cudaMemcpyDeviceToHost, stream));
+    FG21_CUDA_TRY(cudaMemcpyAsync(h_log + align256(lbytes), m->ws.d_status, 32, cudaMemcpyDeviceToHost, stream));
+    FG21_CUDA_TRY(cudaStreamSynchronize(stream));
+    std::memcpy(logL, h_log, lbytes);
+    const unsigned *st = (const unsigned *)(h_log + align256(lbytes));
+    unsigned long long inv = 0;
+    std::memcpy(&inv, st + 4, sizeof inv);
+    set_invalid_count((int64_t)inv);
+    if (st[0]) return set_error(FG21_E_DEVICE, "likelihood kernel reported status 0x%x", st[0]);
+    return FG21_OK;
+}
+
+}  // namespace fg21
+
+using namespace fg21;
+
+extern "C" {
+
+int fg21_model_destroy(fg21_model *m) {
+    if (!m) return FG21_OK;
+    {
+        std::lock_guard<std::mutex> lk(m->mu);
+        m->ws.release();
+        void *ptrs[] = {m->d_A, m->d_B, m->d_data, m->d_L, m->d_nu, m->d_A32, m->d_B32, m->d_data32, m->io_d};
+        for (void *p : ptrs)
+            if (p) cudaFree(p);
+        if (m->io_h) cudaFreeHost(m->io_h);
+    }
+    delete m;
+    return FG21_OK;
+}
+
+int fg21_model_set_data(fg21_model *m, const double *data) {
+    if (!m || !data) return set_error(FG21_E_ARG, "NULL model/data");
+    std::lock_guard<std::mutex> lk(m->mu);
+    int rc = device_guard(m);
+    if (rc) return rc;
+    const size_t FT = (size_t)m->F * m->T;
+    std::vector<float> d32(FT);
+    for (size_t k = 0; k < FT; ++k) {
+        if (!std::isfinite(data[k])) return set_error(FG21_E_ARG, "non-finite data[%zu]", k);
+        d32[k] = (float)data[k];
+    }
+    if (m->ws.done) FG21_CUDA_TRY(cudaEventSynchronize(m->ws.done));
+    FG21_CUDA_TRY(cudaMemcpy(m->d_data, data, sizeof(double) * FT, cudaMemcpyHostToDevice));
+    FG21_CUDA_TRY(cudaMemcpy(m->d_data32, d32.data(), sizeof(float) * FT, cudaMemcpyHostToDevice));
+    return FG21_OK;
+}
+
+int fg21_model_get_arrays(const fg21_model *m, double *A, double *B) {
+    if (!m) return set_error(FG21_E_ARG, "NULL model");
+    if (A) std::memcpy(A, m->A.data(), sizeof(double) * m->A.size());
+    if (B) std::memcpy(B, m->B.data(), sizeof(double) * m->B.size());
+    return FG21_OK;
+}
+
+int fg21_model_info(const fg21_model *m, int32_t *N, int32_t *F, int32_t *T, int32_t *n_empty,
+                    size_t *device_bytes) {
+    if (!m) return set_error(FG21_E_ARG, "NULL model");
+    if (N) *N = m->N;
+    if (F) *F = m->F;
+    if (T) *T = m->T;
+    if (n_empty) *n_empty = m->n_empty;
+    if (device_bytes) *device_bytes = m->resident_bytes + m->ws.bytes();
+    return FG21_OK;
+}
+
+int fg21_loglike_batch(fg21_model *m, const double *params, int64_t P, double *logL, int precision,
+                       void *stream) {
+    if (!m) return set_error(FG21_E_ARG, "NULL model");
+    if (P < 0 || (P > 0 && (!params || !logL))) return set_error(FG21_E_ARG, "bad params/logL/P");
+    int rc = check_precision(m, precision);
+    if (rc) return rc;
+    set_invalid_count(0);
+    if (P == 0) return FG21_OK;
+    std::lock_guard<std::mutex> lk(m->mu);
+    rc = device_guard(m);
+    if (rc) return rc;
+    return run_host(m, params, P, logL, precision, (cudaStream_t)stream);
+}
+
+int fg21_loglike_batch_device(fg21_model *m, const double *d_params, int64_t P, double *d_logL,
+                              int precision, void *stream) {
+    if (!m) return set_error(FG21_E_ARG, "NULL model");
+    if (P < 0 || (P > 0 && (!d_params || !d_logL))) return set_error(FG21_E_ARG, "bad params/logL/P");
+    int rc = check_precision(m, precision);
+    if (rc) return rc;
+    if (P == 0) return FG21_OK;
+    std::lock_guard<std::mutex> lk(m->mu);
+    rc = device_guard(m);
+    if (rc) return rc;
+    std::vector<ReqDesc> reqs{model_request(m, d_params, P, d_logL)};
+    return enqueue_requests(m->ws, reqs, precision, (cudaStream_t)stream);
+}
+
+int fg21_model_sync_status(fg21_model *m, void *stream, int64_t *invalid_count) {
+    if (!m) return set_error(FG21_E_ARG, "NULL model");
+    std::lock_guard<std::mutex> lk(m->mu);
+    FG21_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    if (!m->ws.d_status) {
+        if (invalid_count) *invalid_count = 0;
+        return FG21_OK;
+    }
+    unsigned st[8];
+    FG21_CUDA_TRY(cudaMemcpy(st, m->ws.d_status, 32, cudaMemcpyDeviceToHost));
+    unsigned long long inv = 0;
+    std::memcpy(&inv, st + 4, sizeof inv);
+    if (invalid_count) *invalid_count = (int64_t)inv;
+    set_invalid_count((int64_t)inv);
+    if (st[0]) return set_error(FG21_E_DEVICE, "likelihood kernel reported status 0x%x", st[0]);
+    return FG21_OK;
+}
+
+int fg21_model_timing(fg21_model *m, int enable) {
+    if (!m) return set_error(FG21_E_ARG, "NULL model");
+    std::lock_guard<std::mutex> lk(m->mu);
+    if (m->ws.done) FG21_CUDA_TRY(cudaEventSynchronize(m->ws.done));
+    m->ws.timing = enable != 0;
+    m->ws.tcalls = 0;
+    return FG21_OK;
+}
+
+int fg21_model_timing_totals(fg21_model *m, int64_t *calls, double *prep_ms, double *main_ms, double *reduce_ms) {
+    if (!m) return set_error(FG21_E_ARG, "NULL model");
+    std::lock_guard<std::mutex> lk(m->mu);
+    Workspace &ws = m->ws;
+    if (!ws.timing || ws.tcalls == 0) return set_error(FG21_E_STATE, "timing not enabled or no call recorded");
+    const int64_t n = ws.tcalls < Workspace::TIMING_CAP ? ws.tcalls : Workspace::TIMING_CAP;
+    const int64_t last = (ws.tcalls - 1) % Workspace::TIMING_CAP;
+    FG21_CUDA_TRY(cudaEventSynchronize(ws.tev[(size_t)last * 4 + 3]));
+    double a = 0, b = 0, c = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        cudaEvent_t *e = &ws.tev[(size_t)k * 4];
+        float x = 0, y = 0, z = 0;
+        FG21_CUDA_TRY(cudaEventElapsedTime(&x, e[0], e[1]));
+        FG21_CUDA_TRY(cudaEventElapsedTime(&y, e[1], e[2]));
+        FG21_CUDA_TRY(cudaEventElapsedTime(&z, e[2], e[3]));
+        a += x;
+        b += y;
+        c += z;
+    }
+    if (calls) *calls = n;
+    if (prep_ms) *prep_ms = a;
+    if (main_ms) *main_ms = b;
+    if (reduce_ms) *reduce_ms = c;
+    return FG21_OK;
+}
+
+int fg21_model_eval(fg21_model *m, const double *params, int64_t P, double *T_model, int precision,
+                    void *stream) {
+    if (!m || !params || !T_model || P <= 0) return set_error(FG21_E_ARG, "bad model_eval arguments");
+    int rc = check_precision(m, precision);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(m->mu);
+    rc = device_guard(m);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t pbytes = sizeof(double) * (size_t)P * (m->N + 4);
+    const size_t obytes = sizeof(double) * (size_t)P * m->F * m->T;
+    double *d_params = nullptr, *d_out = nullptr, *d_logL = nullptr;
+    if (cudaMalloc((void **)&d_params, pbytes) != cudaSuccess || cudaMalloc((void **)&d_out, obytes) != cudaSuccess ||
+        cudaMalloc((void **)&d_logL, sizeof(double) * P) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(d_params);
+        cudaFree(d_out);
+        return set_error(FG21_E_NOMEM, "model_eval buffers");
+    }
+    int out = FG21_OK;
+    do {
+        if (cudaMemcpyAsync(d_params, params, pbytes, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+            out = cuda_error(cudaGetLastError(), "model_eval H2D");
+            break;
+        }
+        std::vector<ReqDesc> reqs{model_request(m, d_params, P, d_logL)};
+        out = enqueue_requests(m->ws, reqs, precision, s);
+        if (out) break;
+        cudaError_t e = launch_model_eval(&reqs[0], m->ws.d_reqs, precision, d_out, s);
+        if (e != cudaSuccess) {
+            out = cuda_error(e, "model_eval launch");
+            break;
+        }
+        if (cudaMemcpyAsync(T_model, d_out, obytes, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            out = cuda_error(cudaGetLastError(), "model_eval D2H");
+            break;
+        }
+    } while (0);
+    cudaStreamSynchronize(s);
+    cudaFree(d_params);
+    cudaFree(d_out);
+    cudaFree(d_logL);
+    return out;
+}
+
+int fg21_loglike_multi(fg21_model *const *models, const double *const *params, const int64_t *P,
+                       double *const *logL, int n_models, int precision, void *stream) {
+    if (n_models < 0 || (n_models > 0 && (!models || !params || !P || !logL)))
+        return set_error(FG21_E_ARG, "bad multi arguments");
+    set_invalid_count(0);
+    if (n_models == 0) return FG21_OK;
+    if (precision < 0 || precision > 3) return set_error(FG21_E_ARG, "unknown precision %d", precision);
+    for (int k = 0; k < n_models; ++k) {
+        if (!models[k] || P[k] < 0 || (P[k] > 0 && (!params[k] || !logL[k])))
+            return set_error(FG21_E_ARG, "bad request %d", k);
+        int rc = check_precision(models[k], precision);
+        if (rc) return rc;
+    }
+    static std::mutex mu;
+    static Workspace ws;
+    static double *d_io = nullptr;
+    static char *h_io = nullptr;
+    static size_t io_cap = 0;
+    std::lock_guard<std::mutex> lk(mu);
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<size_t> poff(n_models), loff(n_models);
+    size_t total = 0;
+    for (int k = 0; k < n_models; ++k) {
+        poff[k] = total;
+        total += align256(sizeof(double) * (size_t)P[k] * (models[k]->N + 4));
+        loff[k] = total;
+        total += align256(sizeof(double) * (size_t)P[k]);
+    }
+    total += 64;
+    if (ws.done) FG21_CUDA_TRY(cudaEventSynchronize(ws.done));
+    if (total > io_cap) {
+        if (d_io) cudaFree(d_io);
+        if (h_io) cudaFreeHost(h_io);
+        d_io = nullptr;
+        h_io = nullptr;
+        io_cap = 0;
+        if (cudaMalloc((void **)&d_io, total) != cudaSuccess || cudaMallocHost((void **)&h_io, total) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(FG21_E_NOMEM, "multi I/O buffers");
+        }
+        io_cap = total;
+    }
+    std::vector<ReqDesc> reqs;
+    std::vector<int> map;
+    for (int k = 0; k < n_models; ++k) {
+        if (P[k] == 0) continue;
+        const size_t pb = sizeof(double) * (size_t)P[k] * (models[k]->N + 4);
+        std::memcpy(h_io + poff[k], params[k], pb);
+        reqs.push_back(model_request(models[k], (const double *)((char *)d_io + poff[k]), P[k],
+                                     (double *)((char *)d_io + loff[k])));
+        map.push_back(k);
+    }
+    if (reqs.empty()) return FG21_OK;
+    FG21_CUDA_TRY(cudaMemcpyAsync(d_io, h_io, loff[n_models - 1] + align256(sizeof(double) * P[n_models - 1]),
+                                  cudaMemcpyHostToDevice, s));
+    int rc = enqueue_requests(ws, reqs, precision, s);
+    if (rc) return rc;
+    FG21_CUDA_TRY(cudaMemcpyAsync(h_io, d_io, total - 64, cudaMemcpyDeviceToHost, s));
+    unsigned st[8];
+    FG21_CUDA_TRY(cudaMemcpyAsync(st, ws.d_status, 32, cudaMemcpyDeviceToHost, s));
+    FG21_CUDA_TRY(cudaStreamSynchronize(s));
+    for (size_t j = 0; j < map.size(); ++j) {
+        int k = map[j];
+        std::memcpy(logL[k], h_io + loff[k], sizeof(double) * P[k]);
+    }
+    unsigned long long inv = 0;
+    std::memcpy(&inv, st + 4, sizeof inv);
+    set_invalid_count((int64_t)inv);
+    if (st[0]) return set_error(FG21_E_DEVICE, "likelihood kernel reported status 0x%x", st[0]);
+    return FG21_OK;
+}
+
+}  // extern "C"

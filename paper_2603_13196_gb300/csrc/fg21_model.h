@@ -1,0 +1,69 @@
+// Model handle and device workspace of libfg21 (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <vector>
+
+#include "fg21_internal.h"
+
+namespace fg21 {
+
+// Device scratch for one launch (request workspaces, operand-tile arena, the
+// request descriptors, status word) plus pinned host staging.  Grow-only.
+struct Workspace {
+    int device = -1;
+    char *dev = nullptr;
+    size_t dev_bytes = 0;
+    char *arena = nullptr;          // operand tiles, addressed by the TMA tensor map
+    size_t arena_bytes = 0;
+    char *pinned = nullptr;         // host staging (params, logL, descriptors)
+    size_t pinned_bytes = 0;
+    ReqDesc *d_reqs = nullptr;
+    int reqs_cap = 0;
+    unsigned *d_status = nullptr;   // [0] status word, [2..3] invalid counter (64-bit)
+    unsigned long long *d_invalid = nullptr;
+    cudaEvent_t done = nullptr;     // recorded after the last launch of a call
+    bool timing = false;            // record events around prep / main / reduce of every call
+    static constexpr int TIMING_CAP = 8192;
+    std::vector<cudaEvent_t> tev;   // [TIMING_CAP][4], created on first use
+    int64_t tcalls = 0;             // calls recorded since timing was enabled
+    cudaEvent_t *timing_slot();     // the 4 events of the next call (nullptr if timing off)
+
+    int ensure(size_t dev_need, size_t arena_need, size_t pinned_need, int n_reqs);
+    void release();
+    size_t bytes() const { return dev_bytes + arena_bytes; }
+};
+
+// Launch a set of requests whose params/logL device pointers are filled in.
+// Plans shapes, carves request workspaces out of `ws`, and enqueues prep,
+// main and reduce kernels on `stream`.  The status word and invalid counter
+// are cleared first.  Returns FG21_OK or an error code.
+int enqueue_requests(Workspace &ws, std::vector<ReqDesc> &reqs, int precision, cudaStream_t stream);
+
+int num_sms_of(int device);
+
+}  // namespace fg21
+
+struct fg21_model {
+    int N = 0, F = 0, T = 0;
+    int64_t npix = 0;
+    int n_empty = 0;
+    double nu0 = 0, t_cmb = 0, Lmax = 0;
+    std::vector<double> nu, edges, A, B;
+    int device = 0;
+    double *d_A = nullptr, *d_B = nullptr, *d_data = nullptr, *d_L = nullptr, *d_nu = nullptr;
+    float *d_A32 = nullptr, *d_B32 = nullptr, *d_data32 = nullptr;
+    size_t resident_bytes = 0;      // A, B, data, tables (not the workspace)
+    char *io_d = nullptr, *io_h = nullptr;   // params/logL staging of the host-buffer calls
+    size_t io_cap = 0;
+    fg21::Workspace ws;
+    std::mutex mu;
+};
+
+namespace fg21 {
+int model_upload(fg21_model *m);
+// A request descriptor of model m (params/logL device pointers left for the caller).
+ReqDesc model_request(const fg21_model *m, const double *d_params, int64_t P, double *d_logL);
+}  // namespace fg21

@@ -1,0 +1,635 @@
+// Tensor-core (tcgen05) likelihood kernel of libfg21 for sm_103a.
+//
+// Per channel f the reference-subtracted residual of every point is one small
+// GEMM (Sec. 2.2 eq. fast_forward_model, rearranged about a per-request
+// reference; see fg21_kernels.cu):
+//
+//   acc[p, t] = sum_k W[p, k] Bop[k, t],  k = 0..N+1
+//     W[p, i]   = 2^sW expm1(-(beta_{p,i} - bbar_i) L_f)   (i < N)
+//     W[p, N]   = 2^sW T21(nu_f; theta_p)                    (eq. t21model)
+//     W[p, N+1] = -2^sW
+//     Bop[i, t] = 2^sB wbar_{i,f} A[i,f,t],  Bop[N, t] = 2^sB,  Bop[N+1, t] = 2^sB dref[f,t]
+//   so acc = -2^(sW+sB) (D - M)  and  chi2_p += sum_t acc^2 2^-2(sW+sB)   (eq. likelihood)
+//
+// The product runs as split precision on the tensor cores: both operands are
+// split into hi + mid 16-bit values (FP16 or BF16) and three MMAs
+// (hi*hi + hi*mid + mid*hi) accumulate in FP32 in tensor memory.
+//
+// One persistent CTA per SM walks a static list of work items (request, tile
+// of 128 points, group of channels).  Warp roles:
+//   warps 0-3  weight generators: thread m owns point m of the tile; computes
+//              its W row per channel in registers and stores it (hi and mid)
+//              to shared memory in the K-major core-matrix layout;
+//   warps 4-7  epilogue: tcgen05.ld of the accumulator rows (warp w reads lanes
+//              32(w%4)..+31), square-and-sum over t, unscale, compensated sum
+//              over channels, one partial chi2 per (point, item);
+//   warp 8     TMA producer: cp.async.bulk.tensor loads of the channel's
+//              operand tile Bop (prepared per request in global memory);
+//   warp 9     MMA issuer (one elected thread) and tensor-memory owner.
+// Pipelines: 4 operand-tile stages, 2 weight stages, 2 accumulator stages, all
+// handed over with mbarriers.  Every wait is bounded (a few seconds of
+// %globaltimer); on expiry the kernel sets a status bit, the roles stop, the
+// in-flight copies and MMAs are drained with bounded waits and tensor memory is
+// released before the CTA exits.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+
+#include "fg21_internal.h"
+
+namespace fg21 {
+
+namespace {
+
+constexpr int NUM_THREADS = 320;
+constexpr int NB_STAGES = 4;     // operand-tile (TMA) stages
+constexpr int NW_STAGES = 2;     // weight stages
+constexpr int NACC = 2;          // accumulator stages in tensor memory
+constexpr int BOX_ROWS = 8;      // rows of 128 bytes per TMA box
+constexpr uint64_t WAIT_LIMIT_NS = 4000000000ull;
+
+struct __align__(8) Barriers {
+    uint64_t b_full[NB_STAGES], b_empty[NB_STAGES];
+    uint64_t w_full[NW_STAGES], w_empty[NW_STAGES];
+    uint64_t acc_full[NACC], acc_empty[NACC];
+    uint64_t drain;
+    uint32_t tmem_base;
+    volatile uint32_t abort_flag;
+};
+
+// ------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: true when the phase completed; false on timeout or abort.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, Barriers *S, unsigned *status,
+                                          unsigned code) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (S->abort_flag) return false;
+        if (globaltimer() - t0 > WAIT_LIMIT_NS) {
+            atomicOr(status, code);
+            S->abort_flag = 1;
+            return false;
+        }
+    }
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+// Shared-memory matrix descriptor, K-major, no swizzle: core matrices of 8 rows
+// x 16 bytes; lbo = byte distance between the two 8-element K chunks of an MMA
+// step, sbo = byte distance between consecutive 8-row groups.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;   // descriptor version of tcgen05
+    return d;                 // base offset 0, relative LBO, swizzle none
+}
+// Instruction descriptor of kind::f16: D = F32, A = B = F16 (0) or BF16 (1),
+// both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__device__ __forceinline__ uint32_t instr_desc(int M, int N, bool bf16) {
+    const uint32_t fmt = bf16 ? 1u : 0u;
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void kahan_add_dev(float &s, float &c, float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+// ---------------------------------------------------------- work items
+struct Item {
+    int req, tile, g, f0, f1;
+};
+__device__ __forceinline__ int find_req(const ReqDesc *__restrict__ reqs, int n, int64_t item) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (reqs[mid].item_begin <= item) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+__device__ __forceinline__ Item decode_item(const ReqDesc *__restrict__ reqs, int n, int64_t item) {
+    Item it;
+    it.req = find_req(reqs, n, item);
+    const ReqDesc &r = reqs[it.req];
+    const int64_t lid = item - r.item_begin;
+    it.tile = (int)(lid / r.G);
+    it.g = (int)(lid % r.G);
+    it.f0 = it.g * r.ch_per_group;
+    it.f1 = min(r.F, it.f0 + r.ch_per_group);
+    return it;
+}
+
+// ----------------------------------------------------- weight generation
+// expm1 by its Taylor series x (1 + x/2! + ... + x^(D-1)/D!), scaled by 2^sW
+// through the coefficients c[j] = 2^sW / j!.  Relative truncation error
+// |x|^D / (D+1)!: D = 3 for |x| <= 0.01, 5 for |x| <= 0.1, 8 for |x| <= 0.55.
+template <int D>
+__device__ __forceinline__ float em1_series(float x, const float *c) {
+    float p = c[D];
+#pragma unroll
+    for (int j = D - 1; j >= 1; --j) p = fmaf(p, x, c[j]);
+    return p * x;
+}
+// Larger |x|: Cody-Waite reduction x = k ln2 + r (ln2 split into a 12-bit-short
+// head and a tail), expm1(r) by the degree-7 series (|r| <= ln2/2), then
+// 2^sW (e^x - 1) = 2^(k+sW) expm1(r) + 2^sW (2^k - 1).
+__device__ __forceinline__ float em1_reduced(float x, const float *cu, float sW) {
+    const float k = rintf(x * 1.4426950408889634f);
+    float r = fmaf(-k, 0.693115234375f, x);
+    r = fmaf(-k, 3.194618329871446e-05f, r);
+    const float p = em1_series<7>(r, cu);
+    const int ki = max(-100, min(100, (int)k));
+    const float two_k = ldexpf(1.0f, ki);
+    return fmaf(p, two_k * sW, (two_k - 1.0f) * sW);
+}
+
+template <bool BF16>
+__device__ __forceinline__ uint32_t pack2(float a, float b) {
+    if (BF16) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<uint32_t *>(&h);
+    } else {
+        __half2 h = __floats2half2_rn(a, b);
+        return *reinterpret_cast<uint32_t *>(&h);
+    }
+}
+template <bool BF16>
+__device__ __forceinline__ float2 unpack2(uint32_t u) {
+    if (BF16) {
+        __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162 *>(&u);
+        return __bfloat1622float2(h);
+    } else {
+        __half2 h = *reinterpret_cast<__half2 *>(&u);
+        return __half22float2(h);
+    }
+}
+// split a pair into hi (rounded) and mid (rounded remainder)
+template <bool BF16>
+__device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t &mid) {
+    hi = pack2<BF16>(a, b);
+    const float2 h = unpack2<BF16>(hi);
+    mid = pack2<BF16>(a - h.x, b - h.y);
+}
+
+// One channel's weight row of point m into weight stage `wbuf`:
+// layout [split][kc][m][8 values], split stride KP/8 * 2048 bytes.
+template <int KP, bool BF16, int MODE>   // MODE: 3, 5, 8 = series degree; 0 = reduced
+__device__ __forceinline__ void gen_row(char *wbuf, int m, const float *dlt, int N, float nL, float s21,
+                                        float sW, const float *c, const float *cu) {
+#pragma unroll
+    for (int kc = 0; kc < KP / 8; ++kc) {
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int k = kc * 8 + e;
+            float val = 0.0f;
+            if (k < N) {
+                const float x = dlt[k] * nL;
+                if (MODE == 0) val = em1_reduced(x, cu, sW);
+                else val = em1_series<MODE>(x, c);
+            } else if (k == N) {
+                val = s21;
+            } else if (k == N + 1) {
+                val = -sW;
+            }
+            v[e] = val;
+        }
+        uint4 H, M;
+        split2<BF16>(v[0], v[1], H.x, M.x);
+        split2<BF16>(v[2], v[3], H.y, M.y);
+        split2<BF16>(v[4], v[5], H.z, M.z);
+        split2<BF16>(v[6], v[7], H.w, M.w);
+        *reinterpret_cast<uint4 *>(wbuf + kc * 2048 + m * 16) = H;
+        *reinterpret_cast<uint4 *>(wbuf + (KP / 8) * 2048 + kc * 2048 + m * 16) = M;
+    }
+}
+
+struct Params {
+    const ReqDesc *reqs;
+    int n_reqs;
+    int64_t n_items;
+    int b_stage_bytes;     // bytes of one operand-tile stage
+    int acc_cols;          // tensor-memory columns per accumulator stage
+    uint32_t tmem_cols;    // allocated tensor-memory columns
+    unsigned *status;
+    float *resid;          // validation mode: residuals [P][F][T] of request 0, else null
+};
+
+template <int KP, bool BF16>
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    tc_loglike_kernel(const __grid_constant__ CUtensorMap tmap, const Params prm) {
+    extern __shared__ __align__(1024) char smem_raw[];
+    char *smem = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    constexpr int W_STAGE_BYTES = 2 * KP * 128 * 2;
+    char *w_stages = smem;                                            // NW_STAGES x W_STAGE_BYTES
+    char *b_stages = smem + NW_STAGES * W_STAGE_BYTES;                // NB_STAGES x b_stage_bytes
+    Barriers *S = reinterpret_cast<Barriers *>(b_stages + NB_STAGES * prm.b_stage_bytes);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NB_STAGES; ++s) {
+            mbar_init(&S->b_full[s], 1);
+            mbar_init(&S->b_empty[s], 1);
+        }
+        for (int s = 0; s < NW_STAGES; ++s) {
+            mbar_init(&S->w_full[s], 128);
+            mbar_init(&S->w_empty[s], 1);
+        }
+        for (int s = 0; s < NACC; ++s) {
+            mbar_init(&S->acc_full[s], 1);
+            mbar_init(&S->acc_empty[s], 128);
+        }
+        mbar_init(&S->drain, 1);
+        S->abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 9) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S->tmem_base)),
+                     "r"(prm.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        tc_fence_before();
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = S->tmem_base;
+    const ReqDesc *__restrict__ reqs = prm.reqs;
+
+    if (warp < 4) {
+        // ================================================ weight generators
+        const int m = threadIdx.x;
+        uint32_t w_stage = 0;
+        bool ok = true;
+        for (int64_t item = blockIdx.x; item < prm.n_items && ok; item += gridDim.x) {
+            const Item it = decode_item(reqs, prm.n_reqs, item);
+            const ReqDesc &r = reqs[it.req];
+            const int N = r.N;
+            const int64_t p = (int64_t)it.tile * 128 + m;
+            float dlt[KP];
+#pragma unroll
+            for (int k = 0; k < KP; ++k) dlt[k] = 0.0f;
+            float a21 = 0.0f, nu21 = 0.0f, inv2s2 = 0.0f;
+            if (p < r.P) {
+                const double *th = r.params + p * (N + 4);
+#pragma unroll
+                for (int k = 0; k < KP; ++k)
+                    if (k < N) dlt[k] = (float)(th[k] - r.beta_bar[k]);
+                a21 = (float)th[N];
+                nu21 = (float)th[N + 1];
+                inv2s2 = (float)(1.0 / (2.0 * th[N + 2] * th[N + 2]));
+            }
+            const float sW = ldexpf(1.0f, *r.scaleW);
+            const double xmax = r.req_stats[1];
+            const int mode = xmax <= 0.01 ? 3 : xmax <= 0.1 ? 5 : xmax <= 0.55 ? 8 : 0;
+            float c[10], cu[10];
+            {
+                float fact = 1.0f;
+                c[0] = cu[0] = 0.0f;
+#pragma unroll
+                for (int j = 1; j < 10; ++j) {
+                    fact *= (float)j;
+                    cu[j] = 1.0f / fact;
+                    c[j] = cu[j] * sW;
+                }
+            }
+            for (int f = it.f0; f < it.f1; ++f) {
+                const uint32_t ws = w_stage % NW_STAGES, wph = (w_stage / NW_STAGES) & 1;
+                if (!mbar_wait(&S->w_empty[ws], wph ^ 1, S, prm.status, STATUS_TIMEOUT_GEN)) { ok = false; break; }
+                const float nL = r.nL32[f];
+                const float dnu = r.nu32[f] - nu21;
+                const float s21 = sW * a21 * __expf(-dnu * dnu * inv2s2);
+                char *wbuf = w_stages + ws * W_STAGE_BYTES;
+                switch (mode) {
+                    case 3: gen_row<KP, BF16, 3>(wbuf, m, dlt, N, nL, s21, sW, c, cu); break;
+                    case 5: gen_row<KP, BF16, 5>(wbuf, m, dlt, N, nL, s21, sW, c, cu); break;
+                    case 8: gen_row<KP, BF16, 8>(wbuf, m, dlt, N, nL, s21, sW, c, cu); break;
+                    default: gen_row<KP, BF16, 0>(wbuf, m, dlt, N, nL, s21, sW, c, cu); break;
+                }
+                fence_proxy_async_smem();
+                mbar_arrive(&S->w_full[ws]);
+                ++w_stage;
+            }
+        }
+    } else if (warp < 8) {
+        // ========================================================= epilogue
+        const int quad = warp & 3;
+        const int m = quad * 32 + lane;
+        uint32_t acc_stage = 0;
+        bool ok = true;
+        for (int64_t item = blockIdx.x; item < prm.n_items && ok; item += gridDim.x) {
+            const Item it = decode_item(reqs, prm.n_reqs, item);
+            const ReqDesc &r = reqs[it.req];
+            const int64_t p = (int64_t)it.tile * 128 + m;
+            const int sWexp = *r.scaleW;
+            float qs = 0.0f, qc = 0.0f;
+            for (int f = it.f0; f < it.f1 && ok; ++f) {
+                float qf = 0.0f;
+                for (int cch = 0; cch < r.n_tchunks; ++cch) {
+                    const uint32_t a = acc_stage % NACC, aph = (acc_stage / NACC) & 1;
+                    if (!mbar_wait(&S->acc_full[a], aph, S, prm.status, STATUS_TIMEOUT_EPI)) { ok = false; break; }
+                    tc_fence_after();
+                    const int fc = f * r.n_tchunks + cch;
+                    const int t0 = cch * r.Tc, tn = min(r.Tc, r.T - t0);
+                    const float unscale = ldexpf(1.0f, -(sWexp + r.scaleB[fc]));
+                    const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + a * prm.acc_cols;
+                    float q = 0.0f;
+                    for (int col = 0; col < r.Tc_pad; col += 16) {
+                        float v[16];
+                        tmem_ld16(taddr + col, v);
+                        tmem_ld_wait();
+                        if (prm.resid) {
+                            if (p < r.P) {
+#pragma unroll
+                                for (int j = 0; j < 16; ++j)
+                                    if (col + j < tn)
+                                        prm.resid[((size_t)p * r.F + f) * r.T + t0 + col + j] = -v[j] * unscale;
+                            }
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) q = fmaf(v[j], v[j], q);
+                        }
+                    }
+                    tc_fence_before();
+                    mbar_arrive(&S->acc_empty[a]);
+                    ++acc_stage;
+                    qf += q * unscale * unscale;
+                }
+                kahan_add_dev(qs, qc, qf);
+            }
+            if (ok && !prm.resid && p < r.P) r.partials[(size_t)p * r.G + it.g] = make_float2(qs, -qc);
+        }
+    } else if (warp == 8) {
+        // ====================================================== TMA producer
+        uint32_t b_stage = 0;
+        bool ok = true;
+        if (lane == 0) {
+            for (int64_t item = blockIdx.x; item < prm.n_items && ok; item += gridDim.x) {
+                const Item it = decode_item(reqs, prm.n_reqs, item);
+                const ReqDesc &r = reqs[it.req];
+                const int rows = (int)r.tile_rows;
+                for (int f = it.f0; f < it.f1 && ok; ++f) {
+                    for (int cch = 0; cch < r.n_tchunks; ++cch) {
+                        const uint32_t bs = b_stage % NB_STAGES, bph = (b_stage / NB_STAGES) & 1;
+                        if (!mbar_wait(&S->b_empty[bs], bph ^ 1, S, prm.status, STATUS_TIMEOUT_TMA)) { ok = false; break; }
+                        mbar_arrive_expect_tx(&S->b_full[bs], (uint32_t)rows * 128u);
+                        const int64_t row0 = r.tile_row0 + (int64_t)(f * r.n_tchunks + cch) * rows;
+                        char *dst = b_stages + bs * prm.b_stage_bytes;
+                        for (int j = 0; j < rows; j += BOX_ROWS)
+                            tma_load_2d(dst + j * 128, &tmap, 0, (int)(row0 + j), &S->b_full[bs]);
+                        ++b_stage;
+                    }
+                }
+            }
+            // drain: wait for the copies of the last stages issued (they land
+            // whether or not the MMA consumed them)
+            const uint32_t n_tail = b_stage < NB_STAGES ? b_stage : NB_STAGES;
+            for (uint32_t k = b_stage - n_tail; k < b_stage; ++k) {
+                const uint32_t bs = k % NB_STAGES, bph = (k / NB_STAGES) & 1;
+                uint64_t t0 = globaltimer();
+                while (!mbar_try_wait(&S->b_full[bs], bph)) {
+                    if (globaltimer() - t0 > WAIT_LIMIT_NS) {
+                        atomicOr(prm.status, STATUS_TIMEOUT_DRAIN);
+                        break;
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    } else {
+        // ========================================================= MMA issuer
+        uint32_t b_stage = 0, w_stage = 0, acc_stage = 0;
+        bool ok = true;
+        if (lane == 0) {
+            for (int64_t item = blockIdx.x; item < prm.n_items && ok; item += gridDim.x) {
+                const Item it = decode_item(reqs, prm.n_reqs, item);
+                const ReqDesc &r = reqs[it.req];
+                const uint32_t idesc = instr_desc(128, r.Tc_pad, BF16);
+                const uint32_t b_lbo = (uint32_t)r.Tc_pad * 16;
+                const uint32_t b_split = (uint32_t)(r.Kp / 8) * b_lbo;
+                const int ksteps = r.Kp / 16;
+                for (int f = it.f0; f < it.f1 && ok; ++f) {
+                    const uint32_t ws = w_stage % NW_STAGES, wph = (w_stage / NW_STAGES) & 1;
+                    if (!mbar_wait(&S->w_full[ws], wph, S, prm.status, STATUS_TIMEOUT_MMA)) { ok = false; break; }
+                    const uint32_t w_addr = smem_u32(w_stages + ws * W_STAGE_BYTES);
+                    for (int cch = 0; cch < r.n_tchunks; ++cch) {
+                        const uint32_t bs = b_stage % NB_STAGES, bph = (b_stage / NB_STAGES) & 1;
+                        const uint32_t a = acc_stage % NACC, aph = (acc_stage / NACC) & 1;
+                        if (!mbar_wait(&S->b_full[bs], bph, S, prm.status, STATUS_TIMEOUT_MMA)) { ok = false; break; }
+                        if (!mbar_wait(&S->acc_empty[a], aph ^ 1, S, prm.status, STATUS_TIMEOUT_MMA)) { ok = false; break; }
+                        tc_fence_after();
+                        const uint32_t b_addr = smem_u32(b_stages + bs * prm.b_stage_bytes);
+                        const uint32_t d_tmem = tmem + a * prm.acc_cols;
+                        for (int ks = 0; ks < ksteps; ++ks) {
+                            const uint64_t a_hi = smem_desc(w_addr + ks * 4096, 2048, 128);
+                            const uint64_t a_mid = smem_desc(w_addr + (KP / 8) * 2048 + ks * 4096, 2048, 128);
+                            const uint64_t b_hi = smem_desc(b_addr + ks * 2 * b_lbo, b_lbo, 128);
+                            const uint64_t b_mid = smem_desc(b_addr + b_split + ks * 2 * b_lbo, b_lbo, 128);
+                            mma_f16(d_tmem, a_hi, b_hi, idesc, ks > 0 ? 1u : 0u);
+                            mma_f16(d_tmem, a_hi, b_mid, idesc, 1u);
+                            mma_f16(d_tmem, a_mid, b_hi, idesc, 1u);
+                        }
+                        mma_commit(&S->b_empty[bs]);
+                        mma_commit(&S->acc_full[a]);
+                        if (cch == r.n_tchunks - 1) mma_commit(&S->w_empty[ws]);
+                        ++b_stage;
+                        ++acc_stage;
+                    }
+                    ++w_stage;
+                }
+            }
+            // drain: every MMA issued so far completes before tensor memory is freed
+            mma_commit(&S->drain);
+            uint64_t t0 = globaltimer();
+            while (!mbar_try_wait(&S->drain, 0)) {
+                if (globaltimer() - t0 > WAIT_LIMIT_NS) {
+                    atomicOr(prm.status, STATUS_TIMEOUT_DRAIN);
+                    break;
+                }
+            }
+        }
+        __syncwarp();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 9) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(prm.tmem_cols)
+                     : "memory");
+    }
+}
+
+// ------------------------------------------------------------ host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn g_encode = nullptr;
+std::once_flag g_encode_once;
+int g_encode_rc = FG21_OK;
+
+size_t smem_bytes(int kp, int b_stage_bytes) {
+    return 1024 + (size_t)NW_STAGES * 2 * kp * 128 * 2 + (size_t)NB_STAGES * b_stage_bytes + sizeof(Barriers) + 64;
+}
+
+template <int KP, bool BF16>
+cudaError_t launch_kp(const CUtensorMap &map, const Params &prm, int grid, size_t sm, cudaStream_t stream) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(tc_loglike_kernel<KP, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             227 * 1024);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    tc_loglike_kernel<KP, BF16><<<grid, NUM_THREADS, sm, stream>>>(map, prm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_common(const ReqDesc *d_reqs, int n_reqs, int64_t n_items, int kp_max, int tc_pad_max,
+                          int precision, void *arena, int64_t arena_rows, unsigned *status, float *resid,
+                          int num_sms, cudaStream_t stream) {
+    if (n_items == 0) return cudaSuccess;
+    if (tc_map_init() != FG21_OK) return cudaErrorNotSupported;
+    CUtensorMap map;
+    cuuint64_t gdim[2] = {64, (cuuint64_t)arena_rows};
+    cuuint64_t gstride[1] = {128};
+    cuuint32_t box[2] = {64, BOX_ROWS};
+    cuuint32_t estride[2] = {1, 1};
+    CUresult cr = g_encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, arena, gdim, gstride, box, estride,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    Params prm;
+    prm.reqs = d_reqs;
+    prm.n_reqs = n_reqs;
+    prm.n_items = n_items;
+    prm.b_stage_bytes = ((4 * kp_max * tc_pad_max) + 1023) & ~1023;
+    prm.acc_cols = tc_pad_max;
+    uint32_t cols = 32;
+    while (cols < (uint32_t)(NACC * tc_pad_max)) cols *= 2;
+    prm.tmem_cols = cols;
+    prm.status = status;
+    prm.resid = resid;
+    const int kp = kp_max <= 16 ? 16 : kp_max <= 32 ? 32 : 64;
+    // at least ~120 KB so that a single CTA (and its tensor memory) owns each SM
+    size_t sm = smem_bytes(kp, prm.b_stage_bytes);
+    if (sm < 120 * 1024) sm = 120 * 1024;
+    const int grid = (int)(n_items < num_sms ? n_items : num_sms);
+    const bool bf16 = precision == FG21_PREC_BF16X3;
+    if (kp == 16) return bf16 ? launch_kp<16, true>(map, prm, grid, sm, stream) : launch_kp<16, false>(map, prm, grid, sm, stream);
+    if (kp == 32) return bf16 ? launch_kp<32, true>(map, prm, grid, sm, stream) : launch_kp<32, false>(map, prm, grid, sm, stream);
+    return bf16 ? launch_kp<64, true>(map, prm, grid, sm, stream) : launch_kp<64, false>(map, prm, grid, sm, stream);
+}
+
+}  // namespace
+
+int tc_map_init() {
+    std::call_once(g_encode_once, [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+            cudaGetLastError();
+            g_encode_rc = set_error(FG21_E_CUDA, "cuTensorMapEncodeTiled is not available");
+            return;
+        }
+        g_encode = (EncodeTiledFn)fn;
+    });
+    return g_encode_rc;
+}
+
+cudaError_t launch_tc(const TcLaunch &L, int num_sms, cudaStream_t stream) {
+    return launch_common(L.d_reqs, L.n_reqs, L.n_items, L.kp_max, L.tc_pad_max, L.precision, L.arena,
+                         L.arena_rows, L.status, nullptr, num_sms, stream);
+}
+
+cudaError_t launch_tc_residuals(const ReqDesc *h_req, const ReqDesc *d_req, int precision, float *resid,
+                                cudaStream_t stream) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    int sms = 1;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    char *arena = h_req->tiles - h_req->tile_row0 * 128;
+    const int64_t rows = h_req->tile_row0 + (int64_t)h_req->F * h_req->n_tchunks * h_req->tile_rows;
+    const int64_t items = (int64_t)h_req->n_tiles * h_req->G;
+    return launch_common(d_req, 1, items, h_req->Kp, h_req->Tc_pad, precision, arena, rows, h_req->status, resid,
+                         sms, stream);
+}
+
+}  // namespace fg21

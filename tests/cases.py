@@ -1,0 +1,126 @@
+"""Shared parity cases: seeded inputs, oracle expectations and tolerances.
+
+Every expected value comes from the FP64 oracle (oracle/); inputs come from
+paper_2603_13196_gb300.inputs.  Nothing here calls the CUDA library.
+
+Tolerances (derived from the arithmetic; see the design notes):
+  * logL, any point:  |dlogL| <= 1e-2 + REL_CHI2[prec] * chi2 / (2 sigma_n^2)
+    The data term chi2/(2 sigma^2) is what carries rounding: each residual r is
+    formed from terms of size |S| (the point's departure from the request
+    reference, or the whole foreground for the direct form) with relative
+    error eta, so |d(r^2)| <= 2 |r| eta |S|; summed, the error is a fixed
+    fraction of the data term when |S| ~ |r| (far-from-data points) and far
+    below 1e-2 nats when |r| ~ sigma (points at the posterior).
+  * logL at near-posterior points (chi2 / (F T sigma^2) <= 10): |dlogL| <= 1e-2.
+  * T_model per (p, f, t) at near-posterior points: |dT| <= 1e-3 K.
+  * T_model per (p, f, t), any point: |dT| <= 1e-3 K + REL_T[prec] * scale, the
+    scale being what the form's arithmetic carries (t_model_scale): the
+    departure from the request reference plus |D - M| for the
+    reference-subtracted forms, the whole foreground for the plain form.
+"""
+from __future__ import annotations
+
+import functools
+import math
+
+import numpy as np
+
+import oracle as O
+from paper_2603_13196_gb300 import inputs as I
+
+# Unit roundoff of the operand representation of each form: split 16-bit
+# (hi + mid) keeps 22 significand bits for FP16 (2 x 11) and 16 for BF16
+# (2 x 8); the SIMT forms are FP32 (24 bits).
+U = {"fp16x3": 2.0 ** -22, "bf16x3": 2.0 ** -16, "fp32_delta": 2.0 ** -24, "fp32_direct": 2.0 ** -24}
+# relative error of the data term chi2/(2 sigma^2) allowed per precision:
+# d(r^2)/r^2 <= 2 eta |S|/|r|, eta <= 3u (three split products) plus the FP32
+# accumulation; for far-from-data points |S| ~ |r| -> 8u.  The plain FP32 form
+# carries the whole foreground (|M| >> |r|), so it gets no such bound: it is
+# the comparator and its looser limit only guards against gross failure.
+REL_CHI2 = {"fp16x3": 8 * U["fp16x3"], "bf16x3": 8 * U["bf16x3"], "fp32_delta": 8 * U["fp32_delta"],
+            "fp32_direct": 1e-4}
+# T_model per (p,f,t), relative to the magnitude the form carries (see
+# t_model_scale): split products 3u plus FP32 accumulation over K ~ 100 terms.
+REL_T = {"fp16x3": 16 * U["fp16x3"], "bf16x3": 16 * U["bf16x3"], "fp32_delta": 16 * U["fp32_delta"],
+         "fp32_direct": 16 * U["fp32_direct"]}
+
+
+@functools.lru_cache(maxsize=None)
+def workload_case(k: int, P: int = None):
+    """(wl, sky, obs, oracle model, data, params) of workload k (1..3)."""
+    wl = I.workload(k)
+    sky, obs = wl.sky(), wl.obs()
+    m = O.build_model(sky, obs, wl.N, wl.scheme, wl.weighting)
+    data = O.simulate_data(sky, obs, np.array(I.FIDUCIAL_T21), I.NOISE_K, wl.noise())
+    params = wl.params(P)
+    return wl, sky, obs, m, data, params
+
+
+def small_case(npix=3072, N=5, F=31, T=7, window=4.0, seed=77, scheme="recursive", weighting="beam",
+               lst0=3.0, achromatic_p=None):
+    sky = I.make_sky(npix, seed)
+    obs = I.make_obs(F, T, window, lst0, achromatic_p=achromatic_p)
+    m = O.build_model(sky, obs, N, scheme, weighting)
+    data = O.simulate_data(sky, obs, np.array(I.FIDUCIAL_T21), I.NOISE_K, I.noise_draws(F, T, seed))
+    return sky, obs, m, data
+
+
+def near_posterior(m, obs, dbeta: float, P: int, seed: int = 5, sigma=I.NOISE_K):
+    """Data equal to the N-region model at a truth theta* plus 25 mK noise, and
+    P points scattered uniformly by +-dbeta around theta* (sigma_n = 25 mK)."""
+    N = m.A.shape[0]
+    rng = I.rng(seed, I.SUB_PARAMS, 77)
+    truth = np.concatenate([rng.uniform(2.5, 2.7, N), [0.155, 85.0, 15.0, sigma]])
+    data = O.fast_model(m.A, m.B, obs, truth)[0] + sigma * I.noise_draws(obs.F, obs.T, seed, 3)
+    pts = I.scatter_around(truth, P, dbeta, seed)
+    return truth, data, pts
+
+
+def expected(m, obs, data, params):
+    """(logL, chi2/(2 sigma^2)) from the oracle."""
+    L = O.loglike(m.A, m.B, data, obs, params)
+    c2 = O.chi2(m.A, m.B, data, obs, params)
+    sig = params[:, -1]
+    return L, c2 / (2.0 * sig * sig)
+
+
+def logl_tolerance(prec: str, data_term: np.ndarray) -> np.ndarray:
+    return 1e-2 + REL_CHI2[prec] * np.abs(data_term)
+
+
+def foreground_departure(m, obs, params, beta_ref):
+    """S_abs[p,f,t] = sum_i |A_i| |w(beta_p,i) - w(beta_ref,i)| (K)."""
+    N = m.A.shape[0]
+    L = np.log(obs.nu / obs.nu0)
+    w = np.exp(-params[:, :N, None] * L[None, None, :])          # [P,N,F]
+    w0 = np.exp(-beta_ref[:, None] * L[None, :])                  # [N,F]
+    d = np.abs(w - w0[None])
+    return np.einsum("pif,ift->pft", d, np.abs(m.A))
+
+
+def t_model_scale(prec, m, obs, data, params):
+    """Magnitude carried by each form's arithmetic for T_model[p,f,t]: the
+    departure from the request reference plus the residual |D - M| for the
+    reference-subtracted forms; the foreground sum for the plain form."""
+    if prec == "fp32_direct":
+        return foreground_magnitude(m, obs, params)
+    bbar = params[:, :m.A.shape[0]].mean(axis=0)
+    r = np.abs(data[None] - O.fast_model(m.A, m.B, obs, params))
+    return foreground_departure(m, obs, params, bbar) + r
+
+
+def foreground_magnitude(m, obs, params):
+    N = m.A.shape[0]
+    L = np.log(obs.nu / obs.nu0)
+    w = np.exp(-params[:, :N, None] * L[None, None, :])
+    return np.einsum("pif,ift->pft", w, np.abs(m.A))
+
+
+def fmt_err(name, got, want, tol):
+    err = np.abs(got - want)
+    k = int(np.argmax(err / tol))
+    return f"{name}: max|err|={err.max():.3e} worst err/tol={float((err / tol)[k]):.3f} at {k}"
+
+
+def sigma_floor():
+    return math.log(2 * math.pi * I.NOISE_K ** 2)

@@ -1,0 +1,39 @@
+"""GPU parity of the SIMT forms (plain FP32 and FP32 reference-subtracted)
+against the FP64 oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import cases
+from conftest import report
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("prec", ["fp32_delta", "fp32_direct"])
+@pytest.mark.parametrize("P", [1, 129])
+def test_simt_small(fg21lib, prec, P):
+    sky, obs, m, data = cases.small_case()
+    model = fg21lib.fg21_build_regions(sky, obs, 5)
+    assert np.array_equal(model.labels, m.labels)
+    fg21lib.fg21_model_set_data(model, data)
+    params = cases.I.prior_draws(P, 5, seed=3)
+    got = fg21lib.fg21_loglike_batch(model, params, prec)
+    want, dterm = cases.expected(m, obs, data, params)
+    tol = cases.logl_tolerance(prec, dterm)
+    report(f"simt_small_{prec}_{P}", max_abs=np.max(np.abs(got - want)),
+           max_rel_dterm=np.max(np.abs(got - want) / np.abs(dterm)))
+    assert np.all(np.abs(got - want) <= tol), cases.fmt_err(prec, got, want, tol)
+
+
+@pytest.mark.parametrize("prec", ["fp32_delta", "fp32_direct"])
+def test_simt_workload1(fg21lib, prec):
+    wl, sky, obs, m, data, params = cases.workload_case(1)
+    model = fg21lib.fg21_build_regions(sky, obs, wl.N, wl.scheme)
+    assert np.array_equal(model.labels, m.labels)
+    fg21lib.fg21_model_set_data(model, data)
+    got = fg21lib.fg21_loglike_batch(model, params, prec)
+    want, dterm = cases.expected(m, obs, data, params)
+    tol = cases.logl_tolerance(prec, dterm)
+    report(f"simt_w1_{prec}", max_abs=np.max(np.abs(got - want)),
+           max_rel_dterm=np.max(np.abs(got - want) / np.abs(dterm)))
+    assert np.all(np.abs(got - want) <= tol), cases.fmt_err(prec, got, want, tol)

@@ -1,0 +1,159 @@
+"""GPU parity of the tensor-core (tcgen05) path against the FP64 oracle,
+through the C ABI: prior draws at several shapes (ragged tiles, t-chunks,
+K = 16 / 32 / 64), near-posterior sets with the absolute 1e-2 nats bound,
+per-channel model temperatures, invalid points, BF16 operands."""
+import numpy as np
+import pytest
+
+import cases
+import oracle as O
+from conftest import report
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [
+    # (npix, N, F, T, P)
+    (1024, 3, 9, 1, 1),        # one point, one LST bin, K = 16
+    (2048, 5, 31, 7, 129),     # ragged tile tail
+    (2048, 14, 17, 20, 300),   # K = 16 exactly
+    (2048, 30, 11, 40, 257),   # K = 32
+    (3072, 40, 9, 9, 140),     # K = 64
+    (1024, 4, 5, 300, 130),    # two t-chunks (T > 256)
+]
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "npix%d_N%d_F%d_T%d_P%d" % s)
+@pytest.mark.parametrize("prec", ["fp16x3", "bf16x3"])
+def test_tc_prior_draws(fg21lib, shape, prec):
+    npix, N, F, T, P = shape
+    sky, obs, m, data = cases.small_case(npix=npix, N=N, F=F, T=T, window=3.0)
+    model = fg21lib.fg21_build_regions(sky, obs, N)
+    assert np.array_equal(model.labels, m.labels)
+    fg21lib.fg21_model_set_data(model, data)
+    params = cases.I.prior_draws(P, N, seed=N * 7 + T)
+    got = fg21lib.fg21_loglike_batch(model, params, prec)
+    want, dterm = cases.expected(m, obs, data, params)
+    tol = cases.logl_tolerance(prec, dterm)
+    report(f"tc_prior_{prec}_{shape}", max_abs=np.max(np.abs(got - want)),
+           max_rel_dterm=np.max(np.abs(got - want) / np.abs(dterm)))
+    assert np.all(np.abs(got - want) <= tol), cases.fmt_err(prec, got, want, tol)
+
+
+@pytest.mark.parametrize("prec", ["fp16x3", "fp32_delta", "fp32_direct", "bf16x3"])
+@pytest.mark.parametrize("dbeta", [1e-6, 1e-5, 1e-4])
+def test_near_posterior(fg21lib, prec, dbeta):
+    """Points within the posterior bulk of an N-region truth: the absolute
+    1e-2 nats bound for the reference-subtracted forms; the plain FP32 form's
+    error is recorded (it is the comparator and is expected to miss it)."""
+    sky, obs, m, _ = cases.small_case(npix=3072, N=9, F=151, T=20, window=6.0)
+    truth, data, pts = cases.near_posterior(m, obs, dbeta, 512)
+    model = fg21lib.fg21_build_regions(sky, obs, 9)
+    fg21lib.fg21_model_set_data(model, data)
+    got = fg21lib.fg21_loglike_batch(model, pts, prec)
+    want, dterm = cases.expected(m, obs, data, pts)
+    err = np.abs(got - want)
+    red = 2 * dterm / (obs.F * obs.T)
+    report(f"near_post_{prec}_{dbeta}", max_abs=err.max(), max_chi2_red=red.max(), min_chi2_red=red.min())
+    if prec in ("fp16x3", "fp32_delta"):
+        near = red <= 10
+        assert np.all(err[near] <= 1e-2), cases.fmt_err(prec, got[near], want[near], 1e-2)
+    tol = cases.logl_tolerance(prec, dterm)
+    if prec != "fp32_direct":
+        assert np.all(err <= tol), cases.fmt_err(prec, got, want, tol)
+
+
+@pytest.mark.parametrize("prec", ["fp16x3", "bf16x3", "fp32_delta", "fp32_direct"])
+def test_model_temperature_prior_draws(fg21lib, prec):
+    """T_model[p,f,t] of the kernel's own arithmetic against eq. fast_forward_model,
+    relative to the magnitude the form carries (prior draws, far from the data)."""
+    sky, obs, m, data = cases.small_case(npix=2048, N=6, F=41, T=5)
+    model = fg21lib.fg21_build_regions(sky, obs, 6)
+    fg21lib.fg21_model_set_data(model, data)
+    params = cases.I.prior_draws(40, 6, seed=9)
+    got = fg21lib.fg21_model_eval(model, params, prec)
+    want = O.fast_model(m.A, m.B, obs, params)
+    scale = cases.t_model_scale(prec, m, obs, data, params)
+    tol = 1e-3 + cases.REL_T[prec] * scale
+    err = np.abs(got - want)
+    report(f"T_model_prior_{prec}", max_abs=err.max(), max_rel_scale=np.max(err / scale))
+    assert np.all(err <= tol), cases.fmt_err(prec, got, want, tol)
+
+
+@pytest.mark.parametrize("prec", ["fp16x3", "fp32_delta", "fp32_direct", "bf16x3"])
+@pytest.mark.parametrize("dbeta", [1e-6, 1e-5])
+def test_model_temperature_near_posterior(fg21lib, prec, dbeta):
+    """|dT_model| <= 1e-3 K per (p, f, t) at points within the posterior bulk
+    (data = N-region truth + 25 mK noise) for the reference-subtracted forms;
+    the plain FP32 form's error (one FP32 ulp of a 1e4 K foreground is ~1e-3 K)
+    is recorded."""
+    sky, obs, m, _ = cases.small_case(npix=3072, N=9, F=151, T=4, window=2.0)
+    truth, data, pts = cases.near_posterior(m, obs, dbeta, 64)
+    model = fg21lib.fg21_build_regions(sky, obs, 9)
+    fg21lib.fg21_model_set_data(model, data)
+    got = fg21lib.fg21_model_eval(model, pts, prec)
+    want = O.fast_model(m.A, m.B, obs, pts)
+    err = np.abs(got - want)
+    report(f"T_model_near_{prec}_{dbeta}", max_abs=err.max())
+    if prec != "fp32_direct":
+        assert err.max() <= 1e-3, f"{prec}: max |dT| = {err.max():.3e} K"
+
+
+def test_invalid_points(fg21lib):
+    sky, obs, m, data = cases.small_case(npix=1024, N=3, F=9, T=2)
+    model = fg21lib.fg21_build_regions(sky, obs, 3)
+    fg21lib.fg21_model_set_data(model, data)
+    params = cases.I.prior_draws(10, 3, seed=1)
+    params[1, 0] = np.nan
+    params[3, -1] = 0.0          # sigma_n = 0
+    params[5, -1] = -1.0         # sigma_n < 0
+    params[7, 5] = 0.0           # sigma21 = 0
+    params[8, 4] = np.inf
+    for prec in ("fp16x3", "fp32_delta", "fp32_direct"):
+        got = fg21lib.fg21_loglike_batch(model, params, prec)
+        bad = [1, 3, 5, 7, 8]
+        assert np.all(np.isneginf(got[bad]))
+        assert fg21lib.fg21_last_invalid_count() == 5
+        good = [0, 2, 4, 6, 9]
+        want, dterm = cases.expected(m, obs, data, params[good])
+        assert np.all(np.abs(got[good] - want) <= cases.logl_tolerance(prec, dterm))
+
+
+def test_empty_batch_and_errors(fg21lib):
+    sky, obs, m, data = cases.small_case(npix=512, N=2, F=5, T=1)
+    model = fg21lib.fg21_build_regions(sky, obs, 2)
+    assert fg21lib.fg21_loglike_batch(model, np.empty((0, 6))).shape == (0,)
+    with pytest.raises(fg21lib.Fg21Error) as e:
+        fg21lib.fg21_loglike_batch(model, np.zeros((3, 6)), precision=7)
+    assert e.value.code == fg21lib.FG21_E_ARG
+
+
+def test_workload1_all_precisions(fg21lib):
+    wl, sky, obs, m, data, params = cases.workload_case(1)
+    model = fg21lib.fg21_build_regions(sky, obs, wl.N, wl.scheme)
+    assert np.array_equal(model.labels, m.labels)
+    np.testing.assert_array_equal(model.edges, m.edges)
+    A, B = fg21lib.fg21_model_get_arrays(model)
+    np.testing.assert_allclose(A, m.A, rtol=1e-12, atol=1e-12 * np.abs(m.A).max())
+    np.testing.assert_allclose(B, m.B, rtol=1e-12)
+    fg21lib.fg21_model_set_data(model, data)
+    want, dterm = cases.expected(m, obs, data, params)
+    for prec in ("fp16x3", "bf16x3", "fp32_delta", "fp32_direct"):
+        got = fg21lib.fg21_loglike_batch(model, params, prec)
+        tol = cases.logl_tolerance(prec, dterm)
+        report(f"w1_{prec}", max_abs=np.max(np.abs(got - want)),
+               max_rel_dterm=np.max(np.abs(got - want) / np.abs(dterm)))
+        assert np.all(np.abs(got - want) <= tol), cases.fmt_err(prec, got, want, tol)
+
+
+def test_workload2_full(fg21lib):
+    wl, sky, obs, m, data, params = cases.workload_case(2)
+    model = fg21lib.fg21_build_regions(sky, obs, wl.N, wl.scheme)
+    assert np.array_equal(model.labels, m.labels)
+    fg21lib.fg21_model_set_data(model, data)
+    want, dterm = cases.expected(m, obs, data, params)
+    for prec in ("fp16x3", "fp32_direct"):
+        got = fg21lib.fg21_loglike_batch(model, params, prec)
+        tol = cases.logl_tolerance(prec, dterm)
+        report(f"w2_{prec}", max_abs=np.max(np.abs(got - want)),
+               max_rel_dterm=np.max(np.abs(got - want) / np.abs(dterm)))
+        assert np.all(np.abs(got - want) <= tol), cases.fmt_err(prec, got, want, tol)
