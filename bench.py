@@ -146,6 +146,113 @@ def cpu_baseline(sky, obs, N, params, seconds):
                       f"OpenMP over points, {dt:.1f} s"}, m, data
 
 
+def serve_phase(fg21, I, seconds=3.0, n_runs=64):
+    """Serving workload: n_runs concurrent runs (N in {5,9,14,20,30}, T in {1,10,50}
+    over differing LST windows, F = 151, 3072-pixel sky), requests of 128-4096
+    prior-draw points to uniformly chosen runs.  (1) closed loop, 8 clients:
+    capacity in points/s; (2) open loop, Poisson arrivals at half that capacity:
+    p50 / p99 submit-to-result latency."""
+    import queue
+    import numpy as np
+
+    g = I.rng(I.BASE_SEED + 5, I.SUB_ARRIVALS)
+    Ns, Ts = [5, 9, 14, 20, 30], [1, 10, 50]
+    srv = fg21.Server(mem_budget_bytes=60 << 30, max_batch_points=65536, max_wait_us=200, max_inflight=2)
+    runs, models = [], []
+    t0 = time.time()
+    for k in range(n_runs):
+        N, T = Ns[k % 5], Ts[(k // 5) % 3]
+        window = 0.0 if T == 1 else float(g.choice([2.0, 6.0, 12.0]))
+        sky = I.make_sky(3072, I.BASE_SEED + 500 + k)
+        obs = I.make_obs(151, T, window, lst0_h=float(g.uniform(0, 24)))
+        m = fg21.fg21_build_regions(sky, obs, N, "recursive")
+        fg21.fg21_model_set_data(m, fg21.fg21_simulate_data(sky, obs, I.FIDUCIAL_T21, I.NOISE_K,
+                                                            I.noise_draws(151, T, k)))
+        rid, _ = fg21.fg21_serve_register_run(srv, m)
+        runs.append((rid, N, T))
+        models.append(m)
+    build_s = time.time() - t0
+    pool = []
+    for j in range(256):
+        k = int(g.integers(0, n_runs))
+        P = int(g.integers(128, 4097))
+        pool.append((runs[k][0], I.prior_draws(P, runs[k][1], seed=j, extra=k), runs[k][1] * 151 * runs[k][2]))
+
+    def closed(dur):
+        stop = time.time() + dur
+        cnt = [0, 0.0]
+        lock = threading.Lock()
+
+        def client(c):
+            j = c
+            while time.time() < stop:
+                rid, p, w = pool[j % len(pool)]
+                t, _ = fg21.fg21_serve_submit(srv, rid, p)
+                fg21.fg21_serve_wait(srv, t, 60000)
+                with lock:
+                    cnt[0] += p.shape[0]
+                    cnt[1] += w * p.shape[0]
+                j += 8
+        th = [threading.Thread(target=client, args=(c,)) for c in range(8)]
+        t = time.time()
+        [x.start() for x in th]
+        [x.join() for x in th]
+        el = time.time() - t
+        return cnt[0] / el, cnt[1] / el
+
+    cap_pts, cap_macs = closed(seconds)
+    st_cap = fg21.fg21_serve_stats(srv)
+    srv.close()
+    # a fresh server for the open-loop latency measurement
+    srv = fg21.Server(mem_budget_bytes=60 << 30, max_batch_points=65536, max_wait_us=200, max_inflight=2)
+    remap = {}
+    for rid, N, T in runs:
+        remap[rid], _ = fg21.fg21_serve_register_run(srv, models[len(remap)])
+    pool = [(remap[rid], p, w) for rid, p, w in pool]
+    mean_pts = float(np.mean([p.shape[0] for _, p, _ in pool]))
+    rate = 0.5 * cap_pts / mean_pts                       # requests per second
+    q = queue.Queue()
+    lat = []
+
+    def waiter():
+        while True:
+            item = q.get()
+            if item is None:
+                return
+            fg21.fg21_serve_wait(srv, item, 60000)
+
+    ws = [threading.Thread(target=waiter) for _ in range(4)]
+    [w.start() for w in ws]
+    rng = np.random.default_rng(7)
+    tnext = time.time()
+    end = tnext + seconds
+    n_sub = 0
+    while tnext < end:
+        now = time.time()
+        if now < tnext:
+            time.sleep(tnext - now)
+        rid, p, _ = pool[n_sub % len(pool)]
+        t, _ = fg21.fg21_serve_submit(srv, rid, p)
+        q.put(t)
+        n_sub += 1
+        tnext += rng.exponential(1.0 / rate)
+    for _ in ws:
+        q.put(None)
+    [w.join() for w in ws]
+    st = fg21.fg21_serve_stats(srv)
+    srv.close()
+    for m in models:
+        m.close()
+    return {"workload": "64 runs, N in {5,9,14,20,30}, T in {1,10,50}, F=151, npix 3072; requests 128-4096 "
+                        "prior-draw points",
+            "capacity_points_per_s": cap_pts, "capacity_macs_per_s": cap_macs,
+            "offered_requests_per_s": rate, "requests": n_sub,
+            "p50_ms_at_half_load": st["p50_ms"], "p99_ms_at_half_load": st["p99_ms"],
+            "mean_ms_at_half_load": st["mean_ms"], "launches_at_half_load": st["launches"],
+            "closed_loop_p50_ms": st_cap["p50_ms"], "closed_loop_p99_ms": st_cap["p99_ms"],
+            "build_s": build_s}
+
+
 def run_reference(args):
     """Reference arm: the FP64 oracle as it stands, on the bench workload."""
     import numpy as np
@@ -326,6 +433,11 @@ def main():
         "clocks": clk,
         "macs_per_s": N * F * T * P * ws / (step_ms * 1e-3),
     }
+    if rank == 0 and not args.no_serve:
+        sv = serve_phase(fg21, I)
+        line["serve"] = sv
+        line["serve_p50_ms"] = sv["p50_ms_at_half_load"]
+        line["serve_p99_ms"] = sv["p99_ms_at_half_load"]
     if rank == 0 and not args.no_cpu_baseline:
         cb, _, _ = cpu_baseline(sky, obs, N, params, args.cpu_seconds)
         line["cpu_baseline"] = cb

@@ -155,7 +155,8 @@ int fg21_model_set_data(fg21_model *m, const double *data);
 int fg21_model_get_arrays(const fg21_model *m, double *A, double *B);
 
 /* Sizes of a model; any output pointer may be NULL.  device_bytes counts the
- * model's resident device memory (A, B, data, tables, workspace). */
+ * model's resident device memory (A, B, data and tables; the bytes the
+ * serving loop budgets for a run); the per-call workspace comes on top. */
 int fg21_model_info(const fg21_model *m, int32_t *N, int32_t *F, int32_t *T, int32_t *n_empty,
                     size_t *device_bytes);
 

@@ -72,16 +72,18 @@ struct ReqDesc {
     float *Bp32;           // [N][F][T] wbar_i A (FP32, SIMT delta form)
     float *dref32;         // [F][T]    reference residual (FP32, SIMT delta form)
     float2 *partials;      // [P][G] compensated partial chi^2 (hi, lo)
+    float *pts32;          // [n_tiles][Kp + 4][128] per point: beta - bbar (rows < Kp-2, zero
+                           // beyond N), then A21, nu21, 1/(2 sigma21^2) (rows Kp-2..Kp); tensor path
     unsigned *status;      // device status word (shared by a launch)
     unsigned long long *invalid;  // invalid-point counter
 };
 
 // Sizes of one request's workspace pieces (bytes, each 256-aligned).
 struct ReqLayout {
-    size_t stat_part, beta_bar, req_stats, nL32, nu32, scaleB, scaleW, Bp32, dref32, partials, tiles;
+    size_t stat_part, beta_bar, req_stats, nL32, nu32, scaleB, scaleW, Bp32, dref32, partials, pts32, tiles;
     size_t total() const {
         return stat_part + beta_bar + req_stats + nL32 + nu32 + scaleB + scaleW + Bp32 + dref32 +
-               partials + tiles;
+               partials + pts32 + tiles;
     }
 };
 
@@ -92,7 +94,7 @@ ReqLayout request_layout(const ReqDesc &r, int precision);
 // ------------------------------------------------------- kernel launchers
 // All enqueue on `stream` and return cudaError_t of the launch.
 cudaError_t launch_prep(const ReqDesc *h_reqs, const ReqDesc *d_reqs, int n_reqs, int precision,
-                        int max_stat_blocks, int max_F_chunks, cudaStream_t stream);
+                        int max_stat_blocks, int max_F_chunks, int max_tiles, cudaStream_t stream);
 cudaError_t launch_simt(const ReqDesc *h_reqs, const ReqDesc *d_reqs, int n_reqs, int precision,
                         cudaStream_t stream);
 cudaError_t launch_reduce(const ReqDesc *h_reqs, const ReqDesc *d_reqs, int n_reqs,
@@ -112,11 +114,14 @@ struct TcLaunch {
     int kp_max;              // max padded K over requests
     int tc_pad_max;          // max padded t-chunk over requests
     int precision;           // FG21_PREC_FP16X3 / BF16X3
+    int box_rows;            // TMA box height (divides every request's tile height)
     void *arena;             // operand tile arena (device), 128-byte rows
     int64_t arena_rows;
     unsigned *status;
 };
 cudaError_t launch_tc(const TcLaunch &L, int num_sms, cudaStream_t stream);
+// Largest multiple of 8 (<= 256 rows of 128 bytes) dividing every tile height.
+int tc_box_rows(const int64_t *tile_rows, int n);
 int tc_map_init();  // resolves cuTensorMapEncodeTiled; FG21_OK or error
 
 }  // namespace fg21

@@ -53,32 +53,54 @@ struct OpMin { __device__ double operator()(double a, double b) const { return f
 struct OpMax { __device__ double operator()(double a, double b) const { return fmax(a, b); } };
 
 // a1, pass 1: per block of STAT_BLOCK points, the sum / min / max of each
-// region's beta over valid points, the valid count and max |A21|.
+// region's beta over valid points (FP32: the reference point only has to be a
+// deterministic value near the points; the rearranged likelihood is exact for
+// any reference), the valid count and max |A21|.  Warps reduce by shuffles in
+// a fixed tree, then thread i combines the warps' partials of region i in
+// warp order, so the result is deterministic.
 __global__ void __launch_bounds__(PREP_THREADS) prep_stats_kernel(const ReqDesc *__restrict__ reqs) {
-    __shared__ double sh[32];
+    extern __shared__ float sh_stats[];        // [PREP_THREADS / 32][3N + 2]
     const ReqDesc &r = reqs[blockIdx.y];
     if ((int)blockIdx.x >= r.n_stat_blocks) return;
-    const int N = r.N;
+    const int N = r.N, W = 3 * N + 2, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t p = (int64_t)blockIdx.x * STAT_BLOCK + threadIdx.x;
     const double *th = r.params + p * (N + 4);
     const bool valid = p < r.P && point_valid(th, N);
-    double *out = r.stat_part + (size_t)blockIdx.x * (3 * N + 2);
+    float *mine = sh_stats + warp * W;
     for (int i = 0; i < N; ++i) {
-        double b = valid ? th[i] : 0.0;
-        double s = block_reduce(b, OpSum(), sh);
-        double mn = block_reduce(valid ? b : INFINITY, OpMin(), sh);
-        double mx = block_reduce(valid ? b : -INFINITY, OpMax(), sh);
-        if (threadIdx.x == 0) {
-            out[3 * i] = s;
-            out[3 * i + 1] = mn;
-            out[3 * i + 2] = mx;
+        const float b = valid ? (float)th[i] : 0.0f;
+        float s = b, mn = valid ? b : INFINITY, mx = valid ? b : -INFINITY;
+        for (int o = 16; o > 0; o >>= 1) {
+            s += __shfl_xor_sync(0xffffffffu, s, o);
+            mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        }
+        if (lane == 0) {
+            mine[3 * i] = s;
+            mine[3 * i + 1] = mn;
+            mine[3 * i + 2] = mx;
         }
     }
-    double nv = block_reduce(valid ? 1.0 : 0.0, OpSum(), sh);
-    double ma = block_reduce(valid ? fabs(th[N]) : 0.0, OpMax(), sh);
-    if (threadIdx.x == 0) {
-        out[3 * N] = nv;
-        out[3 * N + 1] = ma;
+    float nv = valid ? 1.0f : 0.0f, ma = valid ? fabsf((float)th[N]) : 0.0f;
+    for (int o = 16; o > 0; o >>= 1) {
+        nv += __shfl_xor_sync(0xffffffffu, nv, o);
+        ma = fmaxf(ma, __shfl_xor_sync(0xffffffffu, ma, o));
+    }
+    if (lane == 0) {
+        mine[3 * N] = nv;
+        mine[3 * N + 1] = ma;
+    }
+    __syncthreads();
+    double *out = r.stat_part + (size_t)blockIdx.x * W;
+    const int nw = blockDim.x >> 5;
+    for (int j = threadIdx.x; j < W; j += blockDim.x) {
+        const int kind = j < 3 * N ? j % 3 : (j == 3 * N ? 0 : 2);   // 0 sum, 1 min, 2 max
+        float v = sh_stats[j];
+        for (int w = 1; w < nw; ++w) {
+            const float x = sh_stats[w * W + j];
+            v = kind == 0 ? v + x : kind == 1 ? fminf(v, x) : fmaxf(v, x);
+        }
+        out[j] = (double)v;
     }
 }
 
@@ -102,23 +124,23 @@ __device__ __forceinline__ int pow2_exponent_for(double maxabs) {
 // column of the weights), row N+1 holds dref 2^sB (multiplies -1), other rows
 // and columns t >= Tc are zero.
 template <bool BF16>
-__device__ __forceinline__ uint16_t to_bits(double v) {
+__device__ __forceinline__ uint32_t pack_pair(float a, float b) {
     if (BF16) {
-        __nv_bfloat16 h = __double2bfloat16(v);
-        return *reinterpret_cast<uint16_t *>(&h);
+        __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<uint32_t *>(&h);
     } else {
-        __half h = __double2half(v);
-        return *reinterpret_cast<uint16_t *>(&h);
+        __half2 h = __floats2half2_rn(a, b);
+        return *reinterpret_cast<uint32_t *>(&h);
     }
 }
 template <bool BF16>
-__device__ __forceinline__ double from_bits(uint16_t b) {
+__device__ __forceinline__ float2 unpack_pair(uint32_t u) {
     if (BF16) {
-        __nv_bfloat16 h = *reinterpret_cast<__nv_bfloat16 *>(&b);
-        return (double)__bfloat162float(h);
+        __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162 *>(&u);
+        return __bfloat1622float2(h);
     } else {
-        __half h = *reinterpret_cast<__half *>(&b);
-        return (double)__half2float(h);
+        __half2 h = *reinterpret_cast<__half2 *>(&u);
+        return __half22float2(h);
     }
 }
 
@@ -171,17 +193,43 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_finalize_kernel(const ReqDe
 // Operand tile layout (one per channel and t-chunk, 2 x Kp x Tc_pad 16-bit
 // values): [split s in {hi, mid}][k-chunk kc = k/8][t][8 values k%8], i.e. the
 // K-major core-matrix layout (8 rows of 16 bytes) the tensor cores read; row k
-// < N holds wbar_k A[k,f,t] 2^sB, row N holds 2^sB (multiplies the trough
-// column of the weights), row N+1 holds dref 2^sB (multiplies -1), other rows
+// < N holds wbar_k A[k,f,t] 2^sB, row Kp-2 holds 2^sB (multiplies the trough
+// column of the weights), row Kp-1 holds dref 2^sB (multiplies -1), other rows
 // and columns t >= Tc are zero.
+//
+// Blocks beyond the tiles (tensor path only) write the per-point operands of
+// the weight generators, one block per 128-point tile, point-minor so that a
+// thread per point reads them coalesced: rows k < Kp-2 hold beta_{p,k} - bbar_k
+// in FP32 (zero for k >= N), then A21, nu21 and 1/(2 sigma21^2).
+template <int MODE>
+__device__ __forceinline__ void prep_points(const ReqDesc &r, int tile) {
+    const int64_t p = (int64_t)tile * TILE_M + threadIdx.x;
+    if (threadIdx.x >= TILE_M) return;
+    const int N = r.N, R = r.Kp + 4;
+    float *out = r.pts32 + (size_t)tile * R * TILE_M + threadIdx.x;
+    const bool in = p < r.P;
+    const double *th = r.params + (in ? p : 0) * (N + 4);
+    for (int k = 0; k < r.Kp - 2; ++k)
+        out[(size_t)k * TILE_M] = (in && k < N) ? (float)(th[k] - r.beta_bar[k]) : 0.0f;
+    out[(size_t)(r.Kp - 2) * TILE_M] = in ? (float)th[N] : 0.0f;
+    out[(size_t)(r.Kp - 1) * TILE_M] = in ? (float)th[N + 1] : 0.0f;
+    const float s21 = in ? (float)th[N + 2] : 1.0f;
+    out[(size_t)r.Kp * TILE_M] = 1.0f / (2.0f * s21 * s21);
+}
+
 template <int MODE>  // 0 = tensor FP16, 1 = tensor BF16, 2 = SIMT delta, 3 = SIMT direct
 __global__ void __launch_bounds__(PREP_THREADS) prep_tiles_kernel(const ReqDesc *__restrict__ reqs) {
     extern __shared__ double smem_d[];
     __shared__ double sh[32];
     __shared__ int s_scaleB;
     const ReqDesc &r = reqs[blockIdx.y];
+    const int nfc = r.F * r.n_tchunks;
+    if (MODE <= 1 && (int)blockIdx.x >= nfc) {
+        if ((int)blockIdx.x - nfc < r.n_tiles) prep_points<MODE>(r, blockIdx.x - nfc);
+        return;
+    }
     const int fc = blockIdx.x;
-    if (fc >= r.F * r.n_tchunks) return;
+    if (fc >= nfc) return;
     const int f = fc / r.n_tchunks, c = fc % r.n_tchunks;
     const int N = r.N, T = r.T;
     const int t0 = c * r.Tc, tn = min(r.Tc, T - t0);
@@ -194,55 +242,64 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_tiles_kernel(const ReqDesc 
         r.nu32[f] = (float)r.nu[f];
     }
     __syncthreads();
-    // --- reference residual dref[t] = D - sum_i wbar_i A_i - T_CMB B ---
-    double vmax = 1.0;
+    // --- reference residual dref[t] = D - sum_i wbar_i A_i - T_CMB B (FP64: the
+    // foreground cancels here) ---
+    float vmax = 1.0f;
     for (int t = threadIdx.x; t < tn; t += blockDim.x) {
         const size_t ft = (size_t)f * T + t0 + t;
         double s = 0.0;
         for (int i = 0; i < N; ++i) {
-            double bw = wbar[i] * r.A[(size_t)i * r.F * T + ft];
+            const double bw = wbar[i] * r.A[(size_t)i * r.F * T + ft];
             s += bw;
-            vmax = fmax(vmax, fabs(bw));
+            vmax = fmaxf(vmax, fabsf((float)bw));
             if (MODE == 2) r.Bp32[(size_t)i * r.F * T + ft] = (float)bw;
         }
-        double d = r.data[ft] - s - r.t_cmb * r.B[ft];
+        const double d = r.data[ft] - s - r.t_cmb * r.B[ft];
         dref[t] = d;
-        vmax = fmax(vmax, fabs(d));
+        vmax = fmaxf(vmax, fabsf((float)d));
         if (MODE == 2) r.dref32[ft] = (float)d;
     }
     if (MODE >= 2) return;
-    vmax = block_reduce(vmax, OpMax(), sh);
+    for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = vmax;
+    __syncthreads();
     if (threadIdx.x == 0) {
-        s_scaleB = pow2_exponent_for(vmax);
+        float v = sh[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = fmaxf(v, (float)sh[w]);
+        s_scaleB = pow2_exponent_for((double)v);
         r.scaleB[fc] = s_scaleB;
     }
     __syncthreads();
-    const double sB = ldexp(1.0, s_scaleB);
-    // --- operand tile: one 16-byte chunk (8 values of k) per (split, kc, t) ---
+    const float sB = ldexpf(1.0f, s_scaleB);
+    // --- operand tile: one 16-byte chunk (8 values of k) per (split, kc, t).
+    // Region rows in FP32 (wbar_k A[k,f,t] to 24 bits, finer than the 22-bit
+    // split), the dref row from its FP64 value. ---
     const int Kp = r.Kp, Tcp = r.Tc_pad, nkc = Kp / 8;
     uint4 *tile = reinterpret_cast<uint4 *>(r.tiles + (size_t)fc * r.tile_rows * 128);
+    float *wbar32 = reinterpret_cast<float *>(dref + r.Tc_pad);     // [N]
+    for (int i = threadIdx.x; i < N; i += blockDim.x) wbar32[i] = (float)wbar[i];
+    __syncthreads();
     for (int j = threadIdx.x; j < nkc * Tcp; j += blockDim.x) {
         const int kc = j / Tcp, t = j % Tcp;
-        uint16_t hi[8], mid[8];
+        float v[8];
         for (int e = 0; e < 8; ++e) {
             const int k = kc * 8 + e;
-            double v = 0.0;
+            float x = 0.0f;
             if (t < tn) {
-                if (k < N) v = wbar[k] * r.A[(size_t)k * r.F * T + (size_t)f * T + t0 + t];
-                else if (k == N) v = 1.0;
-                else if (k == N + 1) v = dref[t];
+                if (k < N) x = wbar32[k] * r.A32[(size_t)k * r.F * T + (size_t)f * T + t0 + t] * sB;
+                else if (k == Kp - 2) x = sB;
+                else if (k == Kp - 1) x = (float)(dref[t] * (double)sB);
             }
-            v *= sB;
-            hi[e] = to_bits<MODE == 1>(v);
-            mid[e] = to_bits<MODE == 1>(v - from_bits<MODE == 1>(hi[e]));
+            v[e] = x;
         }
-        uint4 H, M;
-        H.x = hi[0] | ((uint32_t)hi[1] << 16); H.y = hi[2] | ((uint32_t)hi[3] << 16);
-        H.z = hi[4] | ((uint32_t)hi[5] << 16); H.w = hi[6] | ((uint32_t)hi[7] << 16);
-        M.x = mid[0] | ((uint32_t)mid[1] << 16); M.y = mid[2] | ((uint32_t)mid[3] << 16);
-        M.z = mid[4] | ((uint32_t)mid[5] << 16); M.w = mid[6] | ((uint32_t)mid[7] << 16);
-        tile[(size_t)kc * Tcp + t] = H;                      // split 0 (hi)
-        tile[(size_t)(nkc + kc) * Tcp + t] = M;              // split 1 (mid)
+        uint32_t H[4], M[4];
+        for (int e = 0; e < 8; e += 2) {
+            H[e / 2] = pack_pair<MODE == 1>(v[e], v[e + 1]);
+            const float2 h = unpack_pair<MODE == 1>(H[e / 2]);
+            M[e / 2] = pack_pair<MODE == 1>(v[e] - h.x, v[e + 1] - h.y);
+        }
+        tile[(size_t)kc * Tcp + t] = make_uint4(H[0], H[1], H[2], H[3]);                 // split 0 (hi)
+        tile[(size_t)(nkc + kc) * Tcp + t] = make_uint4(M[0], M[1], M[2], M[3]);         // split 1 (mid)
     }
 }
 
@@ -440,9 +497,11 @@ __global__ void resid_to_model_kernel(const ReqDesc *__restrict__ req, const flo
 }  // namespace
 
 cudaError_t launch_prep(const ReqDesc *h_reqs, const ReqDesc *d_reqs, int n_reqs, int precision,
-                        int max_stat_blocks, int max_F_chunks, cudaStream_t stream) {
+                        int max_stat_blocks, int max_F_chunks, int max_tiles, cudaStream_t stream) {
+    int maxN0 = 0;
+    for (int k = 0; k < n_reqs; ++k) maxN0 = maxN0 > h_reqs[k].N ? maxN0 : h_reqs[k].N;
     dim3 g1(max_stat_blocks, n_reqs);
-    prep_stats_kernel<<<g1, PREP_THREADS, 0, stream>>>(d_reqs);
+    prep_stats_kernel<<<g1, PREP_THREADS, sizeof(float) * (PREP_THREADS / 32) * (3 * (size_t)maxN0 + 2), stream>>>(d_reqs);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     prep_finalize_kernel<<<n_reqs, PREP_THREADS, 0, stream>>>(d_reqs);
@@ -453,8 +512,9 @@ cudaError_t launch_prep(const ReqDesc *h_reqs, const ReqDesc *d_reqs, int n_reqs
         maxN = maxN > h_reqs[k].N ? maxN : h_reqs[k].N;
         maxTcp = maxTcp > h_reqs[k].Tc_pad ? maxTcp : h_reqs[k].Tc_pad;
     }
-    const size_t sm = sizeof(double) * ((size_t)maxN + maxTcp);
-    dim3 g2(max_F_chunks, n_reqs);
+    const size_t sm = sizeof(double) * ((size_t)maxN + maxTcp) + sizeof(float) * (size_t)maxN;
+    const bool tc = precision == FG21_PREC_FP16X3 || precision == FG21_PREC_BF16X3;
+    dim3 g2(max_F_chunks + (tc ? max_tiles : 0), n_reqs);
     switch (precision) {
         case FG21_PREC_FP16X3: prep_tiles_kernel<0><<<g2, PREP_THREADS, sm, stream>>>(d_reqs); break;
         case FG21_PREC_BF16X3: prep_tiles_kernel<1><<<g2, PREP_THREADS, sm, stream>>>(d_reqs); break;

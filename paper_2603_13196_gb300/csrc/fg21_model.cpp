@@ -183,6 +183,7 @@ ReqLayout request_layout(const ReqDesc &r, int precision) {
     L.Bp32 = delta ? align256(sizeof(float) * (size_t)r.N * r.F * r.T) : 0;
     L.dref32 = delta ? align256(sizeof(float) * (size_t)r.F * r.T) : 0;
     L.partials = align256(sizeof(float2) * (size_t)r.P * r.G);
+    L.pts32 = tc ? align256(sizeof(float) * (size_t)r.n_tiles * (r.Kp + 4) * TILE_M) : 0;
     L.tiles = tc ? (size_t)r.F * r.n_tchunks * r.tile_rows * 128 : 0;
     return L;
 }
@@ -208,7 +209,7 @@ int enqueue_requests(Workspace &ws, std::vector<ReqDesc> &reqs, int precision, c
     if (rc) return rc;
     char *p = ws.dev;
     int64_t item = 0, row = 0, pts = 0;
-    int kp_max = 16, tc_max = 16, max_blocks = 1, max_fchunks = 1;
+    int kp_max = 16, tc_max = 16, max_blocks = 1, max_fchunks = 1, max_tiles = 1;
     for (int k = 0; k < n; ++k) {
         ReqDesc &r = reqs[k];
         const ReqLayout &L = lay[k];
@@ -222,6 +223,7 @@ int enqueue_requests(Workspace &ws, std::vector<ReqDesc> &reqs, int precision, c
         r.Bp32 = L.Bp32 ? (float *)p : nullptr; p += L.Bp32;
         r.dref32 = L.dref32 ? (float *)p : nullptr; p += L.dref32;
         r.partials = (float2 *)p; p += L.partials;
+        r.pts32 = L.pts32 ? (float *)p : nullptr; p += L.pts32;
         r.item_begin = item;
         item += (int64_t)r.n_tiles * r.G;
         r.pt_begin = pts;
@@ -235,6 +237,7 @@ int enqueue_requests(Workspace &ws, std::vector<ReqDesc> &reqs, int precision, c
         tc_max = std::max(tc_max, r.Tc_pad);
         max_blocks = std::max(max_blocks, r.n_stat_blocks);
         max_fchunks = std::max(max_fchunks, r.F * r.n_tchunks);
+        max_tiles = std::max(max_tiles, r.n_tiles);
     }
     if (tc && kp_max > KP_MAX)
         return set_error(FG21_E_RANGE, "N = %d regions exceeds the tensor-core limit %d", kp_max - 2,
@@ -244,7 +247,7 @@ int enqueue_requests(Workspace &ws, std::vector<ReqDesc> &reqs, int precision, c
     FG21_CUDA_TRY(cudaMemcpyAsync(ws.d_reqs, ws.pinned, sizeof(ReqDesc) * n, cudaMemcpyHostToDevice, stream));
     cudaEvent_t *ev = ws.timing_slot();
     if (ev) FG21_CUDA_TRY(cudaEventRecord(ev[0], stream));
-    FG21_CUDA_TRY(launch_prep(reqs.data(), ws.d_reqs, n, precision, max_blocks, max_fchunks, stream));
+    FG21_CUDA_TRY(launch_prep(reqs.data(), ws.d_reqs, n, precision, max_blocks, max_fchunks, max_tiles, stream));
     if (ev) FG21_CUDA_TRY(cudaEventRecord(ev[1], stream));
     if (tc) {
         TcLaunch L;
@@ -254,6 +257,9 @@ int enqueue_requests(Workspace &ws, std::vector<ReqDesc> &reqs, int precision, c
         L.kp_max = kp_max;
         L.tc_pad_max = tc_max;
         L.precision = precision;
+        std::vector<int64_t> rows_of(n);
+        for (int k = 0; k < n; ++k) rows_of[k] = reqs[k].tile_rows;
+        L.box_rows = tc_box_rows(rows_of.data(), n);
         L.arena = ws.arena;
         L.arena_rows = row;
         L.status = ws.d_status;
@@ -439,7 +445,7 @@ int fg21_model_info(const fg21_model *m, int32_t *N, int32_t *F, int32_t *T, int
     if (F) *F = m->F;
     if (T) *T = m->T;
     if (n_empty) *n_empty = m->n_empty;
-    if (device_bytes) *device_bytes = m->resident_bytes + m->ws.bytes();
+    if (device_bytes) *device_bytes = m->resident_bytes;
     return FG21_OK;
 }
 

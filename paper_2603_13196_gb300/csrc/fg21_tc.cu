@@ -49,7 +49,8 @@ constexpr int NUM_THREADS = 320;
 constexpr int NB_STAGES = 4;     // operand-tile (TMA) stages
 constexpr int NW_STAGES = 2;     // weight stages
 constexpr int NACC = 2;          // accumulator stages in tensor memory
-constexpr int BOX_ROWS = 8;      // rows of 128 bytes per TMA box
+// TMA boxes are 64 x box_rows 16-bit values (128-byte rows); box_rows divides
+// every request's tile height (a multiple of 8, at most 256)
 constexpr uint64_t WAIT_LIMIT_NS = 4000000000ull;
 
 struct __align__(8) Barriers {
@@ -196,15 +197,42 @@ __device__ __forceinline__ Item decode_item(const ReqDesc *__restrict__ reqs, in
 }
 
 // ----------------------------------------------------- weight generation
+// Packed FP32 pairs (fma/mul/sub .f32x2): one instruction for two lanes' worth
+// of the Horner chains and splits.
+__device__ __forceinline__ uint64_t pk2(float a, float b) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2(uint64_t v, float &a, float &b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 // expm1 by its Taylor series x (1 + x/2! + ... + x^(D-1)/D!), scaled by 2^sW
-// through the coefficients c[j] = 2^sW / j!.  Relative truncation error
-// |x|^D / (D+1)!: D = 3 for |x| <= 0.01, 5 for |x| <= 0.1, 8 for |x| <= 0.55.
+// through the coefficient pairs c2[j] = (2^sW / j!, 2^sW / j!), on two
+// arguments at once.  Relative truncation error |x|^D / (D+1)!: D = 3 for
+// |x| <= 0.01, 5 for |x| <= 0.1, 8 for |x| <= 0.55.
 template <int D>
-__device__ __forceinline__ float em1_series(float x, const float *c) {
-    float p = c[D];
+__device__ __forceinline__ uint64_t em1_series2(uint64_t x2, const uint64_t *c2) {
+    uint64_t p = c2[D];
 #pragma unroll
-    for (int j = D - 1; j >= 1; --j) p = fmaf(p, x, c[j]);
-    return p * x;
+    for (int j = D - 1; j >= 1; --j) p = fma2(p, x2, c2[j]);
+    return mul2(p, x2);
 }
 // Larger |x|: Cody-Waite reduction x = k ln2 + r (ln2 split into a 12-bit-short
 // head and a tail), expm1(r) by the degree-7 series (|r| <= ln2/2), then
@@ -213,7 +241,10 @@ __device__ __forceinline__ float em1_reduced(float x, const float *cu, float sW)
     const float k = rintf(x * 1.4426950408889634f);
     float r = fmaf(-k, 0.693115234375f, x);
     r = fmaf(-k, 3.194618329871446e-05f, r);
-    const float p = em1_series<7>(r, cu);
+    float p = cu[7];
+#pragma unroll
+    for (int j = 6; j >= 1; --j) p = fmaf(p, r, cu[j]);
+    p *= r;
     const int ki = max(-100, min(100, (int)k));
     const float two_k = ldexpf(1.0f, ki);
     return fmaf(p, two_k * sW, (two_k - 1.0f) * sW);
@@ -244,39 +275,53 @@ template <bool BF16>
 __device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t &mid) {
     hi = pack2<BF16>(a, b);
     const float2 h = unpack2<BF16>(hi);
-    mid = pack2<BF16>(a - h.x, b - h.y);
+    float ra, rb;
+    upk2(sub2(pk2(a, b), pk2(h.x, h.y)), ra, rb);
+    mid = pack2<BF16>(ra, rb);
 }
 
-// One channel's weight row of point m into weight stage `wbuf`:
-// layout [split][kc][m][8 values], split stride KP/8 * 2048 bytes.
-template <int KP, bool BF16, int MODE>   // MODE: 3, 5, 8 = series degree; 0 = reduced
-__device__ __forceinline__ void gen_row(char *wbuf, int m, const float *dlt, int N, float nL, float s21,
-                                        float sW, const float *c, const float *cu) {
+// One channel's weight row of point m into weight stage `wbuf`, for a request
+// whose padded K is KPR (<= KP): columns k < KPR-2 carry the regions (zero
+// deviation -> zero weight beyond N), column KPR-2 the trough, KPR-1 the -1
+// that multiplies dref.  Layout [split][kc][m][8 values], split stride
+// KP/8 * 2048 bytes.
+template <int KPR, int KP, bool BF16, int MODE>   // MODE: 3, 5, 8 = series degree; 0 = reduced
+__device__ __forceinline__ void gen_row(char *wbuf, int m, const float *dlt, float nL, float s21, float sW,
+                                        const uint64_t *c2, const float *cu) {
+    const uint64_t nL2 = pk2(nL, nL);
 #pragma unroll
-    for (int kc = 0; kc < KP / 8; ++kc) {
-        float v[8];
+    for (int kc = 0; kc < KPR / 8; ++kc) {
+        uint32_t H[4], M[4];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
+        for (int e = 0; e < 8; e += 2) {
             const int k = kc * 8 + e;
-            float val = 0.0f;
-            if (k < N) {
-                const float x = dlt[k] * nL;
-                if (MODE == 0) val = em1_reduced(x, cu, sW);
-                else val = em1_series<MODE>(x, c);
-            } else if (k == N) {
-                val = s21;
-            } else if (k == N + 1) {
-                val = -sW;
+            float a, b;
+            if (k < KPR - 2) {
+                if (MODE == 0) {
+                    a = em1_reduced(dlt[k] * nL, cu, sW);
+                    b = em1_reduced(dlt[k + 1] * nL, cu, sW);
+                } else {
+                    upk2(em1_series2<MODE>(mul2(pk2(dlt[k], dlt[k + 1]), nL2), c2), a, b);
+                }
+            } else {
+                a = s21;
+                b = -sW;
             }
-            v[e] = val;
+            split2<BF16>(a, b, H[e / 2], M[e / 2]);
         }
-        uint4 H, M;
-        split2<BF16>(v[0], v[1], H.x, M.x);
-        split2<BF16>(v[2], v[3], H.y, M.y);
-        split2<BF16>(v[4], v[5], H.z, M.z);
-        split2<BF16>(v[6], v[7], H.w, M.w);
-        *reinterpret_cast<uint4 *>(wbuf + kc * 2048 + m * 16) = H;
-        *reinterpret_cast<uint4 *>(wbuf + (KP / 8) * 2048 + kc * 2048 + m * 16) = M;
+        *reinterpret_cast<uint4 *>(wbuf + kc * 2048 + m * 16) = make_uint4(H[0], H[1], H[2], H[3]);
+        *reinterpret_cast<uint4 *>(wbuf + (KP / 8) * 2048 + kc * 2048 + m * 16) = make_uint4(M[0], M[1], M[2], M[3]);
+    }
+}
+
+template <int KPR, int KP, bool BF16>
+__device__ __forceinline__ void gen_row_mode(int mode, char *wbuf, int m, const float *dlt, float nL, float s21,
+                                             float sW, const uint64_t *c2, const float *cu) {
+    switch (mode) {
+        case 3: gen_row<KPR, KP, BF16, 3>(wbuf, m, dlt, nL, s21, sW, c2, cu); break;
+        case 5: gen_row<KPR, KP, BF16, 5>(wbuf, m, dlt, nL, s21, sW, c2, cu); break;
+        case 8: gen_row<KPR, KP, BF16, 8>(wbuf, m, dlt, nL, s21, sW, c2, cu); break;
+        default: gen_row<KPR, KP, BF16, 0>(wbuf, m, dlt, nL, s21, sW, c2, cu); break;
     }
 }
 
@@ -289,6 +334,7 @@ struct Params {
     uint32_t tmem_cols;    // allocated tensor-memory columns
     unsigned *status;
     float *resid;          // validation mode: residuals [P][F][T] of request 0, else null
+    int box_rows;          // rows per TMA box
 };
 
 template <int KP, bool BF16>
@@ -307,13 +353,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             mbar_init(&S->b_full[s], 1);
             mbar_init(&S->b_empty[s], 1);
         }
+        // weight stages and accumulators are handed back by one arrival per
+        // warp (4 generator / 4 epilogue warps), after a __syncwarp
         for (int s = 0; s < NW_STAGES; ++s) {
-            mbar_init(&S->w_full[s], 128);
+            mbar_init(&S->w_full[s], 4);
             mbar_init(&S->w_empty[s], 1);
         }
         for (int s = 0; s < NACC; ++s) {
             mbar_init(&S->acc_full[s], 1);
-            mbar_init(&S->acc_empty[s], 128);
+            mbar_init(&S->acc_empty[s], 4);
         }
         mbar_init(&S->drain, 1);
         S->abort_flag = 0;
@@ -339,50 +387,53 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         for (int64_t item = blockIdx.x; item < prm.n_items && ok; item += gridDim.x) {
             const Item it = decode_item(reqs, prm.n_reqs, item);
             const ReqDesc &r = reqs[it.req];
-            const int N = r.N;
-            const int64_t p = (int64_t)it.tile * 128 + m;
+            const int Kpr = r.Kp;
+            const float *__restrict__ pts = r.pts32 + (size_t)it.tile * (Kpr + 4) * 128 + m;
+            const float *__restrict__ nLp = r.nL32;
+            const float *__restrict__ nup = r.nu32;
             float dlt[KP];
 #pragma unroll
-            for (int k = 0; k < KP; ++k) dlt[k] = 0.0f;
-            float a21 = 0.0f, nu21 = 0.0f, inv2s2 = 0.0f;
-            if (p < r.P) {
-                const double *th = r.params + p * (N + 4);
-#pragma unroll
-                for (int k = 0; k < KP; ++k)
-                    if (k < N) dlt[k] = (float)(th[k] - r.beta_bar[k]);
-                a21 = (float)th[N];
-                nu21 = (float)th[N + 1];
-                inv2s2 = (float)(1.0 / (2.0 * th[N + 2] * th[N + 2]));
-            }
+            for (int k = 0; k < KP; ++k) dlt[k] = k < Kpr - 2 ? pts[(size_t)k * 128] : 0.0f;
+            const float a21 = pts[(size_t)(Kpr - 2) * 128];
+            const float nu21 = pts[(size_t)(Kpr - 1) * 128];
+            const float inv2s2 = pts[(size_t)Kpr * 128];
             const float sW = ldexpf(1.0f, *r.scaleW);
             const double xmax = r.req_stats[1];
             const int mode = xmax <= 0.01 ? 3 : xmax <= 0.1 ? 5 : xmax <= 0.55 ? 8 : 0;
-            float c[10], cu[10];
+            uint64_t c2[10];
+            float cu[10];
             {
                 float fact = 1.0f;
-                c[0] = cu[0] = 0.0f;
+                cu[0] = 0.0f;
+                c2[0] = 0;
 #pragma unroll
                 for (int j = 1; j < 10; ++j) {
                     fact *= (float)j;
                     cu[j] = 1.0f / fact;
-                    c[j] = cu[j] * sW;
+                    c2[j] = pk2(cu[j] * sW, cu[j] * sW);
                 }
             }
+            float nL_next = __ldg(nLp + it.f0), nu_next = __ldg(nup + it.f0);
             for (int f = it.f0; f < it.f1; ++f) {
+                const float nL = nL_next, nuf = nu_next;
+                if (f + 1 < it.f1) {
+                    nL_next = __ldg(nLp + f + 1);
+                    nu_next = __ldg(nup + f + 1);
+                }
                 const uint32_t ws = w_stage % NW_STAGES, wph = (w_stage / NW_STAGES) & 1;
                 if (!mbar_wait(&S->w_empty[ws], wph ^ 1, S, prm.status, STATUS_TIMEOUT_GEN)) { ok = false; break; }
-                const float nL = r.nL32[f];
-                const float dnu = r.nu32[f] - nu21;
+                const float dnu = nuf - nu21;
                 const float s21 = sW * a21 * __expf(-dnu * dnu * inv2s2);
                 char *wbuf = w_stages + ws * W_STAGE_BYTES;
-                switch (mode) {
-                    case 3: gen_row<KP, BF16, 3>(wbuf, m, dlt, N, nL, s21, sW, c, cu); break;
-                    case 5: gen_row<KP, BF16, 5>(wbuf, m, dlt, N, nL, s21, sW, c, cu); break;
-                    case 8: gen_row<KP, BF16, 8>(wbuf, m, dlt, N, nL, s21, sW, c, cu); break;
-                    default: gen_row<KP, BF16, 0>(wbuf, m, dlt, N, nL, s21, sW, c, cu); break;
-                }
+                // the request's padded K (a multiple of 16, <= KP) fixes where the
+                // trough and -1 columns sit; it must match its operand tiles
+                if (Kpr == 16) gen_row_mode<16, KP, BF16>(mode, wbuf, m, dlt, nL, s21, sW, c2, cu);
+                else if (KP >= 32 && Kpr == 32) gen_row_mode<(KP >= 32 ? 32 : 16), KP, BF16>(mode, wbuf, m, dlt, nL, s21, sW, c2, cu);
+                else if (KP >= 48 && Kpr == 48) gen_row_mode<(KP >= 48 ? 48 : 16), KP, BF16>(mode, wbuf, m, dlt, nL, s21, sW, c2, cu);
+                else if (KP >= 64 && Kpr == 64) gen_row_mode<(KP >= 64 ? 64 : 16), KP, BF16>(mode, wbuf, m, dlt, nL, s21, sW, c2, cu);
                 fence_proxy_async_smem();
-                mbar_arrive(&S->w_full[ws]);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&S->w_full[ws]);
                 ++w_stage;
             }
         }
@@ -397,42 +448,65 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             const ReqDesc &r = reqs[it.req];
             const int64_t p = (int64_t)it.tile * 128 + m;
             const int sWexp = *r.scaleW;
+            const int nch = r.n_tchunks, Tc = r.Tc, T = r.T, F = r.F;
+            const int nblk = r.Tc_pad / 16;
+            const int *__restrict__ scaleB = r.scaleB;
+            const bool in = p < r.P;
             float qs = 0.0f, qc = 0.0f;
+            int sb_next = __ldg(scaleB + it.f0 * nch);
             for (int f = it.f0; f < it.f1 && ok; ++f) {
                 float qf = 0.0f;
-                for (int cch = 0; cch < r.n_tchunks; ++cch) {
+                for (int cch = 0; cch < nch; ++cch) {
+                    const int fc = f * nch + cch;
+                    const int sb = sb_next;
+                    if (fc + 1 < it.f1 * nch) sb_next = __ldg(scaleB + fc + 1);
                     const uint32_t a = acc_stage % NACC, aph = (acc_stage / NACC) & 1;
                     if (!mbar_wait(&S->acc_full[a], aph, S, prm.status, STATUS_TIMEOUT_EPI)) { ok = false; break; }
                     tc_fence_after();
-                    const int fc = f * r.n_tchunks + cch;
-                    const int t0 = cch * r.Tc, tn = min(r.Tc, r.T - t0);
-                    const float unscale = ldexpf(1.0f, -(sWexp + r.scaleB[fc]));
+                    const float unscale = ldexpf(1.0f, -(sWexp + sb));
                     const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + a * prm.acc_cols;
-                    float q = 0.0f;
-                    for (int col = 0; col < r.Tc_pad; col += 16) {
-                        float v[16];
-                        tmem_ld16(taddr + col, v);
+                    uint64_t q2 = 0;
+                    for (int b0 = 0; b0 < nblk; b0 += 4) {
+                        float v[4][16];
+                        tmem_ld16(taddr + b0 * 16, v[0]);
+                        if (b0 + 1 < nblk) tmem_ld16(taddr + (b0 + 1) * 16, v[1]);
+                        if (b0 + 2 < nblk) tmem_ld16(taddr + (b0 + 2) * 16, v[2]);
+                        if (b0 + 3 < nblk) tmem_ld16(taddr + (b0 + 3) * 16, v[3]);
                         tmem_ld_wait();
                         if (prm.resid) {
-                            if (p < r.P) {
+                            const int t0 = cch * Tc, tn = min(Tc, T - t0);
+                            if (in) {
+                                for (int bb = 0; bb < 4 && b0 + bb < nblk; ++bb)
 #pragma unroll
-                                for (int j = 0; j < 16; ++j)
-                                    if (col + j < tn)
-                                        prm.resid[((size_t)p * r.F + f) * r.T + t0 + col + j] = -v[j] * unscale;
+                                    for (int j = 0; j < 16; ++j) {
+                                        const int t = (b0 + bb) * 16 + j;
+                                        if (t < tn) prm.resid[((size_t)p * F + f) * T + t0 + t] = -v[bb][j] * unscale;
+                                    }
                             }
                         } else {
 #pragma unroll
-                            for (int j = 0; j < 16; ++j) q = fmaf(v[j], v[j], q);
+                            for (int bb = 0; bb < 4; ++bb) {
+                                if (b0 + bb < nblk) {
+#pragma unroll
+                                    for (int j = 0; j < 16; j += 2) {
+                                        const uint64_t x = pk2(v[bb][j], v[bb][j + 1]);
+                                        q2 = fma2(x, x, q2);
+                                    }
+                                }
+                            }
                         }
                     }
                     tc_fence_before();
-                    mbar_arrive(&S->acc_empty[a]);
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&S->acc_empty[a]);
                     ++acc_stage;
-                    qf += q * unscale * unscale;
+                    float qa, qb;
+                    upk2(q2, qa, qb);
+                    qf += (qa + qb) * unscale * unscale;
                 }
                 kahan_add_dev(qs, qc, qf);
             }
-            if (ok && !prm.resid && p < r.P) r.partials[(size_t)p * r.G + it.g] = make_float2(qs, -qc);
+            if (ok && !prm.resid && in) r.partials[(size_t)p * r.G + it.g] = make_float2(qs, -qc);
         }
     } else if (warp == 8) {
         // ====================================================== TMA producer
@@ -450,7 +524,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                         mbar_arrive_expect_tx(&S->b_full[bs], (uint32_t)rows * 128u);
                         const int64_t row0 = r.tile_row0 + (int64_t)(f * r.n_tchunks + cch) * rows;
                         char *dst = b_stages + bs * prm.b_stage_bytes;
-                        for (int j = 0; j < rows; j += BOX_ROWS)
+                        for (int j = 0; j < rows; j += prm.box_rows)
                             tma_load_2d(dst + j * 128, &tmap, 0, (int)(row0 + j), &S->b_full[bs]);
                         ++b_stage;
                     }
@@ -561,13 +635,14 @@ cudaError_t launch_kp(const CUtensorMap &map, const Params &prm, int grid, size_
 
 cudaError_t launch_common(const ReqDesc *d_reqs, int n_reqs, int64_t n_items, int kp_max, int tc_pad_max,
                           int precision, void *arena, int64_t arena_rows, unsigned *status, float *resid,
-                          int num_sms, cudaStream_t stream) {
+                          int box_rows, int num_sms, cudaStream_t stream) {
     if (n_items == 0) return cudaSuccess;
     if (tc_map_init() != FG21_OK) return cudaErrorNotSupported;
     CUtensorMap map;
     cuuint64_t gdim[2] = {64, (cuuint64_t)arena_rows};
     cuuint64_t gstride[1] = {128};
-    cuuint32_t box[2] = {64, BOX_ROWS};
+    if (box_rows < 8 || box_rows > 256 || box_rows % 8) return cudaErrorInvalidValue;
+    cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
     cuuint32_t estride[2] = {1, 1};
     CUresult cr = g_encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, arena, gdim, gstride, box, estride,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -584,6 +659,7 @@ cudaError_t launch_common(const ReqDesc *d_reqs, int n_reqs, int64_t n_items, in
     prm.tmem_cols = cols;
     prm.status = status;
     prm.resid = resid;
+    prm.box_rows = box_rows;
     const int kp = kp_max <= 16 ? 16 : kp_max <= 32 ? 32 : 64;
     // at least ~120 KB so that a single CTA (and its tensor memory) owns each SM
     size_t sm = smem_bytes(kp, prm.b_stage_bytes);
@@ -612,9 +688,29 @@ int tc_map_init() {
     return g_encode_rc;
 }
 
+int tc_box_rows(const int64_t *tile_rows, int n) {
+    int64_t g = 0;
+    for (int k = 0; k < n; ++k) {
+        int64_t a = tile_rows[k], b = g;
+        while (b) {
+            int64_t t = a % b;
+            a = b;
+            b = t;
+        }
+        g = a;
+    }
+    int64_t box = 8;
+    for (int64_t c = 256; c >= 8; c -= 8)
+        if (g % c == 0) {
+            box = c;
+            break;
+        }
+    return (int)box;
+}
+
 cudaError_t launch_tc(const TcLaunch &L, int num_sms, cudaStream_t stream) {
     return launch_common(L.d_reqs, L.n_reqs, L.n_items, L.kp_max, L.tc_pad_max, L.precision, L.arena,
-                         L.arena_rows, L.status, nullptr, num_sms, stream);
+                         L.arena_rows, L.status, nullptr, L.box_rows, num_sms, stream);
 }
 
 cudaError_t launch_tc_residuals(const ReqDesc *h_req, const ReqDesc *d_req, int precision, float *resid,
@@ -629,7 +725,7 @@ cudaError_t launch_tc_residuals(const ReqDesc *h_req, const ReqDesc *d_req, int 
     const int64_t rows = h_req->tile_row0 + (int64_t)h_req->F * h_req->n_tchunks * h_req->tile_rows;
     const int64_t items = (int64_t)h_req->n_tiles * h_req->G;
     return launch_common(d_req, 1, items, h_req->Kp, h_req->Tc_pad, precision, arena, rows, h_req->status, resid,
-                         sms, stream);
+                         tc_box_rows(&h_req->tile_rows, 1), sms, stream);
 }
 
 }  // namespace fg21

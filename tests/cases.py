@@ -4,13 +4,10 @@ Every expected value comes from the FP64 oracle (oracle/); inputs come from
 paper_2603_13196_gb300.inputs.  Nothing here calls the CUDA library.
 
 Tolerances (derived from the arithmetic; see the design notes):
-  * logL, any point:  |dlogL| <= 1e-2 + REL_CHI2[prec] * chi2 / (2 sigma_n^2)
-    The data term chi2/(2 sigma^2) is what carries rounding: each residual r is
-    formed from terms of size |S| (the point's departure from the request
-    reference, or the whole foreground for the direct form) with relative
-    error eta, so |d(r^2)| <= 2 |r| eta |S|; summed, the error is a fixed
-    fraction of the data term when |S| ~ |r| (far-from-data points) and far
-    below 1e-2 nats when |r| ~ sigma (points at the posterior).
+  * logL, any point: |dlogL| <= 1e-2 + C u sum_{f,t} |r| (S + |r|) / sigma_n^2
+    (logl_tolerance): each residual r is formed from terms of size S (the
+    point's departure from the request reference, or the whole foreground for
+    the plain form) with relative error ~u, and d(r^2 / 2 sigma^2) = r dr / sigma^2.
   * logL at near-posterior points (chi2 / (F T sigma^2) <= 10): |dlogL| <= 1e-2.
   * T_model per (p, f, t) at near-posterior points: |dT| <= 1e-3 K.
   * T_model per (p, f, t), any point: |dT| <= 1e-3 K + REL_T[prec] * scale, the
@@ -32,17 +29,17 @@ from paper_2603_13196_gb300 import inputs as I
 # (hi + mid) keeps 22 significand bits for FP16 (2 x 11) and 16 for BF16
 # (2 x 8); the SIMT forms are FP32 (24 bits).
 U = {"fp16x3": 2.0 ** -22, "bf16x3": 2.0 ** -16, "fp32_delta": 2.0 ** -24, "fp32_direct": 2.0 ** -24}
-# relative error of the data term chi2/(2 sigma^2) allowed per precision:
-# d(r^2)/r^2 <= 2 eta |S|/|r|, eta <= 3u (three split products) plus the FP32
-# accumulation; for far-from-data points |S| ~ |r| -> 8u.  The plain FP32 form
-# carries the whole foreground (|M| >> |r|), so it gets no such bound: it is
-# the comparator and its looser limit only guards against gross failure.
-REL_CHI2 = {"fp16x3": 8 * U["fp16x3"], "bf16x3": 8 * U["bf16x3"], "fp32_delta": 8 * U["fp32_delta"],
-            "fp32_direct": 1e-4}
-# T_model per (p,f,t), relative to the magnitude the form carries (see
-# t_model_scale): split products 3u plus FP32 accumulation over K ~ 100 terms.
-REL_T = {"fp16x3": 16 * U["fp16x3"], "bf16x3": 16 * U["bf16x3"], "fp32_delta": 16 * U["fp32_delta"],
-         "fp32_direct": 16 * U["fp32_direct"]}
+# Per-point logL tolerance (first order in the rounding of r):
+#   |dlogL| <= 1e-2 + C u sum_{f,t} |r| (S + |r|) / sigma_n^2
+# r = D - M (oracle), S the magnitude the form's arithmetic carries at each
+# (f, t): the departure of the point from the request reference (sum_i |A_i|
+# |w(beta_p,i) - w(bbar_i)|) for the reference-subtracted forms, the whole
+# foreground for the plain form; dref is carried too (|dref| <= S + |r| +
+# |T21|).  C = 16 covers the three split products (3u each operand pair) and
+# the FP32 accumulation over K <= 100 terms with headroom.
+C_TOL = 16.0
+# T_model per (p,f,t), relative to the same magnitude (see t_model_scale).
+REL_T = {k: C_TOL * v for k, v in U.items()}
 
 
 @functools.lru_cache(maxsize=None)
@@ -84,8 +81,24 @@ def expected(m, obs, data, params):
     return L, c2 / (2.0 * sig * sig)
 
 
-def logl_tolerance(prec: str, data_term: np.ndarray) -> np.ndarray:
-    return 1e-2 + REL_CHI2[prec] * np.abs(data_term)
+def reference_beta(params, N):
+    """The kernels' reference point: mean beta_i over the request's valid points."""
+    ok = np.all(np.isfinite(params), axis=1) & (params[:, N + 3] > 0) & (params[:, N + 2] != 0)
+    return params[ok, :N].mean(axis=0) if ok.any() else np.zeros(N)
+
+
+def logl_tolerance(prec: str, m, obs, data, params) -> np.ndarray:
+    """Per-point bound on |dlogL| for precision `prec` (see the module notes)."""
+    N = m.A.shape[0]
+    M = O.fast_model(m.A, m.B, obs, params)
+    r = np.abs(data[None] - M)
+    if prec == "fp32_direct":
+        # the plain form rounds each of its N + 4 terms (A32, the FP32 power
+        # law, the products, T_CMB B, the trough) at the size of the foreground
+        S, C = np.abs(M), 4.0 * (N + 4)
+    else:
+        S, C = foreground_departure(m, obs, params, reference_beta(params, N)), C_TOL
+    return 1e-2 + C * U[prec] * np.sum(r * (S + r), axis=(1, 2)) / params[:, N + 3] ** 2
 
 
 def foreground_departure(m, obs, params, beta_ref):
@@ -104,7 +117,7 @@ def t_model_scale(prec, m, obs, data, params):
     reference-subtracted forms; the foreground sum for the plain form."""
     if prec == "fp32_direct":
         return foreground_magnitude(m, obs, params)
-    bbar = params[:, :m.A.shape[0]].mean(axis=0)
+    bbar = reference_beta(params, m.A.shape[0])
     r = np.abs(data[None] - O.fast_model(m.A, m.B, obs, params))
     return foreground_departure(m, obs, params, bbar) + r
 

@@ -19,7 +19,7 @@ def test_simt_small(fg21lib, prec, P):
     params = cases.I.prior_draws(P, 5, seed=3)
     got = fg21lib.fg21_loglike_batch(model, params, prec)
     want, dterm = cases.expected(m, obs, data, params)
-    tol = cases.logl_tolerance(prec, dterm)
+    tol = cases.logl_tolerance(prec, m, obs, data, params)
     report(f"simt_small_{prec}_{P}", max_abs=np.max(np.abs(got - want)),
            max_rel_dterm=np.max(np.abs(got - want) / np.abs(dterm)))
     assert np.all(np.abs(got - want) <= tol), cases.fmt_err(prec, got, want, tol)
@@ -33,7 +33,7 @@ def test_simt_workload1(fg21lib, prec):
     fg21lib.fg21_model_set_data(model, data)
     got = fg21lib.fg21_loglike_batch(model, params, prec)
     want, dterm = cases.expected(m, obs, data, params)
-    tol = cases.logl_tolerance(prec, dterm)
+    tol = cases.logl_tolerance(prec, m, obs, data, params)
     report(f"simt_w1_{prec}", max_abs=np.max(np.abs(got - want)),
            max_rel_dterm=np.max(np.abs(got - want) / np.abs(dterm)))
     assert np.all(np.abs(got - want) <= tol), cases.fmt_err(prec, got, want, tol)

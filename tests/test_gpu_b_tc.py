@@ -33,7 +33,7 @@ def test_tc_prior_draws(fg21lib, shape, prec):
     params = cases.I.prior_draws(P, N, seed=N * 7 + T)
     got = fg21lib.fg21_loglike_batch(model, params, prec)
     want, dterm = cases.expected(m, obs, data, params)
-    tol = cases.logl_tolerance(prec, dterm)
+    tol = cases.logl_tolerance(prec, m, obs, data, params)
     report(f"tc_prior_{prec}_{shape}", max_abs=np.max(np.abs(got - want)),
            max_rel_dterm=np.max(np.abs(got - want) / np.abs(dterm)))
     assert np.all(np.abs(got - want) <= tol), cases.fmt_err(prec, got, want, tol)
@@ -57,7 +57,7 @@ def test_near_posterior(fg21lib, prec, dbeta):
     if prec in ("fp16x3", "fp32_delta"):
         near = red <= 10
         assert np.all(err[near] <= 1e-2), cases.fmt_err(prec, got[near], want[near], 1e-2)
-    tol = cases.logl_tolerance(prec, dterm)
+    tol = cases.logl_tolerance(prec, m, obs, data, pts)
     if prec != "fp32_direct":
         assert np.all(err <= tol), cases.fmt_err(prec, got, want, tol)
 
@@ -115,7 +115,7 @@ def test_invalid_points(fg21lib):
         assert fg21lib.fg21_last_invalid_count() == 5
         good = [0, 2, 4, 6, 9]
         want, dterm = cases.expected(m, obs, data, params[good])
-        assert np.all(np.abs(got[good] - want) <= cases.logl_tolerance(prec, dterm))
+        assert np.all(np.abs(got[good] - want) <= cases.logl_tolerance(prec, m, obs, data, params[good]))
 
 
 def test_empty_batch_and_errors(fg21lib):
@@ -139,7 +139,7 @@ def test_workload1_all_precisions(fg21lib):
     want, dterm = cases.expected(m, obs, data, params)
     for prec in ("fp16x3", "bf16x3", "fp32_delta", "fp32_direct"):
         got = fg21lib.fg21_loglike_batch(model, params, prec)
-        tol = cases.logl_tolerance(prec, dterm)
+        tol = cases.logl_tolerance(prec, m, obs, data, params)
         report(f"w1_{prec}", max_abs=np.max(np.abs(got - want)),
                max_rel_dterm=np.max(np.abs(got - want) / np.abs(dterm)))
         assert np.all(np.abs(got - want) <= tol), cases.fmt_err(prec, got, want, tol)
@@ -153,7 +153,7 @@ def test_workload2_full(fg21lib):
     want, dterm = cases.expected(m, obs, data, params)
     for prec in ("fp16x3", "fp32_direct"):
         got = fg21lib.fg21_loglike_batch(model, params, prec)
-        tol = cases.logl_tolerance(prec, dterm)
+        tol = cases.logl_tolerance(prec, m, obs, data, params)
         report(f"w2_{prec}", max_abs=np.max(np.abs(got - want)),
                max_rel_dterm=np.max(np.abs(got - want) / np.abs(dterm)))
         assert np.all(np.abs(got - want) <= tol), cases.fmt_err(prec, got, want, tol)
