@@ -62,7 +62,7 @@ struct ReqDesc {
     int64_t pt_begin;            // first global point index of this request (reduction)
     char *tiles;                 // this request's operand tiles (arena + tile_row0 * 128)
     // workspace (device)
-    double *stat_part;     // [n_stat_blocks][3N + 2]: sum, min, max per region, n_valid, max|A21|
+    float *stat_part;      // [n_stat_blocks][3N + 2]: sum, min, max per region, n_valid, max|A21|
     double *beta_bar;      // [N]
     double *req_stats;     // [4]: n_valid, max|dev|*max|L| (x), max|A21|, reserved
     float *nL32;           // [F] -ln(nu_f/nu0)

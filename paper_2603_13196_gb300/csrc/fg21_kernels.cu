@@ -25,6 +25,7 @@ namespace fg21 {
 namespace {
 
 constexpr int PREP_THREADS = 256;
+constexpr size_t PREP_FIN_SMEM = 32 * 1024;   // shared bytes of the finalize kernel
 
 __device__ __forceinline__ bool point_valid(const double *th, int N) {
     bool ok = true;
@@ -91,7 +92,7 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_stats_kernel(const ReqDesc 
         mine[3 * N + 1] = ma;
     }
     __syncthreads();
-    double *out = r.stat_part + (size_t)blockIdx.x * W;
+    float *out = r.stat_part + (size_t)blockIdx.x * W;
     const int nw = blockDim.x >> 5;
     for (int j = threadIdx.x; j < W; j += blockDim.x) {
         const int kind = j < 3 * N ? j % 3 : (j == 3 * N ? 0 : 2);   // 0 sum, 1 min, 2 max
@@ -100,7 +101,7 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_stats_kernel(const ReqDesc 
             const float x = sh_stats[w * W + j];
             v = kind == 0 ? v + x : kind == 1 ? fminf(v, x) : fmaxf(v, x);
         }
-        out[j] = (double)v;
+        out[j] = v;
     }
 }
 
@@ -145,42 +146,55 @@ __device__ __forceinline__ float2 unpack_pair(uint32_t u) {
 }
 
 // a1, pass 2 (one block per request): the reference point bbar_i = mean of
-// the valid points' beta_i (stat blocks summed in a fixed order), the largest
-// weight argument x = max_i |beta - bbar_i| * max_f |L_f| (which sets the
-// weight polynomial and the power-of-two scale sW of the weight operand), the
-// valid count and max |A21|.
+// the valid points' beta_i, the largest weight argument x = max_i |beta -
+// bbar_i| * max_f |L_f| (which sets the weight polynomial and the
+// power-of-two scale sW of the weight operand), the valid count and max |A21|.
+// The stat-block partials are staged in shared memory by all threads first
+// (coalesced), then combined in a fixed order.
 __global__ void __launch_bounds__(PREP_THREADS) prep_finalize_kernel(const ReqDesc *__restrict__ reqs) {
-    __shared__ double sh[32];
+    extern __shared__ float fin_sm[];
+    __shared__ float red[3][PREP_THREADS / 32];
     const ReqDesc &r = reqs[blockIdx.x];
-    const int N = r.N, nb = r.n_stat_blocks, stride = 3 * N + 2;
-    double nv = 0.0, ma = 0.0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        nv += r.stat_part[(size_t)b * stride + 3 * N];
-        ma = fmax(ma, r.stat_part[(size_t)b * stride + 3 * N + 1]);
-    }
-    // fixed-order: per-thread strided partials, then the deterministic tree
-    nv = block_reduce(nv, OpSum(), sh);
-    ma = block_reduce(ma, OpMax(), sh);
-    double dmax = 0.0;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        double s = 0.0, mn = INFINITY, mx = -INFINITY;
-        for (int b = 0; b < nb; ++b) {
-            const double *q = r.stat_part + (size_t)b * stride + 3 * i;
-            s += q[0];
-            mn = fmin(mn, q[1]);
-            mx = fmax(mx, q[2]);
+    const int N = r.N, nb = r.n_stat_blocks, W = 3 * N + 2;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int chunk = (int)(PREP_FIN_SMEM / sizeof(float)) / W;      // stat blocks per shared-memory pass
+    float s_acc = 0.0f, mn_acc = INFINITY, mx_acc = -INFINITY, nv_acc = 0.0f, ma_acc = 0.0f;
+    const int i = threadIdx.x;          // region of this thread (if < N)
+    for (int b0 = 0; b0 < nb; b0 += chunk) {
+        const int nbc = min(chunk, nb - b0);
+        __syncthreads();
+        for (int j = threadIdx.x; j < nbc * W; j += blockDim.x) fin_sm[j] = r.stat_part[(size_t)b0 * W + j];
+        __syncthreads();
+        for (int b = 0; b < nbc; ++b) {
+            const float *q = fin_sm + b * W;
+            if (i < N) {
+                s_acc += q[3 * i];
+                mn_acc = fminf(mn_acc, q[3 * i + 1]);
+                mx_acc = fmaxf(mx_acc, q[3 * i + 2]);
+            }
+            nv_acc += q[3 * N];
+            ma_acc = fmaxf(ma_acc, q[3 * N + 1]);
         }
-        const double bb = nv > 0.0 ? s / nv : 0.0;
-        r.beta_bar[i] = bb;
-        if (nv > 0.0) dmax = fmax(dmax, fmax(mx - bb, bb - mn));
     }
-    dmax = block_reduce(dmax, OpMax(), sh);
+    const float nv = nv_acc;     // identical in every thread (same order)
+    float dev = 0.0f;
+    if (i < N) {
+        const float bb = nv > 0.0f ? s_acc / nv : 0.0f;
+        r.beta_bar[i] = (double)bb;
+        if (nv > 0.0f) dev = fmaxf(mx_acc - bb, bb - mn_acc);
+    }
+    for (int o = 16; o > 0; o >>= 1) dev = fmaxf(dev, __shfl_xor_sync(0xffffffffu, dev, o));
+    if (lane == 0) red[0][warp] = dev;
+    __syncthreads();
     if (threadIdx.x == 0) {
-        const double x = dmax * r.Lmax;
+        float dmax = 0.0f;
+        for (int w = 0; w < nw; ++w) dmax = fmaxf(dmax, red[0][w]);
+        // a small margin on x covers the FP32 statistics
+        const float x = dmax * (float)r.Lmax * 1.0001f;
         r.req_stats[0] = nv;
         r.req_stats[1] = x;
-        r.req_stats[2] = ma;
-        *r.scaleW = pow2_exponent_for(fmax(fmax(expm1(x), ma), 1.0));
+        r.req_stats[2] = ma_acc;
+        *r.scaleW = pow2_exponent_for(fmax(fmax((double)expm1f(x), (double)ma_acc), 1.0));
     }
 }
 
@@ -245,14 +259,23 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_tiles_kernel(const ReqDesc 
     // --- reference residual dref[t] = D - sum_i wbar_i A_i - T_CMB B (FP64: the
     // foreground cancels here) ---
     float vmax = 1.0f;
+    const size_t istride = (size_t)r.F * T;
     for (int t = threadIdx.x; t < tn; t += blockDim.x) {
         const size_t ft = (size_t)f * T + t0 + t;
         double s = 0.0;
-        for (int i = 0; i < N; ++i) {
-            const double bw = wbar[i] * r.A[(size_t)i * r.F * T + ft];
-            s += bw;
-            vmax = fmaxf(vmax, fabsf((float)bw));
-            if (MODE == 2) r.Bp32[(size_t)i * r.F * T + ft] = (float)bw;
+        for (int i0 = 0; i0 < N; i0 += 8) {
+            double a[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) a[j] = i0 + j < N ? r.A[(size_t)(i0 + j) * istride + ft] : 0.0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                if (i0 + j < N) {
+                    const double bw = wbar[i0 + j] * a[j];
+                    s += bw;
+                    vmax = fmaxf(vmax, fabsf((float)bw));
+                    if (MODE == 2) r.Bp32[(size_t)(i0 + j) * istride + ft] = (float)bw;
+                }
+            }
         }
         const double d = r.data[ft] - s - r.t_cmb * r.B[ft];
         dref[t] = d;
@@ -504,7 +527,7 @@ cudaError_t launch_prep(const ReqDesc *h_reqs, const ReqDesc *d_reqs, int n_reqs
     prep_stats_kernel<<<g1, PREP_THREADS, sizeof(float) * (PREP_THREADS / 32) * (3 * (size_t)maxN0 + 2), stream>>>(d_reqs);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    prep_finalize_kernel<<<n_reqs, PREP_THREADS, 0, stream>>>(d_reqs);
+    prep_finalize_kernel<<<n_reqs, PREP_THREADS, PREP_FIN_SMEM, stream>>>(d_reqs);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     int maxN = 0, maxTcp = 0;

@@ -172,7 +172,7 @@ void plan_request(ReqDesc &r, int precision, int num_sms, int64_t total_tiles) {
 ReqLayout request_layout(const ReqDesc &r, int precision) {
     ReqLayout L{};
     const bool tc = precision == FG21_PREC_FP16X3 || precision == FG21_PREC_BF16X3;
-    L.stat_part = align256(sizeof(double) * (size_t)r.n_stat_blocks * (3 * r.N + 2));
+    L.stat_part = align256(sizeof(float) * (size_t)r.n_stat_blocks * (3 * r.N + 2));
     L.beta_bar = align256(sizeof(double) * r.N);
     L.req_stats = align256(sizeof(double) * 4);
     L.nL32 = align256(sizeof(float) * r.F);
@@ -213,7 +213,7 @@ int enqueue_requests(Workspace &ws, std::vector<ReqDesc> &reqs, int precision, c
     for (int k = 0; k < n; ++k) {
         ReqDesc &r = reqs[k];
         const ReqLayout &L = lay[k];
-        r.stat_part = (double *)p; p += L.stat_part;
+        r.stat_part = (float *)p; p += L.stat_part;
         r.beta_bar = (double *)p; p += L.beta_bar;
         r.req_stats = (double *)p; p += L.req_stats;
         r.nL32 = (float *)p; p += L.nL32;
