@@ -195,6 +195,31 @@ int fg21_loglike_batch(fg21_model *m, const double *params, int64_t P, double *l
 int fg21_loglike_batch_device(fg21_model *m, const double *d_params, int64_t P, double *d_logL,
                               int precision, void *stream);
 
+/* Size of the scratch array of fg21_loglike_batch_device_noalloc (per GPU). */
+#define FG21_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* The paper has no counterpart to this call.  It serves callers that cannot
+ * allocate GPU memory while they evaluate the likelihood: code that runs while
+ * a CUDA graph is being captured (an allocation there is not allowed), or a
+ * host that fixes the library's device memory up front and forbids growth
+ * later.  Same arguments and results as fg21_loglike_batch_device, for the
+ * tensor-core precisions (FG21_PREC_FP16X3, FG21_PREC_BF16X3), but it calls no
+ * cudaMalloc / cudaFree and allocates nothing: all per-call scratch comes from
+ * one static device array of FG21_NOALLOC_SCRATCH_BYTES (32 MiB) that every GPU
+ * which loads the library keeps until the process exits.  The model itself
+ * must already exist (fg21_build_regions allocates it).  A request whose
+ * scratch would not fit returns FG21_E_RANGE (the limit is about 140,000
+ * points at N = 24, F = 301, T = 100; split larger batches).  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current, so make that first call before any stream capture.
+ * All calls share the array and leave its contents behind (the status word is
+ * cleared at the start of each call, everything else is rewritten): calls
+ * that overlap on the GPU race, so order them, e.g. on one stream.  Invalid
+ * points get logL = -inf as in the other calls; the invalid count and the
+ * kernels' internal status are not reported by this call. */
+int fg21_loglike_batch_device_noalloc(fg21_model *m, const double *d_params, int64_t P, double *d_logL,
+                                      int precision, void *stream);
+
 /* Wait for the model's outstanding work on `stream`, then report the invalid
  * count of its last device call (may be NULL) and FG21_E_DEVICE if a kernel
  * reported an internal failure. */

@@ -80,6 +80,7 @@ _SIGS = {
     "fg21_simulate_data": (C.c_int, [_P, _P, _P, C.c_double, _P, _P]),
     "fg21_loglike_batch": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int, _P]),
     "fg21_loglike_batch_device": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int, _P]),
+    "fg21_loglike_batch_device_noalloc": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int, _P]),
     "fg21_model_sync_status": (C.c_int, [_P, _P, _P]),
     "fg21_model_eval": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int, _P]),
     "fg21_model_timing": (C.c_int, [_P, C.c_int]),
@@ -251,6 +252,13 @@ def fg21_loglike_batch_device(m: Model, d_params: int, P: int, d_logL: int, prec
                               stream: int = 0):
     _check(lib().fg21_loglike_batch_device(m.handle, d_params, int(P), d_logL, _prec(precision), stream or None),
            "fg21_loglike_batch_device")
+
+
+def fg21_loglike_batch_device_noalloc(m: Model, d_params: int, P: int, d_logL: int, precision="fp16x3",
+                                      stream: int = 0):
+    """The device call that allocates nothing (scratch in a static device array)."""
+    _check(lib().fg21_loglike_batch_device_noalloc(m.handle, d_params, int(P), d_logL, _prec(precision),
+                                                   stream or None), "fg21_loglike_batch_device_noalloc")
 
 
 def fg21_model_sync_status(m: Model, stream: int = 0) -> int:
