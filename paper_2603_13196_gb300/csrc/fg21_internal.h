@@ -115,6 +115,7 @@ struct TcLaunch {
     int tc_pad_max;          // max padded t-chunk over requests
     int precision;           // FG21_PREC_FP16X3 / BF16X3
     int box_rows;            // TMA box height (divides every request's tile height)
+    bool single_chunk;       // every request has one t-chunk (allows two channels per stage)
     void *arena;             // operand tile arena (device), 128-byte rows
     int64_t arena_rows;
     unsigned *status;

@@ -260,6 +260,8 @@ int enqueue_requests(Workspace &ws, std::vector<ReqDesc> &reqs, int precision, c
         std::vector<int64_t> rows_of(n);
         for (int k = 0; k < n; ++k) rows_of[k] = reqs[k].tile_rows;
         L.box_rows = tc_box_rows(rows_of.data(), n);
+        L.single_chunk = true;
+        for (int k = 0; k < n; ++k) L.single_chunk = L.single_chunk && reqs[k].n_tchunks == 1;
         L.arena = ws.arena;
         L.arena_rows = row;
         L.status = ws.d_status;

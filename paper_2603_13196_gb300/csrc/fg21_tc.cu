@@ -26,11 +26,18 @@
 //   warp 8     TMA producer: cp.async.bulk.tensor loads of the channel's
 //              operand tile Bop (prepared per request in global memory);
 //   warp 9     MMA issuer (one elected thread) and tensor-memory owner.
-// Pipelines: 4 operand-tile stages, 2 weight stages, 2 accumulator stages, all
-// handed over with mbarriers.  Every wait is bounded (a few seconds of
-// %globaltimer); on expiry the kernel sets a status bit, the roles stop, the
-// in-flight copies and MMAs are drained with bounded waits and tensor memory is
-// released before the CTA exits.
+// A stage is one or two channels (CPS) of one tile; RING = 2 stage slots each
+// hold the weights, the operand tiles and the accumulators of a stage.  Each
+// slot has two mbarriers: `full` completes when the 4 generator warps have
+// written the weights, the TMA bytes have landed and the 4 epilogue warps have
+// released the slot's accumulators (9 arrivals + transaction bytes); `done`
+// receives the single tcgen05.commit of the stage's MMAs and tells the
+// producers the slot is free and the epilogue the accumulators are ready.
+// One commit per stage matters: the MMA warp's tcgen05 synchronisation is what
+// limits throughput, so each commit covers as much tensor work as fits.
+// Every wait is bounded (a few seconds of %globaltimer); on expiry the kernel
+// sets a status bit, the roles stop, in-flight MMAs are drained with bounded
+// waits and tensor memory is released before the CTA exits.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -46,17 +53,15 @@ namespace fg21 {
 namespace {
 
 constexpr int NUM_THREADS = 320;
-constexpr int NB_STAGES = 4;     // operand-tile (TMA) stages
-constexpr int NW_STAGES = 2;     // weight stages
-constexpr int NACC = 2;          // accumulator stages in tensor memory
+constexpr int RING = 2;          // stage slots
+constexpr int FULL_ARRIVALS = 9; // 4 generator warps + 1 TMA producer + 4 epilogue warps
 // TMA boxes are 64 x box_rows 16-bit values (128-byte rows); box_rows divides
 // every request's tile height (a multiple of 8, at most 256)
 constexpr uint64_t WAIT_LIMIT_NS = 4000000000ull;
 
 struct __align__(8) Barriers {
-    uint64_t b_full[NB_STAGES], b_empty[NB_STAGES];
-    uint64_t w_full[NW_STAGES], w_empty[NW_STAGES];
-    uint64_t acc_full[NACC], acc_empty[NACC];
+    uint64_t full[RING];
+    uint64_t done[RING];
     uint64_t drain;
     uint32_t tmem_base;
     volatile uint32_t abort_flag;
@@ -337,31 +342,21 @@ struct Params {
     int box_rows;          // rows per TMA box
 };
 
-template <int KP, bool BF16>
+template <int KP, bool BF16, int CPS>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     tc_loglike_kernel(const __grid_constant__ CUtensorMap tmap, const Params prm) {
     extern __shared__ __align__(1024) char smem_raw[];
     char *smem = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    constexpr int W_STAGE_BYTES = 2 * KP * 128 * 2;
-    char *w_stages = smem;                                            // NW_STAGES x W_STAGE_BYTES
-    char *b_stages = smem + NW_STAGES * W_STAGE_BYTES;                // NB_STAGES x b_stage_bytes
-    Barriers *S = reinterpret_cast<Barriers *>(b_stages + NB_STAGES * prm.b_stage_bytes);
+    constexpr int W_CH_BYTES = 2 * KP * 128 * 2;                      // one channel's weights (hi + mid)
+    char *w_slots = smem;                                             // [RING][CPS] x W_CH_BYTES
+    char *b_slots = smem + RING * CPS * W_CH_BYTES;                   // [RING][CPS] x b_stage_bytes
+    Barriers *S = reinterpret_cast<Barriers *>(b_slots + RING * CPS * prm.b_stage_bytes);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < NB_STAGES; ++s) {
-            mbar_init(&S->b_full[s], 1);
-            mbar_init(&S->b_empty[s], 1);
-        }
-        // weight stages and accumulators are handed back by one arrival per
-        // warp (4 generator / 4 epilogue warps), after a __syncwarp
-        for (int s = 0; s < NW_STAGES; ++s) {
-            mbar_init(&S->w_full[s], 4);
-            mbar_init(&S->w_empty[s], 1);
-        }
-        for (int s = 0; s < NACC; ++s) {
-            mbar_init(&S->acc_full[s], 1);
-            mbar_init(&S->acc_empty[s], 4);
+        for (int s = 0; s < RING; ++s) {
+            mbar_init(&S->full[s], FULL_ARRIVALS);
+            mbar_init(&S->done[s], 1);
         }
         mbar_init(&S->drain, 1);
         S->abort_flag = 0;
@@ -378,16 +373,17 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = S->tmem_base;
     const ReqDesc *__restrict__ reqs = prm.reqs;
+    // stage s uses slot s % RING; phase parity of its k-th use is k & 1
 
     if (warp < 4) {
         // ================================================ weight generators
         const int m = threadIdx.x;
-        uint32_t w_stage = 0;
+        uint32_t stage = 0;
         bool ok = true;
         for (int64_t item = blockIdx.x; item < prm.n_items && ok; item += gridDim.x) {
             const Item it = decode_item(reqs, prm.n_reqs, item);
             const ReqDesc &r = reqs[it.req];
-            const int Kpr = r.Kp;
+            const int Kpr = r.Kp, nch = CPS == 1 ? r.n_tchunks : 1;
             const float *__restrict__ pts = r.pts32 + (size_t)it.tile * (Kpr + 4) * 128 + m;
             const float *__restrict__ nLp = r.nL32;
             const float *__restrict__ nup = r.nu32;
@@ -413,142 +409,171 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     c2[j] = pk2(cu[j] * sW, cu[j] * sW);
                 }
             }
-            float nL_next = __ldg(nLp + it.f0), nu_next = __ldg(nup + it.f0);
-            for (int f = it.f0; f < it.f1; ++f) {
-                const float nL = nL_next, nuf = nu_next;
-                if (f + 1 < it.f1) {
-                    nL_next = __ldg(nLp + f + 1);
-                    nu_next = __ldg(nup + f + 1);
+            // channel constants of the next stage are loaded one stage ahead
+            float nL_n[CPS], nu_n[CPS];
+#pragma unroll
+            for (int j = 0; j < CPS; ++j) {
+                const int fj = min(it.f0 + j, it.f1 - 1);
+                nL_n[j] = __ldg(nLp + fj);
+                nu_n[j] = __ldg(nup + fj);
+            }
+            for (int f = it.f0; f < it.f1 && ok; f += CPS) {
+                const int nf = min(CPS, it.f1 - f);
+                float nL[CPS], nuf[CPS];
+#pragma unroll
+                for (int j = 0; j < CPS; ++j) {
+                    nL[j] = nL_n[j];
+                    nuf[j] = nu_n[j];
+                    const int fj = min(f + CPS + j, it.f1 - 1);
+                    nL_n[j] = __ldg(nLp + fj);
+                    nu_n[j] = __ldg(nup + fj);
                 }
-                const uint32_t ws = w_stage % NW_STAGES, wph = (w_stage / NW_STAGES) & 1;
-                if (!mbar_wait(&S->w_empty[ws], wph ^ 1, S, prm.status, STATUS_TIMEOUT_GEN)) { ok = false; break; }
-                const float dnu = nuf - nu21;
-                const float s21 = sW * a21 * __expf(-dnu * dnu * inv2s2);
-                char *wbuf = w_stages + ws * W_STAGE_BYTES;
-                // the request's padded K (a multiple of 16, <= KP) fixes where the
-                // trough and -1 columns sit; it must match its operand tiles
-                if (Kpr == 16) gen_row_mode<16, KP, BF16>(mode, wbuf, m, dlt, nL, s21, sW, c2, cu);
-                else if (KP >= 32 && Kpr == 32) gen_row_mode<(KP >= 32 ? 32 : 16), KP, BF16>(mode, wbuf, m, dlt, nL, s21, sW, c2, cu);
-                else if (KP >= 48 && Kpr == 48) gen_row_mode<(KP >= 48 ? 48 : 16), KP, BF16>(mode, wbuf, m, dlt, nL, s21, sW, c2, cu);
-                else if (KP >= 64 && Kpr == 64) gen_row_mode<(KP >= 64 ? 64 : 16), KP, BF16>(mode, wbuf, m, dlt, nL, s21, sW, c2, cu);
-                fence_proxy_async_smem();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&S->w_full[ws]);
-                ++w_stage;
+                for (int c = 0; c < nch; ++c) {
+                    const uint32_t slot = stage % RING, ph = (stage / RING) & 1;
+                    if (!mbar_wait(&S->done[slot], ph ^ 1, S, prm.status, STATUS_TIMEOUT_GEN)) { ok = false; break; }
+#pragma unroll
+                    for (int j = 0; j < CPS; ++j) {
+                        if (j < nf) {
+                            const float dnu = nuf[j] - nu21;
+                            const float s21 = sW * a21 * __expf(-dnu * dnu * inv2s2);
+                            char *wbuf = w_slots + (slot * CPS + j) * W_CH_BYTES;
+                            // the request's padded K (a multiple of 16, <= KP) fixes where the
+                            // trough and -1 columns sit; it must match its operand tiles
+                            if (Kpr == 16) gen_row_mode<16, KP, BF16>(mode, wbuf, m, dlt, nL[j], s21, sW, c2, cu);
+                            else if (KP >= 32 && Kpr == 32) gen_row_mode<(KP >= 32 ? 32 : 16), KP, BF16>(mode, wbuf, m, dlt, nL[j], s21, sW, c2, cu);
+                            else if (KP >= 48 && Kpr == 48) gen_row_mode<(KP >= 48 ? 48 : 16), KP, BF16>(mode, wbuf, m, dlt, nL[j], s21, sW, c2, cu);
+                            else if (KP >= 64 && Kpr == 64) gen_row_mode<(KP >= 64 ? 64 : 16), KP, BF16>(mode, wbuf, m, dlt, nL[j], s21, sW, c2, cu);
+                        }
+                    }
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&S->full[slot]);
+                    ++stage;
+                }
             }
         }
     } else if (warp < 8) {
         // ========================================================= epilogue
         const int quad = warp & 3;
         const int m = quad * 32 + lane;
-        uint32_t acc_stage = 0;
+        // the accumulators of every slot start free: count their first release
+        if (lane == 0)
+            for (int sl = 0; sl < RING; ++sl) mbar_arrive(&S->full[sl]);
+        uint32_t stage = 0;
         bool ok = true;
         for (int64_t item = blockIdx.x; item < prm.n_items && ok; item += gridDim.x) {
             const Item it = decode_item(reqs, prm.n_reqs, item);
             const ReqDesc &r = reqs[it.req];
             const int64_t p = (int64_t)it.tile * 128 + m;
             const int sWexp = *r.scaleW;
-            const int nch = r.n_tchunks, Tc = r.Tc, T = r.T, F = r.F;
+            const int nch_all = r.n_tchunks, nch = CPS == 1 ? nch_all : 1, Tc = r.Tc, T = r.T, F = r.F;
             const int nblk = r.Tc_pad / 16;
             const int *__restrict__ scaleB = r.scaleB;
             const bool in = p < r.P;
             float qs = 0.0f, qc = 0.0f;
-            int sb_next = __ldg(scaleB + it.f0 * nch);
-            for (int f = it.f0; f < it.f1 && ok; ++f) {
-                float qf = 0.0f;
-                for (int cch = 0; cch < nch; ++cch) {
-                    const int fc = f * nch + cch;
-                    const int sb = sb_next;
-                    if (fc + 1 < it.f1 * nch) sb_next = __ldg(scaleB + fc + 1);
-                    const uint32_t a = acc_stage % NACC, aph = (acc_stage / NACC) & 1;
-                    if (!mbar_wait(&S->acc_full[a], aph, S, prm.status, STATUS_TIMEOUT_EPI)) { ok = false; break; }
+            for (int f = it.f0; f < it.f1 && ok; f += CPS) {
+                const int nf = min(CPS, it.f1 - f);
+                float qf[CPS];
+#pragma unroll
+                for (int j = 0; j < CPS; ++j) qf[j] = 0.0f;
+                for (int c = 0; c < nch; ++c) {
+                    const uint32_t slot = stage % RING, ph = (stage / RING) & 1;
+                    int sb[CPS];
+#pragma unroll
+                    for (int j = 0; j < CPS; ++j) sb[j] = j < nf ? __ldg(scaleB + (f + j) * nch_all + c) : 0;
+                    if (!mbar_wait(&S->done[slot], ph, S, prm.status, STATUS_TIMEOUT_EPI)) { ok = false; break; }
                     tc_fence_after();
-                    const float unscale = ldexpf(1.0f, -(sWexp + sb));
-                    const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + a * prm.acc_cols;
-                    uint64_t q2 = 0;
-                    for (int b0 = 0; b0 < nblk; b0 += 4) {
-                        float v[4][16];
-                        tmem_ld16(taddr + b0 * 16, v[0]);
-                        if (b0 + 1 < nblk) tmem_ld16(taddr + (b0 + 1) * 16, v[1]);
-                        if (b0 + 2 < nblk) tmem_ld16(taddr + (b0 + 2) * 16, v[2]);
-                        if (b0 + 3 < nblk) tmem_ld16(taddr + (b0 + 3) * 16, v[3]);
-                        tmem_ld_wait();
-                        if (prm.resid) {
-                            const int t0 = cch * Tc, tn = min(Tc, T - t0);
-                            if (in) {
-                                for (int bb = 0; bb < 4 && b0 + bb < nblk; ++bb)
 #pragma unroll
-                                    for (int j = 0; j < 16; ++j) {
-                                        const int t = (b0 + bb) * 16 + j;
-                                        if (t < tn) prm.resid[((size_t)p * F + f) * T + t0 + t] = -v[bb][j] * unscale;
-                                    }
-                            }
-                        } else {
+                    for (int j = 0; j < CPS; ++j) {
+                        if (j >= nf) break;
+                        const float unscale = ldexpf(1.0f, -(sWexp + sb[j]));
+                        const uint32_t taddr =
+                            tmem + ((uint32_t)(quad * 32) << 16) + (slot * CPS + j) * prm.acc_cols;
+                        uint64_t q2 = 0;
+                        for (int b0 = 0; b0 < nblk; b0 += 4) {
+                            float v[4][16];
+                            tmem_ld16(taddr + b0 * 16, v[0]);
+                            if (b0 + 1 < nblk) tmem_ld16(taddr + (b0 + 1) * 16, v[1]);
+                            if (b0 + 2 < nblk) tmem_ld16(taddr + (b0 + 2) * 16, v[2]);
+                            if (b0 + 3 < nblk) tmem_ld16(taddr + (b0 + 3) * 16, v[3]);
+                            tmem_ld_wait();
+                            if (prm.resid) {
+                                const int t0 = c * Tc, tn = min(Tc, T - t0);
+                                if (in) {
+                                    for (int bb = 0; bb < 4 && b0 + bb < nblk; ++bb)
 #pragma unroll
-                            for (int bb = 0; bb < 4; ++bb) {
-                                if (b0 + bb < nblk) {
+                                        for (int jj = 0; jj < 16; ++jj) {
+                                            const int t = (b0 + bb) * 16 + jj;
+                                            if (t < tn)
+                                                prm.resid[((size_t)p * F + f + j) * T + t0 + t] = -v[bb][jj] * unscale;
+                                        }
+                                }
+                            } else {
 #pragma unroll
-                                    for (int j = 0; j < 16; j += 2) {
-                                        const uint64_t x = pk2(v[bb][j], v[bb][j + 1]);
-                                        q2 = fma2(x, x, q2);
+                                for (int bb = 0; bb < 4; ++bb) {
+                                    if (b0 + bb < nblk) {
+#pragma unroll
+                                        for (int jj = 0; jj < 16; jj += 2) {
+                                            const uint64_t x = pk2(v[bb][jj], v[bb][jj + 1]);
+                                            q2 = fma2(x, x, q2);
+                                        }
                                     }
                                 }
                             }
                         }
+                        float qa, qb;
+                        upk2(q2, qa, qb);
+                        qf[j] += (qa + qb) * unscale * unscale;
                     }
                     tc_fence_before();
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(&S->acc_empty[a]);
-                    ++acc_stage;
-                    float qa, qb;
-                    upk2(q2, qa, qb);
-                    qf += (qa + qb) * unscale * unscale;
+                    if (lane == 0) mbar_arrive(&S->full[slot]);      // accumulators free for stage + RING
+                    ++stage;
                 }
-                kahan_add_dev(qs, qc, qf);
+#pragma unroll
+                for (int j = 0; j < CPS; ++j)
+                    if (j < nf) kahan_add_dev(qs, qc, qf[j]);
             }
             if (ok && !prm.resid && in) r.partials[(size_t)p * r.G + it.g] = make_float2(qs, -qc);
         }
     } else if (warp == 8) {
         // ====================================================== TMA producer
-        uint32_t b_stage = 0;
         bool ok = true;
+        uint32_t stage = 0;
         if (lane == 0) {
             for (int64_t item = blockIdx.x; item < prm.n_items && ok; item += gridDim.x) {
                 const Item it = decode_item(reqs, prm.n_reqs, item);
                 const ReqDesc &r = reqs[it.req];
-                const int rows = (int)r.tile_rows;
-                for (int f = it.f0; f < it.f1 && ok; ++f) {
-                    for (int cch = 0; cch < r.n_tchunks; ++cch) {
-                        const uint32_t bs = b_stage % NB_STAGES, bph = (b_stage / NB_STAGES) & 1;
-                        if (!mbar_wait(&S->b_empty[bs], bph ^ 1, S, prm.status, STATUS_TIMEOUT_TMA)) { ok = false; break; }
-                        mbar_arrive_expect_tx(&S->b_full[bs], (uint32_t)rows * 128u);
-                        const int64_t row0 = r.tile_row0 + (int64_t)(f * r.n_tchunks + cch) * rows;
-                        char *dst = b_stages + bs * prm.b_stage_bytes;
-                        for (int j = 0; j < rows; j += prm.box_rows)
-                            tma_load_2d(dst + j * 128, &tmap, 0, (int)(row0 + j), &S->b_full[bs]);
-                        ++b_stage;
+                const int rows = (int)r.tile_rows, nch_all = r.n_tchunks, nch = CPS == 1 ? nch_all : 1;
+                for (int f = it.f0; f < it.f1 && ok; f += CPS) {
+                    const int nf = min(CPS, it.f1 - f);
+                    for (int c = 0; c < nch; ++c) {
+                        const uint32_t slot = stage % RING, ph = (stage / RING) & 1;
+                        if (!mbar_wait(&S->done[slot], ph ^ 1, S, prm.status, STATUS_TIMEOUT_TMA)) { ok = false; break; }
+                        mbar_arrive_expect_tx(&S->full[slot], (uint32_t)(nf * rows * 128));
+                        for (int j = 0; j < nf; ++j) {
+                            const int64_t row0 = r.tile_row0 + (int64_t)((f + j) * nch_all + c) * rows;
+                            char *dst = b_slots + (slot * CPS + j) * prm.b_stage_bytes;
+                            for (int jr = 0; jr < rows; jr += prm.box_rows)
+                                tma_load_2d(dst + jr * 128, &tmap, 0, (int)(row0 + jr), &S->full[slot]);
+                        }
+                        ++stage;
                     }
                 }
             }
-            // drain: wait for the copies of the last stages issued (they land
-            // whether or not the MMA consumed them)
-            const uint32_t n_tail = b_stage < NB_STAGES ? b_stage : NB_STAGES;
-            for (uint32_t k = b_stage - n_tail; k < b_stage; ++k) {
-                const uint32_t bs = k % NB_STAGES, bph = (k / NB_STAGES) & 1;
-                uint64_t t0 = globaltimer();
-                while (!mbar_try_wait(&S->b_full[bs], bph)) {
-                    if (globaltimer() - t0 > WAIT_LIMIT_NS) {
-                        atomicOr(prm.status, STATUS_TIMEOUT_DRAIN);
-                        break;
-                    }
+            if (!ok) {
+                // copies already issued land within microseconds; give them time
+                // before the CTA (and its shared memory) goes away
+                const uint64_t t0 = globaltimer();
+                while (globaltimer() - t0 < 200000ull) {
                 }
             }
         }
         __syncwarp();
     } else {
         // ========================================================= MMA issuer
-        uint32_t b_stage = 0, w_stage = 0, acc_stage = 0;
         bool ok = true;
+        uint32_t stage = 0;
         if (lane == 0) {
             for (int64_t item = blockIdx.x; item < prm.n_items && ok; item += gridDim.x) {
                 const Item it = decode_item(reqs, prm.n_reqs, item);
@@ -556,35 +581,30 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 const uint32_t idesc = instr_desc(128, r.Tc_pad, BF16);
                 const uint32_t b_lbo = (uint32_t)r.Tc_pad * 16;
                 const uint32_t b_split = (uint32_t)(r.Kp / 8) * b_lbo;
-                const int ksteps = r.Kp / 16;
-                for (int f = it.f0; f < it.f1 && ok; ++f) {
-                    const uint32_t ws = w_stage % NW_STAGES, wph = (w_stage / NW_STAGES) & 1;
-                    if (!mbar_wait(&S->w_full[ws], wph, S, prm.status, STATUS_TIMEOUT_MMA)) { ok = false; break; }
-                    const uint32_t w_addr = smem_u32(w_stages + ws * W_STAGE_BYTES);
-                    for (int cch = 0; cch < r.n_tchunks; ++cch) {
-                        const uint32_t bs = b_stage % NB_STAGES, bph = (b_stage / NB_STAGES) & 1;
-                        const uint32_t a = acc_stage % NACC, aph = (acc_stage / NACC) & 1;
-                        if (!mbar_wait(&S->b_full[bs], bph, S, prm.status, STATUS_TIMEOUT_MMA)) { ok = false; break; }
-                        if (!mbar_wait(&S->acc_empty[a], aph ^ 1, S, prm.status, STATUS_TIMEOUT_MMA)) { ok = false; break; }
+                const int ksteps = r.Kp / 16, nch = CPS == 1 ? r.n_tchunks : 1;
+                for (int f = it.f0; f < it.f1 && ok; f += CPS) {
+                    const int nf = min(CPS, it.f1 - f);
+                    for (int c = 0; c < nch; ++c) {
+                        const uint32_t slot = stage % RING, ph = (stage / RING) & 1;
+                        if (!mbar_wait(&S->full[slot], ph, S, prm.status, STATUS_TIMEOUT_MMA)) { ok = false; break; }
                         tc_fence_after();
-                        const uint32_t b_addr = smem_u32(b_stages + bs * prm.b_stage_bytes);
-                        const uint32_t d_tmem = tmem + a * prm.acc_cols;
-                        for (int ks = 0; ks < ksteps; ++ks) {
-                            const uint64_t a_hi = smem_desc(w_addr + ks * 4096, 2048, 128);
-                            const uint64_t a_mid = smem_desc(w_addr + (KP / 8) * 2048 + ks * 4096, 2048, 128);
-                            const uint64_t b_hi = smem_desc(b_addr + ks * 2 * b_lbo, b_lbo, 128);
-                            const uint64_t b_mid = smem_desc(b_addr + b_split + ks * 2 * b_lbo, b_lbo, 128);
-                            mma_f16(d_tmem, a_hi, b_hi, idesc, ks > 0 ? 1u : 0u);
-                            mma_f16(d_tmem, a_hi, b_mid, idesc, 1u);
-                            mma_f16(d_tmem, a_mid, b_hi, idesc, 1u);
+                        for (int j = 0; j < nf; ++j) {
+                            const uint32_t w_addr = smem_u32(w_slots + (slot * CPS + j) * W_CH_BYTES);
+                            const uint32_t b_addr = smem_u32(b_slots + (slot * CPS + j) * prm.b_stage_bytes);
+                            const uint32_t d_tmem = tmem + (slot * CPS + j) * prm.acc_cols;
+                            for (int ks = 0; ks < ksteps; ++ks) {
+                                const uint64_t a_hi = smem_desc(w_addr + ks * 4096, 2048, 128);
+                                const uint64_t a_mid = smem_desc(w_addr + (KP / 8) * 2048 + ks * 4096, 2048, 128);
+                                const uint64_t b_hi = smem_desc(b_addr + ks * 2 * b_lbo, b_lbo, 128);
+                                const uint64_t b_mid = smem_desc(b_addr + b_split + ks * 2 * b_lbo, b_lbo, 128);
+                                mma_f16(d_tmem, a_hi, b_hi, idesc, ks > 0 ? 1u : 0u);
+                                mma_f16(d_tmem, a_hi, b_mid, idesc, 1u);
+                                mma_f16(d_tmem, a_mid, b_hi, idesc, 1u);
+                            }
                         }
-                        mma_commit(&S->b_empty[bs]);
-                        mma_commit(&S->acc_full[a]);
-                        if (cch == r.n_tchunks - 1) mma_commit(&S->w_empty[ws]);
-                        ++b_stage;
-                        ++acc_stage;
+                        mma_commit(&S->done[slot]);
+                        ++stage;
                     }
-                    ++w_stage;
                 }
             }
             // drain: every MMA issued so far completes before tensor memory is freed
@@ -616,26 +636,31 @@ EncodeTiledFn g_encode = nullptr;
 std::once_flag g_encode_once;
 int g_encode_rc = FG21_OK;
 
-size_t smem_bytes(int kp, int b_stage_bytes) {
-    return 1024 + (size_t)NW_STAGES * 2 * kp * 128 * 2 + (size_t)NB_STAGES * b_stage_bytes + sizeof(Barriers) + 64;
+size_t smem_bytes(int kp, int cps, int b_stage_bytes) {
+    return 1024 + (size_t)RING * cps * (2 * kp * 128 * 2 + (size_t)b_stage_bytes) + sizeof(Barriers) + 64;
 }
 
-template <int KP, bool BF16>
+template <int KP, bool BF16, int CPS>
 cudaError_t launch_kp(const CUtensorMap &map, const Params &prm, int grid, size_t sm, cudaStream_t stream) {
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(tc_loglike_kernel<KP, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             227 * 1024);
+        cudaError_t e = cudaFuncSetAttribute(tc_loglike_kernel<KP, BF16, CPS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    tc_loglike_kernel<KP, BF16><<<grid, NUM_THREADS, sm, stream>>>(map, prm);
+    tc_loglike_kernel<KP, BF16, CPS><<<grid, NUM_THREADS, sm, stream>>>(map, prm);
     return cudaGetLastError();
 }
 
+template <int KP, bool BF16>
+cudaError_t launch_cps(int cps, const CUtensorMap &map, const Params &prm, int grid, size_t sm, cudaStream_t stream) {
+    return cps == 2 ? launch_kp<KP, BF16, 2>(map, prm, grid, sm, stream) : launch_kp<KP, BF16, 1>(map, prm, grid, sm, stream);
+}
+
 cudaError_t launch_common(const ReqDesc *d_reqs, int n_reqs, int64_t n_items, int kp_max, int tc_pad_max,
-                          int precision, void *arena, int64_t arena_rows, unsigned *status, float *resid,
-                          int box_rows, int num_sms, cudaStream_t stream) {
+                          bool single_chunk, int precision, void *arena, int64_t arena_rows, unsigned *status,
+                          float *resid, int box_rows, int num_sms, cudaStream_t stream) {
     if (n_items == 0) return cudaSuccess;
     if (tc_map_init() != FG21_OK) return cudaErrorNotSupported;
     CUtensorMap map;
@@ -654,21 +679,26 @@ cudaError_t launch_common(const ReqDesc *d_reqs, int n_reqs, int64_t n_items, in
     prm.n_items = n_items;
     prm.b_stage_bytes = ((4 * kp_max * tc_pad_max) + 1023) & ~1023;
     prm.acc_cols = tc_pad_max;
+    const int kp = kp_max <= 16 ? 16 : kp_max <= 32 ? 32 : 64;
+    // two channels per stage when every request fits one t-chunk and the
+    // doubled slots fit shared and tensor memory
+    const int cps = (single_chunk && kp <= 32 && RING * 2 * tc_pad_max <= 512) ? 2 : 1;
     uint32_t cols = 32;
-    while (cols < (uint32_t)(NACC * tc_pad_max)) cols *= 2;
+    while (cols < (uint32_t)(RING * cps * tc_pad_max)) cols *= 2;
+    if (cols > 512) return cudaErrorInvalidValue;
     prm.tmem_cols = cols;
     prm.status = status;
     prm.resid = resid;
     prm.box_rows = box_rows;
-    const int kp = kp_max <= 16 ? 16 : kp_max <= 32 ? 32 : 64;
     // at least ~120 KB so that a single CTA (and its tensor memory) owns each SM
-    size_t sm = smem_bytes(kp, prm.b_stage_bytes);
+    size_t sm = smem_bytes(kp, cps, prm.b_stage_bytes);
     if (sm < 120 * 1024) sm = 120 * 1024;
+    if (sm > 227 * 1024) return cudaErrorInvalidValue;
     const int grid = (int)(n_items < num_sms ? n_items : num_sms);
     const bool bf16 = precision == FG21_PREC_BF16X3;
-    if (kp == 16) return bf16 ? launch_kp<16, true>(map, prm, grid, sm, stream) : launch_kp<16, false>(map, prm, grid, sm, stream);
-    if (kp == 32) return bf16 ? launch_kp<32, true>(map, prm, grid, sm, stream) : launch_kp<32, false>(map, prm, grid, sm, stream);
-    return bf16 ? launch_kp<64, true>(map, prm, grid, sm, stream) : launch_kp<64, false>(map, prm, grid, sm, stream);
+    if (kp == 16) return bf16 ? launch_cps<16, true>(cps, map, prm, grid, sm, stream) : launch_cps<16, false>(cps, map, prm, grid, sm, stream);
+    if (kp == 32) return bf16 ? launch_cps<32, true>(cps, map, prm, grid, sm, stream) : launch_cps<32, false>(cps, map, prm, grid, sm, stream);
+    return bf16 ? launch_cps<64, true>(cps, map, prm, grid, sm, stream) : launch_cps<64, false>(cps, map, prm, grid, sm, stream);
 }
 
 }  // namespace
@@ -709,8 +739,8 @@ int tc_box_rows(const int64_t *tile_rows, int n) {
 }
 
 cudaError_t launch_tc(const TcLaunch &L, int num_sms, cudaStream_t stream) {
-    return launch_common(L.d_reqs, L.n_reqs, L.n_items, L.kp_max, L.tc_pad_max, L.precision, L.arena,
-                         L.arena_rows, L.status, nullptr, L.box_rows, num_sms, stream);
+    return launch_common(L.d_reqs, L.n_reqs, L.n_items, L.kp_max, L.tc_pad_max, L.single_chunk, L.precision,
+                         L.arena, L.arena_rows, L.status, nullptr, L.box_rows, num_sms, stream);
 }
 
 cudaError_t launch_tc_residuals(const ReqDesc *h_req, const ReqDesc *d_req, int precision, float *resid,
@@ -724,8 +754,8 @@ cudaError_t launch_tc_residuals(const ReqDesc *h_req, const ReqDesc *d_req, int 
     char *arena = h_req->tiles - h_req->tile_row0 * 128;
     const int64_t rows = h_req->tile_row0 + (int64_t)h_req->F * h_req->n_tchunks * h_req->tile_rows;
     const int64_t items = (int64_t)h_req->n_tiles * h_req->G;
-    return launch_common(d_req, 1, items, h_req->Kp, h_req->Tc_pad, precision, arena, rows, h_req->status, resid,
-                         tc_box_rows(&h_req->tile_rows, 1), sms, stream);
+    return launch_common(d_req, 1, items, h_req->Kp, h_req->Tc_pad, h_req->n_tchunks == 1, precision, arena, rows,
+                         h_req->status, resid, tc_box_rows(&h_req->tile_rows, 1), sms, stream);
 }
 
 }  // namespace fg21
