@@ -88,17 +88,24 @@ int Workspace::ensure(size_t dev_need, size_t arena_need, size_t pinned_need, in
     return FG21_OK;
 }
 
+// The timing events are created when timing is switched on, never inside a
+// timed call (creating thousands of events takes milliseconds).
+int Workspace::timing_prepare() {
+    if (!tev.empty()) return FG21_OK;
+    tev.assign((size_t)TIMING_CAP * 4, nullptr);
+    for (auto &e : tev)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            for (auto &x : tev)
+                if (x) cudaEventDestroy(x);
+            tev.clear();
+            return set_error(FG21_E_CUDA, "cudaEventCreate of the timing events failed");
+        }
+    return FG21_OK;
+}
+
 cudaEvent_t *Workspace::timing_slot() {
-    if (!timing) return nullptr;
-    if (tev.empty()) {
-        tev.assign((size_t)TIMING_CAP * 4, nullptr);
-        for (auto &e : tev)
-            if (cudaEventCreate(&e) != cudaSuccess) {
-                cudaGetLastError();
-                timing = false;
-                return nullptr;
-            }
-    }
+    if (!timing || tev.empty()) return nullptr;
     cudaEvent_t *slot = &tev[(size_t)(tcalls % TIMING_CAP) * 4];
     ++tcalls;
     return slot;
@@ -501,6 +508,10 @@ int fg21_model_timing(fg21_model *m, int enable) {
     if (!m) return set_error(FG21_E_ARG, "NULL model");
     std::lock_guard<std::mutex> lk(m->mu);
     if (m->ws.done) FG21_CUDA_TRY(cudaEventSynchronize(m->ws.done));
+    if (enable) {
+        int rc = m->ws.timing_prepare();
+        if (rc) return rc;
+    }
     m->ws.timing = enable != 0;
     m->ws.tcalls = 0;
     return FG21_OK;

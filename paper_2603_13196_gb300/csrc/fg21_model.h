@@ -29,6 +29,7 @@ struct Workspace {
     static constexpr int TIMING_CAP = 8192;
     std::vector<cudaEvent_t> tev;   // [TIMING_CAP][4], created on first use
     int64_t tcalls = 0;             // calls recorded since timing was enabled
+    int timing_prepare();           // creates the timing events (when timing is switched on)
     cudaEvent_t *timing_slot();     // the 4 events of the next call (nullptr if timing off)
 
     int ensure(size_t dev_need, size_t arena_need, size_t pinned_need, int n_reqs);

@@ -222,6 +222,11 @@ __device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
     asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
 __device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
     uint64_t d;
     asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
@@ -289,25 +294,42 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t 
 // whose padded K is KPR (<= KP): columns k < KPR-2 carry the regions (zero
 // deviation -> zero weight beyond N), column KPR-2 the trough, KPR-1 the -1
 // that multiplies dref.  Layout [split][kc][m][8 values], split stride
-// KP/8 * 2048 bytes.
+// KP/8 * 2048 bytes.  The Horner chains of all region pairs advance together
+// (step j of every pair before step j-1), so a single warp per scheduler has
+// NP independent packed FMAs in flight instead of one dependent chain.
 template <int KPR, int KP, bool BF16, int MODE>   // MODE: 3, 5, 8 = series degree; 0 = reduced
 __device__ __forceinline__ void gen_row(char *wbuf, int m, const float *dlt, float nL, float s21, float sW,
                                         const uint64_t *c2, const float *cu) {
+    constexpr int NP = (KPR - 2) / 2;            // region pairs
     const uint64_t nL2 = pk2(nL, nL);
+    uint64_t w[NP];
+    if (MODE == 0) {
+#pragma unroll
+        for (int i = 0; i < NP; ++i)
+            w[i] = pk2(em1_reduced(dlt[2 * i] * nL, cu, sW), em1_reduced(dlt[2 * i + 1] * nL, cu, sW));
+    } else {
+        uint64_t x[NP];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            x[i] = mul2(pk2(dlt[2 * i], dlt[2 * i + 1]), nL2);
+            w[i] = c2[MODE];
+        }
+#pragma unroll
+        for (int j = MODE - 1; j >= 1; --j)
+#pragma unroll
+            for (int i = 0; i < NP; ++i) w[i] = fma2(w[i], x[i], c2[j]);
+#pragma unroll
+        for (int i = 0; i < NP; ++i) w[i] = mul2(w[i], x[i]);
+    }
 #pragma unroll
     for (int kc = 0; kc < KPR / 8; ++kc) {
         uint32_t H[4], M[4];
 #pragma unroll
         for (int e = 0; e < 8; e += 2) {
-            const int k = kc * 8 + e;
+            const int pair = (kc * 8 + e) / 2;
             float a, b;
-            if (k < KPR - 2) {
-                if (MODE == 0) {
-                    a = em1_reduced(dlt[k] * nL, cu, sW);
-                    b = em1_reduced(dlt[k + 1] * nL, cu, sW);
-                } else {
-                    upk2(em1_series2<MODE>(mul2(pk2(dlt[k], dlt[k + 1]), nL2), c2), a, b);
-                }
+            if (pair < NP) {
+                upk2(w[pair], a, b);
             } else {
                 a = s21;
                 b = -sW;
@@ -489,7 +511,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                         const float unscale = ldexpf(1.0f, -(sWexp + sb[j]));
                         const uint32_t taddr =
                             tmem + ((uint32_t)(quad * 32) << 16) + (slot * CPS + j) * prm.acc_cols;
-                        uint64_t q2 = 0;
+                        uint64_t q2[4] = {0, 0, 0, 0};          // independent accumulators
                         for (int b0 = 0; b0 < nblk; b0 += 4) {
                             float v[4][16];
                             tmem_ld16(taddr + b0 * 16, v[0]);
@@ -515,15 +537,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll
                                         for (int jj = 0; jj < 16; jj += 2) {
                                             const uint64_t x = pk2(v[bb][jj], v[bb][jj + 1]);
-                                            q2 = fma2(x, x, q2);
+                                            q2[(jj >> 1) & 3] = fma2(x, x, q2[(jj >> 1) & 3]);
                                         }
                                     }
                                 }
                             }
                         }
-                        float qa, qb;
-                        upk2(q2, qa, qb);
-                        qf[j] += (qa + qb) * unscale * unscale;
+                        float qa, qb, qc2, qd;
+                        upk2(add2(q2[0], q2[1]), qa, qb);
+                        upk2(add2(q2[2], q2[3]), qc2, qd);
+                        qf[j] += ((qa + qb) + (qc2 + qd)) * unscale * unscale;
                     }
                     tc_fence_before();
                     __syncwarp();
