@@ -29,7 +29,9 @@ enum : unsigned {
 };
 
 constexpr int TILE_M = 128;         // points per MMA tile (tcgen05 M)
-constexpr int TC_MAX = 256;         // max t-columns per MMA (tcgen05 N)
+constexpr int TC_MAX = 192;         // max t-columns per MMA (tcgen05 N): two stage slots of
+                                    // accumulators (<= 192 columns) plus weights (<= 64 columns)
+                                    // fit the 512 tensor-memory columns of an SM
 constexpr int STAT_BLOCK = 256;     // points per statistics block of the per-request prep
 constexpr int KP_MAX = 64;          // max padded K on the tensor path
 
@@ -54,6 +56,7 @@ struct ReqDesc {
     int Kp;                // K = N + 2 padded to a multiple of 16 (tensor path)
     int Tc, Tc_pad, n_tchunks;   // t-chunks: Tc columns each (last may be shorter), padded to 16
     int G, ch_per_group;         // channel groups per 128-point tile
+    int n_part;                  // partial sums per point (G on the SIMT forms, 2G on the tensor path)
     int n_tiles;                 // ceil(P / 128)
     int n_stat_blocks;           // ceil(P / STAT_BLOCK)
     int64_t item_begin;          // first global work-item id of this request
@@ -71,7 +74,7 @@ struct ReqDesc {
     int *scaleW;           // [1] power-of-two exponent of the weight operand
     float *Bp32;           // [N][F][T] wbar_i A (FP32, SIMT delta form)
     float *dref32;         // [F][T]    reference residual (FP32, SIMT delta form)
-    float2 *partials;      // [P][G] compensated partial chi^2 (hi, lo)
+    float2 *partials;      // [P][n_part] compensated partial chi^2 (hi, lo)
     float *pts32;          // [n_tiles][Kp + 4][128] per point: beta - bbar (rows < Kp-2, zero
                            // beyond N), then A21, nu21, 1/(2 sigma21^2) (rows Kp-2..Kp); tensor path
     unsigned *status;      // device status word (shared by a launch)
@@ -115,7 +118,6 @@ struct TcLaunch {
     int tc_pad_max;          // max padded t-chunk over requests
     int precision;           // FG21_PREC_FP16X3 / BF16X3
     int box_rows;            // TMA box height (divides every request's tile height)
-    bool single_chunk;       // every request has one t-chunk (allows two channels per stage)
     void *arena;             // operand tile arena (device), 128-byte rows
     int64_t arena_rows;
     unsigned *status;

@@ -451,7 +451,7 @@ __global__ void __launch_bounds__(SIMT_THREADS) simt_kernel(const ReqDesc *__res
         }
         kahan_add(qs, qc, qf);
     }
-    if (inb) r.partials[(size_t)p * r.G + g] = make_float2(qs, -qc);
+    if (inb) r.partials[(size_t)p * r.n_part + g] = make_float2(qs, -qc);
 }
 
 // a6: per point, sum the channel-group partials in fixed order (FP64) and form
@@ -469,8 +469,8 @@ __global__ void reduce_kernel(const ReqDesc *__restrict__ reqs, int n_reqs) {
         return;
     }
     double chi2 = 0.0;
-    for (int g = 0; g < r.G; ++g) {
-        float2 v = r.partials[(size_t)p * r.G + g];
+    for (int g = 0; g < r.n_part; ++g) {
+        float2 v = r.partials[(size_t)p * r.n_part + g];
         chi2 += (double)v.x + (double)v.y;
     }
     const double sig = th[N + 3];

@@ -161,10 +161,9 @@ static int choose_channels_per_group(int64_t total_tiles, int F, int num_sms) {
 
 void plan_request(ReqDesc &r, int precision, int num_sms, int64_t total_tiles) {
     r.Kp = round16(r.N + 2);
-    // one operand tile (2 x Kp x Tc_pad x 2 bytes) stays <= 32 KB so that four
-    // pipeline stages fit in shared memory next to the weight stages
-    const int tc_cap = r.Kp <= 32 ? TC_MAX : TC_MAX / 2;
-    r.n_tchunks = (r.T + tc_cap - 1) / tc_cap;
+    // t-chunks of at most TC_MAX columns: the same cap for every K keeps the
+    // plan of a request independent of what it is batched with
+    r.n_tchunks = (r.T + TC_MAX - 1) / TC_MAX;
     r.Tc = (r.T + r.n_tchunks - 1) / r.n_tchunks;
     r.Tc_pad = round16(r.Tc);
     r.n_tiles = (int)((r.P + TILE_M - 1) / TILE_M);
@@ -172,8 +171,9 @@ void plan_request(ReqDesc &r, int precision, int num_sms, int64_t total_tiles) {
     int cpg = choose_channels_per_group(total_tiles, r.F, num_sms);
     r.G = (r.F + cpg - 1) / cpg;
     r.ch_per_group = (r.F + r.G - 1) / r.G;
+    const bool tc = precision == FG21_PREC_FP16X3 || precision == FG21_PREC_BF16X3;
+    r.n_part = tc ? 2 * r.G : r.G;      // the tensor path splits each point's t-columns over two warps
     r.tile_rows = (int64_t)r.Kp * r.Tc_pad / 32;   // 2 splits x Kp x Tc_pad x 2 bytes / 128
-    (void)precision;
 }
 
 ReqLayout request_layout(const ReqDesc &r, int precision) {
@@ -189,7 +189,7 @@ ReqLayout request_layout(const ReqDesc &r, int precision) {
     const bool delta = precision == FG21_PREC_FP32_DELTA;
     L.Bp32 = delta ? align256(sizeof(float) * (size_t)r.N * r.F * r.T) : 0;
     L.dref32 = delta ? align256(sizeof(float) * (size_t)r.F * r.T) : 0;
-    L.partials = align256(sizeof(float2) * (size_t)r.P * r.G);
+    L.partials = align256(sizeof(float2) * (size_t)r.P * r.n_part);
     L.pts32 = tc ? align256(sizeof(float) * (size_t)r.n_tiles * (r.Kp + 4) * TILE_M) : 0;
     L.tiles = tc ? (size_t)r.F * r.n_tchunks * r.tile_rows * 128 : 0;
     return L;
@@ -267,8 +267,6 @@ int enqueue_requests(Workspace &ws, std::vector<ReqDesc> &reqs, int precision, c
         std::vector<int64_t> rows_of(n);
         for (int k = 0; k < n; ++k) rows_of[k] = reqs[k].tile_rows;
         L.box_rows = tc_box_rows(rows_of.data(), n);
-        L.single_chunk = true;
-        for (int k = 0; k < n; ++k) L.single_chunk = L.single_chunk && reqs[k].n_tchunks == 1;
         L.arena = ws.arena;
         L.arena_rows = row;
         L.status = ws.d_status;

@@ -119,7 +119,6 @@ extern "C" int fg21_loglike_batch_device_noalloc(fg21_model *m, const double *d_
     T.tc_pad_max = r.Tc_pad;
     T.precision = precision;
     T.box_rows = tc_box_rows(&r.tile_rows, 1);
-    T.single_chunk = r.n_tchunks == 1;
     T.arena = arena;
     T.arena_rows = (int64_t)(L.tiles / 128);
     T.status = status;

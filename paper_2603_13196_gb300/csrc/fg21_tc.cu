@@ -16,25 +16,30 @@
 // (hi*hi + hi*mid + mid*hi) accumulate in FP32 in tensor memory.
 //
 // One persistent CTA per SM walks a static list of work items (request, tile
-// of 128 points, group of channels).  Warp roles:
-//   warps 0-3  weight generators: thread m owns point m of the tile; computes
-//              its W row per channel in registers and stores it (hi and mid)
-//              to shared memory in the K-major core-matrix layout;
-//   warps 4-7  epilogue: tcgen05.ld of the accumulator rows (warp w reads lanes
-//              32(w%4)..+31), square-and-sum over t, unscale, compensated sum
-//              over channels, one partial chi2 per (point, item);
-//   warp 8     TMA producer: cp.async.bulk.tensor loads of the channel's
-//              operand tile Bop (prepared per request in global memory);
-//   warp 9     MMA issuer (one elected thread) and tensor-memory owner.
-// A stage is one or two channels (CPS) of one tile; RING = 2 stage slots each
-// hold the weights, the operand tiles and the accumulators of a stage.  Each
-// slot has two mbarriers: `full` completes when the 4 generator warps have
-// written the weights, the TMA bytes have landed and the 4 epilogue warps have
-// released the slot's accumulators (9 arrivals + transaction bytes); `done`
-// receives the single tcgen05.commit of the stage's MMAs and tells the
-// producers the slot is free and the epilogue the accumulators are ready.
-// One commit per stage matters: the MMA warp's tcgen05 synchronisation is what
-// limits throughput, so each commit covers as much tensor work as fits.
+// of 128 points, group of channels); a stage is one channel (one t-chunk) of
+// the tile.  Warp roles (18 warps):
+//   warps 0-7    weight generators: warp w serves the points of tensor-memory
+//                lane quadrant w%4 and half w/4 of the weight columns; each
+//                thread evaluates its point's weights for the channel in
+//                registers, splits them into hi + mid and writes them straight
+//                into tensor memory (tcgen05.st), where the MMA reads its A
+//                operand;
+//   warps 8-15   epilogue: tcgen05.ld of the accumulator rows of quadrant w%4,
+//                half (w-8)/4 of the t-columns; square-and-sum over t, unscale,
+//                compensated sum over channels, one partial chi2 per (point,
+//                item, half);
+//   warp 16      TMA producer: cp.async.bulk.tensor loads of the channel's
+//                operand tile Bop (prepared per request in global memory);
+//   warp 17      MMA issuer (one elected thread) and tensor-memory owner.
+// Shared memory carries only the operand tiles (the B side), so the tensor
+// cores' shared-memory reads are one operand per MMA.  RING (2-4) stage slots
+// each hold an operand tile in shared memory and an accumulator plus a weight
+// block in tensor memory.  Each slot has two mbarriers: `full` completes when
+// the 8 generator warps have stored the weights, the TMA bytes have landed and
+// the 8 epilogue warps have released the slot's accumulator (17 arrivals +
+// transaction bytes); `done` receives the single tcgen05.commit of the stage's
+// MMAs and tells the producers the slot is free and the epilogue the
+// accumulator is ready.
 // Every wait is bounded (a few seconds of %globaltimer); on expiry the kernel
 // sets a status bit, the roles stop, in-flight MMAs are drained with bounded
 // waits and tensor memory is released before the CTA exits.
@@ -52,16 +57,17 @@ namespace fg21 {
 
 namespace {
 
-constexpr int NUM_THREADS = 320;
-constexpr int RING = 2;          // stage slots
-constexpr int FULL_ARRIVALS = 9; // 4 generator warps + 1 TMA producer + 4 epilogue warps
+constexpr int NUM_THREADS = 576;
+constexpr int MAX_RING = 4;       // stage slots (the launch picks 2-4 by tensor-memory room)
+constexpr int FULL_ARRIVALS = 17; // 8 generator warps + 1 TMA producer + 8 epilogue warps
+constexpr int WARP_TMA = 16, WARP_MMA = 17;
 // TMA boxes are 64 x box_rows 16-bit values (128-byte rows); box_rows divides
 // every request's tile height (a multiple of 8, at most 256)
 constexpr uint64_t WAIT_LIMIT_NS = 4000000000ull;
 
 struct __align__(8) Barriers {
-    uint64_t full[RING];
-    uint64_t done[RING];
+    uint64_t full[MAX_RING];
+    uint64_t done[MAX_RING];
     uint64_t drain;
     uint32_t tmem_base;
     volatile uint32_t abort_flag;
@@ -113,9 +119,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, Barrie
         }
     }
 }
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
 __device__ __forceinline__ void tc_fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -146,12 +149,15 @@ __device__ __forceinline__ uint32_t instr_desc(int M, int N, bool bf16) {
     const uint32_t fmt = bf16 ? 1u : 0u;
     return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
-__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
+// D (+)= A B with A in tensor memory (128 lanes = rows, K packed two 16-bit
+// values per 32-bit column) and B in shared memory.
+__device__ __forceinline__ void mma_f16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                           uint32_t accum) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(accum)
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(accum)
         : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
@@ -169,7 +175,19 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// This thread's lane, N consecutive 32-bit columns from taddr.
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t *v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr), "r"(v[0]), "r"(v[1]),
+                 "r"(v[2]), "r"(v[3])
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
+// 2^e for integer e in the normal range (exact; the scale exponents here are
+// clamped to +-40 each, so their sums stay within +-80).
+__device__ __forceinline__ float exp2i(int e) {
+    return __int_as_float((min(max(e, -126), 127) + 127) << 23);
+}
 __device__ __forceinline__ void kahan_add_dev(float &s, float &c, float x) {
     const float y = x - c;
     const float t = s + y;
@@ -233,31 +251,23 @@ __device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
     return d;
 }
 
-// expm1 by its Taylor series x (1 + x/2! + ... + x^(D-1)/D!), scaled by 2^sW
-// through the coefficient pairs c2[j] = (2^sW / j!, 2^sW / j!), on two
-// arguments at once.  Relative truncation error |x|^D / (D+1)!: D = 3 for
-// |x| <= 0.01, 5 for |x| <= 0.1, 8 for |x| <= 0.55.
-template <int D>
-__device__ __forceinline__ uint64_t em1_series2(uint64_t x2, const uint64_t *c2) {
-    uint64_t p = c2[D];
+// expm1 by its Taylor series on y = x / 2^s (|y| <= 0.55) and s squarings
+// (1 + e)^2 - 1 = e (e + 2):  with y = d * nL / 2^s,
+//   expm1(y) = sum_{j=1..D} e_j d^j,   e_j = (nL / 2^s)^j / j!,
+// evaluated by Horner's rule in d (the per-point deviation) with the channel's
+// coefficients e_j (2^sW folded into them when s = 0), on two arguments at
+// once.  Relative truncation error |y|^D / (D+1)!: D = 3 for |y| <= 0.01,
+// 5 for |y| <= 0.1, 8 for |y| <= 0.55; each squaring adds about two roundings.
+template <int D, int CH>
+__device__ __forceinline__ void em1_series2(uint64_t (&w)[CH], const uint64_t *d2, const uint64_t *e2) {
 #pragma unroll
-    for (int j = D - 1; j >= 1; --j) p = fma2(p, x2, c2[j]);
-    return mul2(p, x2);
-}
-// Larger |x|: Cody-Waite reduction x = k ln2 + r (ln2 split into a 12-bit-short
-// head and a tail), expm1(r) by the degree-7 series (|r| <= ln2/2), then
-// 2^sW (e^x - 1) = 2^(k+sW) expm1(r) + 2^sW (2^k - 1).
-__device__ __forceinline__ float em1_reduced(float x, const float *cu, float sW) {
-    const float k = rintf(x * 1.4426950408889634f);
-    float r = fmaf(-k, 0.693115234375f, x);
-    r = fmaf(-k, 3.194618329871446e-05f, r);
-    float p = cu[7];
+    for (int i = 0; i < CH; ++i) w[i] = fma2(e2[D], d2[i], e2[D - 1]);
 #pragma unroll
-    for (int j = 6; j >= 1; --j) p = fmaf(p, r, cu[j]);
-    p *= r;
-    const int ki = max(-100, min(100, (int)k));
-    const float two_k = ldexpf(1.0f, ki);
-    return fmaf(p, two_k * sW, (two_k - 1.0f) * sW);
+    for (int j = D - 2; j >= 1; --j)
+#pragma unroll
+        for (int i = 0; i < CH; ++i) w[i] = fma2(w[i], d2[i], e2[j]);
+#pragma unroll
+    for (int i = 0; i < CH; ++i) w[i] = mul2(w[i], d2[i]);
 }
 
 template <bool BF16>
@@ -290,65 +300,68 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t 
     mid = pack2<BF16>(ra, rb);
 }
 
-// One channel's weight row of point m into weight stage `wbuf`, for a request
-// whose padded K is KPR (<= KP): columns k < KPR-2 carry the regions (zero
-// deviation -> zero weight beyond N), column KPR-2 the trough, KPR-1 the -1
-// that multiplies dref.  Layout [split][kc][m][8 values], split stride
-// KP/8 * 2048 bytes.  The Horner chains of all region pairs advance together
-// (step j of every pair before step j-1), so a single warp per scheduler has
-// NP independent packed FMAs in flight instead of one dependent chain.
-template <int KPR, int KP, bool BF16, int MODE>   // MODE: 3, 5, 8 = series degree; 0 = reduced
-__device__ __forceinline__ void gen_row(char *wbuf, int m, const float *dlt, float nL, float s21, float sW,
-                                        const uint64_t *c2, const float *cu) {
-    constexpr int NP = (KPR - 2) / 2;            // region pairs
-    const uint64_t nL2 = pk2(nL, nL);
-    uint64_t w[NP];
-    if (MODE == 0) {
-#pragma unroll
-        for (int i = 0; i < NP; ++i)
-            w[i] = pk2(em1_reduced(dlt[2 * i] * nL, cu, sW), em1_reduced(dlt[2 * i + 1] * nL, cu, sW));
-    } else {
-        uint64_t x[NP];
-#pragma unroll
-        for (int i = 0; i < NP; ++i) {
-            x[i] = mul2(pk2(dlt[2 * i], dlt[2 * i + 1]), nL2);
-            w[i] = c2[MODE];
-        }
-#pragma unroll
-        for (int j = MODE - 1; j >= 1; --j)
-#pragma unroll
-            for (int i = 0; i < NP; ++i) w[i] = fma2(w[i], x[i], c2[j]);
-#pragma unroll
-        for (int i = 0; i < NP; ++i) w[i] = mul2(w[i], x[i]);
+// Series parameters of a request: squarings s and degree D for |x| <= xmax.
+struct SeriesPlan {
+    int D, s;
+};
+__device__ __forceinline__ SeriesPlan series_plan(double xmax) {
+    SeriesPlan sp{8, 0};
+    while (xmax > 0.55 && sp.s < 12) {
+        xmax *= 0.5;
+        ++sp.s;
     }
+    sp.D = xmax <= 0.01 ? 3 : xmax <= 0.1 ? 5 : 8;
+    return sp;
+}
+
+// One channel's weights of this thread's point for its half of the request's
+// Kr columns (nph = Kr/4 pairs, at most NPHMAX; FULL: nph = NPHMAX), written
+// to tensor memory: hi at columns t_hi.., mid at t_mid.. (one 32-bit column
+// per pair: the lower K index in the low half).  Pair i holds deviations d2[i]
+// (zero beyond N -> zero weight); on the last half the final pair is
+// (trough, -1) instead (columns Kr-2, Kr-1).  A chunk whose pairs all lie
+// beyond N (pair index >= nz) is stored as zeros without evaluation.  The
+// Horner chains of a chunk of CH pairs advance together.
+template <int NPHMAX, bool BF16, bool FULL>
+__device__ __forceinline__ void gen_half(uint32_t t_hi, uint32_t t_mid, const uint64_t *d2, const uint64_t *e2,
+                                         SeriesPlan sp, uint64_t sW2, int nph_rt, int nz, bool last, float s21,
+                                         float sW) {
+    constexpr int CH = 4;
+    const int nph = FULL ? NPHMAX : nph_rt;
 #pragma unroll
-    for (int kc = 0; kc < KPR / 8; ++kc) {
-        uint32_t H[4], M[4];
+    for (int c0 = 0; c0 < NPHMAX; c0 += CH) {
+        if (!FULL && c0 >= nph) break;
+        uint64_t w[CH];
+        if (c0 < nz) {
+            if (sp.D == 3) em1_series2<3, CH>(w, d2 + c0, e2);
+            else if (sp.D == 5) em1_series2<5, CH>(w, d2 + c0, e2);
+            else em1_series2<8, CH>(w, d2 + c0, e2);
+            if (sp.s > 0) {
+                const uint64_t two2 = pk2(2.0f, 2.0f);
+                for (int q = 0; q < sp.s; ++q)
 #pragma unroll
-        for (int e = 0; e < 8; e += 2) {
-            const int pair = (kc * 8 + e) / 2;
+                    for (int i = 0; i < CH; ++i) w[i] = mul2(w[i], add2(w[i], two2));
+#pragma unroll
+                for (int i = 0; i < CH; ++i) w[i] = mul2(w[i], sW2);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < CH; ++i) w[i] = 0;
+        }
+        uint32_t H[CH], M[CH];
+#pragma unroll
+        for (int i = 0; i < CH; ++i) {
             float a, b;
-            if (pair < NP) {
-                upk2(w[pair], a, b);
-            } else {
+            upk2(w[i], a, b);
+            const bool tr = FULL ? (c0 + i == NPHMAX - 1) : (c0 + i == nph - 1);
+            if (last && tr) {
                 a = s21;
                 b = -sW;
             }
-            split2<BF16>(a, b, H[e / 2], M[e / 2]);
+            split2<BF16>(a, b, H[i], M[i]);
         }
-        *reinterpret_cast<uint4 *>(wbuf + kc * 2048 + m * 16) = make_uint4(H[0], H[1], H[2], H[3]);
-        *reinterpret_cast<uint4 *>(wbuf + (KP / 8) * 2048 + kc * 2048 + m * 16) = make_uint4(M[0], M[1], M[2], M[3]);
-    }
-}
-
-template <int KPR, int KP, bool BF16>
-__device__ __forceinline__ void gen_row_mode(int mode, char *wbuf, int m, const float *dlt, float nL, float s21,
-                                             float sW, const uint64_t *c2, const float *cu) {
-    switch (mode) {
-        case 3: gen_row<KPR, KP, BF16, 3>(wbuf, m, dlt, nL, s21, sW, c2, cu); break;
-        case 5: gen_row<KPR, KP, BF16, 5>(wbuf, m, dlt, nL, s21, sW, c2, cu); break;
-        case 8: gen_row<KPR, KP, BF16, 8>(wbuf, m, dlt, nL, s21, sW, c2, cu); break;
-        default: gen_row<KPR, KP, BF16, 0>(wbuf, m, dlt, nL, s21, sW, c2, cu); break;
+        tmem_st4(t_hi + c0, H);
+        tmem_st4(t_mid + c0, M);
     }
 }
 
@@ -357,26 +370,208 @@ struct Params {
     int n_reqs;
     int64_t n_items;
     int b_stage_bytes;     // bytes of one operand-tile stage
-    int acc_cols;          // tensor-memory columns per accumulator stage
+    int acc_cols;          // tensor-memory columns of one accumulator slot
+    int ring;              // stage slots (2..MAX_RING)
     uint32_t tmem_cols;    // allocated tensor-memory columns
     unsigned *status;
     float *resid;          // validation mode: residuals [P][F][T] of request 0, else null
     int box_rows;          // rows per TMA box
 };
 
-template <int KP, bool BF16, int CPS>
+// Stage counter of a role: slot = stage mod ring, phase parity flips each lap.
+struct Ring {
+    uint32_t slot = 0, ph = 0;
+    __device__ __forceinline__ void next(int ring) {
+        if (++slot == (uint32_t)ring) {
+            slot = 0;
+            ph ^= 1u;
+        }
+    }
+};
+
+// ------------------------------------------------------------ generators
+// Generator state of one item: this thread's deviations for its half of the
+// columns, and the request constants.
+template <int NPHMAX>
+struct GenItem {
+    uint64_t d2[NPHMAX];
+    float a21, nu21, inv2s2, sW;
+    int Kr, nz;            // nz: pairs of this half from index nz on carry no region
+    SeriesPlan sp;
+};
+template <int NPHMAX>
+__device__ __forceinline__ void gen_item_load(GenItem<NPHMAX> &g, const ReqDesc &r, const Item &it, int half,
+                                              int m) {
+    const int Kr = r.Kp, nph = Kr / 4;
+    const float *__restrict__ pts = r.pts32 + (size_t)it.tile * (Kr + 4) * 128 + m;
+    // this half's pairs [half*nph, half*nph + nph): regions 2*pair, 2*pair+1 (zero beyond N)
+#pragma unroll
+    for (int i = 0; i < NPHMAX; ++i) {
+        const int k = 2 * (half * nph + i);
+        const float a = (i < nph && k < Kr - 2) ? pts[(size_t)k * 128] : 0.0f;
+        const float b = (i < nph && k + 1 < Kr - 2) ? pts[(size_t)(k + 1) * 128] : 0.0f;
+        g.d2[i] = pk2(a, b);
+    }
+    g.a21 = half ? pts[(size_t)(Kr - 2) * 128] : 0.0f;
+    g.nu21 = half ? pts[(size_t)(Kr - 1) * 128] : 0.0f;
+    g.inv2s2 = half ? pts[(size_t)Kr * 128] : 0.0f;
+    g.sW = exp2i(*r.scaleW);
+    g.sp = series_plan(r.req_stats[1]);
+    g.Kr = Kr;
+    g.nz = min(nph, max(0, (r.N + 1) / 2 - half * nph));
+}
+
+// The weights of every stage of one item by one generator warp (FULL: the
+// request's Kr equals the kernel's KP).  Per stage: wait until the weight slot
+// is free (the MMAs of stage - ring are done), evaluate and store the weights,
+// then one arrival on full[slot].  Returns false on a wait timeout.
+template <int KP, bool BF16, bool FULL>
+__device__ __forceinline__ bool gen_item(const Params &prm, Barriers *S, Ring &rg, const ReqDesc &r, const Item &it,
+                                         const GenItem<KP / 4> &gi, uint32_t w_lane, int half) {
+    constexpr int NPHMAX = KP / 4;
+    const int lane = threadIdx.x & 31, nch = r.n_tchunks;
+    const int nph = gi.Kr / 4;
+    const float *__restrict__ nLp = r.nL32;
+    const float *__restrict__ nup = r.nu32;
+    const float ys = exp2i(-gi.sp.s);
+    const uint64_t sW2 = pk2(gi.sW, gi.sW);
+    float nL_n = __ldg(nLp + it.f0), nu_n = __ldg(nup + it.f0);
+    for (int f = it.f0; f < it.f1; ++f) {
+        const float nL = nL_n, nuf = nu_n;
+        const int fn = min(f + 1, it.f1 - 1);            // next channel's constants, one ahead
+        nL_n = __ldg(nLp + fn);
+        nu_n = __ldg(nup + fn);
+        // e_j = (nL / 2^s)^j / j!, times 2^sW when s = 0
+        uint64_t e2[9];
+        {
+            const float y1 = nL * ys;
+            float pw = gi.sp.s ? 1.0f : gi.sW, fact = 1.0f;
+            e2[0] = 0;
+#pragma unroll
+            for (int j = 1; j < 9; ++j) {
+                pw *= y1;
+                fact *= (float)j;
+                const float e = pw * (1.0f / fact);
+                e2[j] = pk2(e, e);
+            }
+        }
+        float s21 = 0.0f;
+        if (half) {
+            const float dnu = nuf - gi.nu21;
+            s21 = gi.sW * gi.a21 * __expf(-dnu * dnu * gi.inv2s2);
+        }
+        for (int c = 0; c < nch; ++c) {
+            if (!mbar_wait(&S->done[rg.slot], rg.ph ^ 1, S, prm.status, STATUS_TIMEOUT_GEN)) return false;
+            tc_fence_after();
+            const uint32_t wb = w_lane + rg.slot * KP;
+            if (FULL)
+                gen_half<NPHMAX, BF16, true>(wb + half * NPHMAX, wb + KP / 2 + half * NPHMAX, gi.d2, e2, gi.sp, sW2,
+                                             NPHMAX, gi.nz, half != 0, s21, gi.sW);
+            else
+                gen_half<NPHMAX, BF16, false>(wb + half * nph, wb + gi.Kr / 2 + half * nph, gi.d2, e2, gi.sp, sW2,
+                                              nph, gi.nz, half != 0, s21, gi.sW);
+            tmem_st_wait();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S->full[rg.slot]);
+            rg.next(prm.ring);
+        }
+    }
+    return true;
+}
+
+// ------------------------------------------------------------- epilogue
+// tcgen05.ld of one or two 16-column blocks of this thread's accumulator row.
+__device__ __forceinline__ void acc_issue2(uint32_t taddr, int b0, int nb, float (&v)[2][16]) {
+    tmem_ld16(taddr + b0 * 16, v[0]);
+    if (nb > 1) tmem_ld16(taddr + (b0 + 1) * 16, v[1]);
+}
+__device__ __forceinline__ float acc_sumsq2(const float (&v)[2][16], int nb) {
+    float q[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // independent accumulators
+#pragma unroll
+    for (int bb = 0; bb < 2; ++bb) {
+        if (bb < nb) {
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) q[jj & 7] = fmaf(v[bb][jj], v[bb][jj], q[jj & 7]);
+        }
+    }
+    return ((q[0] + q[1]) + (q[2] + q[3])) + ((q[4] + q[5]) + (q[6] + q[7]));
+}
+
+// The epilogue of every stage of one item by one epilogue warp: per stage wait
+// for the MMAs (the accumulator), read and reduce this warp's half of the
+// t-blocks, release the accumulator slot; per item one compensated partial.
+template <bool RESID>
+__device__ __forceinline__ bool epi_item(const Params &prm, Barriers *S, Ring &rg, const ReqDesc &r, const Item &it,
+                                         uint32_t lane_addr, int half, int m) {
+    const int lane = threadIdx.x & 31;
+    const int64_t p = (int64_t)it.tile * 128 + m;
+    const bool in = p < r.P;
+    const int sWexp = *r.scaleW;
+    const int nch = r.n_tchunks, Tc = r.Tc, T = r.T, F = r.F;
+    const int nblk = r.Tc_pad / 16, hb = (nblk + 1) / 2;
+    const int b_lo = half * hb, b_hi = min(nblk, b_lo + hb);
+    const int *__restrict__ scaleB = r.scaleB;
+    float qs = 0.0f, qc = 0.0f;
+    int sb_n = __ldg(scaleB + it.f0 * nch);
+    for (int f = it.f0; f < it.f1; ++f) {
+        float qf = 0.0f;
+        for (int c = 0; c < nch; ++c) {
+            const int sb = sb_n;
+            sb_n = __ldg(scaleB + min(f * nch + c + 1, it.f1 * nch - 1));   // next stage's scale, one ahead
+            if (!mbar_wait(&S->done[rg.slot], rg.ph, S, prm.status, STATUS_TIMEOUT_EPI)) return false;
+            tc_fence_after();
+            const float unscale = exp2i(-(sWexp + sb));
+            const uint32_t taddr = lane_addr + rg.slot * prm.acc_cols;
+            float q = 0.0f;
+            for (int b0 = b_lo; b0 < b_hi; b0 += 2) {
+                const int nb = min(2, b_hi - b0);
+                float v[2][16];
+                acc_issue2(taddr, b0, nb, v);
+                tmem_ld_wait();
+                if (RESID) {
+                    if (in) {
+                        const int t0 = c * Tc, tn = min(Tc, T - t0);
+                        for (int bb = 0; bb < nb; ++bb)
+#pragma unroll
+                            for (int jj = 0; jj < 16; ++jj) {
+                                const int t = (b0 + bb) * 16 + jj;
+                                if (t < tn) prm.resid[((size_t)p * F + f) * T + t0 + t] = -v[bb][jj] * unscale;
+                            }
+                    }
+                } else {
+                    q += acc_sumsq2(v, nb);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S->full[rg.slot]);      // accumulator free for stage + ring
+            rg.next(prm.ring);
+            qf += q * unscale * unscale;
+        }
+        kahan_add_dev(qs, qc, qf);
+    }
+    if (!RESID && in) r.partials[(size_t)p * r.n_part + 2 * it.g + half] = make_float2(qs, -qc);
+    return true;
+}
+
+// Tensor-memory columns: accumulator of slot s at s * acc_cols; weights of
+// slot s at ring * acc_cols + s * KP (hi: Kr/2 columns, then mid: Kr/2).
+// RESID: validation mode (residuals of request 0 to prm.resid instead of the
+// chi2 partials); a separate instantiation keeps that code out of the
+// production kernel.
+template <int KP, bool BF16, bool RESID>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     tc_loglike_kernel(const __grid_constant__ CUtensorMap tmap, const Params prm) {
     extern __shared__ __align__(1024) char smem_raw[];
     char *smem = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    constexpr int W_CH_BYTES = 2 * KP * 128 * 2;                      // one channel's weights (hi + mid)
-    char *w_slots = smem;                                             // [RING][CPS] x W_CH_BYTES
-    char *b_slots = smem + RING * CPS * W_CH_BYTES;                   // [RING][CPS] x b_stage_bytes
-    Barriers *S = reinterpret_cast<Barriers *>(b_slots + RING * CPS * prm.b_stage_bytes);
+    const int ring = prm.ring;
+    char *b_slots = smem;                                             // [ring] x b_stage_bytes
+    Barriers *S = reinterpret_cast<Barriers *>(b_slots + ring * prm.b_stage_bytes);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < RING; ++s) {
+        for (int s = 0; s < ring; ++s) {
             mbar_init(&S->full[s], FULL_ARRIVALS);
             mbar_init(&S->done[s], 1);
         }
@@ -384,7 +579,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         S->abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 9) {
+    if (warp == WARP_MMA) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S->tmem_base)),
                      "r"(prm.tmem_cols)
                      : "memory");
@@ -394,193 +589,59 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = S->tmem_base;
+    const uint32_t w_col0 = (uint32_t)(ring * prm.acc_cols);
     const ReqDesc *__restrict__ reqs = prm.reqs;
-    // stage s uses slot s % RING; phase parity of its k-th use is k & 1
 
-    if (warp < 4) {
+    if (warp < 8) {
         // ================================================ weight generators
-        const int m = threadIdx.x;
-        uint32_t stage = 0;
+        const int quad = warp & 3, half = warp >> 2;
+        const int m = quad * 32 + lane;
+        const uint32_t w_lane = tmem + ((uint32_t)(quad * 32) << 16) + w_col0;
+        Ring rg;
         bool ok = true;
+        GenItem<KP / 4> gi;
         for (int64_t item = blockIdx.x; item < prm.n_items && ok; item += gridDim.x) {
             const Item it = decode_item(reqs, prm.n_reqs, item);
             const ReqDesc &r = reqs[it.req];
-            const int Kpr = r.Kp, nch = CPS == 1 ? r.n_tchunks : 1;
-            const float *__restrict__ pts = r.pts32 + (size_t)it.tile * (Kpr + 4) * 128 + m;
-            const float *__restrict__ nLp = r.nL32;
-            const float *__restrict__ nup = r.nu32;
-            float dlt[KP];
-#pragma unroll
-            for (int k = 0; k < KP; ++k) dlt[k] = k < Kpr - 2 ? pts[(size_t)k * 128] : 0.0f;
-            const float a21 = pts[(size_t)(Kpr - 2) * 128];
-            const float nu21 = pts[(size_t)(Kpr - 1) * 128];
-            const float inv2s2 = pts[(size_t)Kpr * 128];
-            const float sW = ldexpf(1.0f, *r.scaleW);
-            const double xmax = r.req_stats[1];
-            const int mode = xmax <= 0.01 ? 3 : xmax <= 0.1 ? 5 : xmax <= 0.55 ? 8 : 0;
-            uint64_t c2[10];
-            float cu[10];
-            {
-                float fact = 1.0f;
-                cu[0] = 0.0f;
-                c2[0] = 0;
-#pragma unroll
-                for (int j = 1; j < 10; ++j) {
-                    fact *= (float)j;
-                    cu[j] = 1.0f / fact;
-                    c2[j] = pk2(cu[j] * sW, cu[j] * sW);
-                }
-            }
-            // channel constants of the next stage are loaded one stage ahead
-            float nL_n[CPS], nu_n[CPS];
-#pragma unroll
-            for (int j = 0; j < CPS; ++j) {
-                const int fj = min(it.f0 + j, it.f1 - 1);
-                nL_n[j] = __ldg(nLp + fj);
-                nu_n[j] = __ldg(nup + fj);
-            }
-            for (int f = it.f0; f < it.f1 && ok; f += CPS) {
-                const int nf = min(CPS, it.f1 - f);
-                float nL[CPS], nuf[CPS];
-#pragma unroll
-                for (int j = 0; j < CPS; ++j) {
-                    nL[j] = nL_n[j];
-                    nuf[j] = nu_n[j];
-                    const int fj = min(f + CPS + j, it.f1 - 1);
-                    nL_n[j] = __ldg(nLp + fj);
-                    nu_n[j] = __ldg(nup + fj);
-                }
-                for (int c = 0; c < nch; ++c) {
-                    const uint32_t slot = stage % RING, ph = (stage / RING) & 1;
-                    if (!mbar_wait(&S->done[slot], ph ^ 1, S, prm.status, STATUS_TIMEOUT_GEN)) { ok = false; break; }
-#pragma unroll
-                    for (int j = 0; j < CPS; ++j) {
-                        if (j < nf) {
-                            const float dnu = nuf[j] - nu21;
-                            const float s21 = sW * a21 * __expf(-dnu * dnu * inv2s2);
-                            char *wbuf = w_slots + (slot * CPS + j) * W_CH_BYTES;
-                            // the request's padded K (a multiple of 16, <= KP) fixes where the
-                            // trough and -1 columns sit; it must match its operand tiles
-                            if (Kpr == 16) gen_row_mode<16, KP, BF16>(mode, wbuf, m, dlt, nL[j], s21, sW, c2, cu);
-                            else if (KP >= 32 && Kpr == 32) gen_row_mode<(KP >= 32 ? 32 : 16), KP, BF16>(mode, wbuf, m, dlt, nL[j], s21, sW, c2, cu);
-                            else if (KP >= 48 && Kpr == 48) gen_row_mode<(KP >= 48 ? 48 : 16), KP, BF16>(mode, wbuf, m, dlt, nL[j], s21, sW, c2, cu);
-                            else if (KP >= 64 && Kpr == 64) gen_row_mode<(KP >= 64 ? 64 : 16), KP, BF16>(mode, wbuf, m, dlt, nL[j], s21, sW, c2, cu);
-                        }
-                    }
-                    fence_proxy_async_smem();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&S->full[slot]);
-                    ++stage;
-                }
-            }
+            gen_item_load(gi, r, it, half, m);
+            // a request's Kr fixes the column count of each half; it must match its operand tiles
+            if (gi.Kr == KP) ok = gen_item<KP, BF16, true>(prm, S, rg, r, it, gi, w_lane, half);
+            else ok = gen_item<KP, BF16, false>(prm, S, rg, r, it, gi, w_lane, half);
         }
-    } else if (warp < 8) {
+    } else if (warp < 16) {
         // ========================================================= epilogue
-        const int quad = warp & 3;
+        const int quad = warp & 3, half = (warp - 8) >> 2;
         const int m = quad * 32 + lane;
+        const uint32_t lane_addr = tmem + ((uint32_t)(quad * 32) << 16);
         // the accumulators of every slot start free: count their first release
         if (lane == 0)
-            for (int sl = 0; sl < RING; ++sl) mbar_arrive(&S->full[sl]);
-        uint32_t stage = 0;
+            for (int sl = 0; sl < ring; ++sl) mbar_arrive(&S->full[sl]);
+        Ring rg;
         bool ok = true;
         for (int64_t item = blockIdx.x; item < prm.n_items && ok; item += gridDim.x) {
             const Item it = decode_item(reqs, prm.n_reqs, item);
-            const ReqDesc &r = reqs[it.req];
-            const int64_t p = (int64_t)it.tile * 128 + m;
-            const int sWexp = *r.scaleW;
-            const int nch_all = r.n_tchunks, nch = CPS == 1 ? nch_all : 1, Tc = r.Tc, T = r.T, F = r.F;
-            const int nblk = r.Tc_pad / 16;
-            const int *__restrict__ scaleB = r.scaleB;
-            const bool in = p < r.P;
-            float qs = 0.0f, qc = 0.0f;
-            for (int f = it.f0; f < it.f1 && ok; f += CPS) {
-                const int nf = min(CPS, it.f1 - f);
-                float qf[CPS];
-#pragma unroll
-                for (int j = 0; j < CPS; ++j) qf[j] = 0.0f;
-                for (int c = 0; c < nch; ++c) {
-                    const uint32_t slot = stage % RING, ph = (stage / RING) & 1;
-                    int sb[CPS];
-#pragma unroll
-                    for (int j = 0; j < CPS; ++j) sb[j] = j < nf ? __ldg(scaleB + (f + j) * nch_all + c) : 0;
-                    if (!mbar_wait(&S->done[slot], ph, S, prm.status, STATUS_TIMEOUT_EPI)) { ok = false; break; }
-                    tc_fence_after();
-#pragma unroll
-                    for (int j = 0; j < CPS; ++j) {
-                        if (j >= nf) break;
-                        const float unscale = ldexpf(1.0f, -(sWexp + sb[j]));
-                        const uint32_t taddr =
-                            tmem + ((uint32_t)(quad * 32) << 16) + (slot * CPS + j) * prm.acc_cols;
-                        uint64_t q2[4] = {0, 0, 0, 0};          // independent accumulators
-                        for (int b0 = 0; b0 < nblk; b0 += 4) {
-                            float v[4][16];
-                            tmem_ld16(taddr + b0 * 16, v[0]);
-                            if (b0 + 1 < nblk) tmem_ld16(taddr + (b0 + 1) * 16, v[1]);
-                            if (b0 + 2 < nblk) tmem_ld16(taddr + (b0 + 2) * 16, v[2]);
-                            if (b0 + 3 < nblk) tmem_ld16(taddr + (b0 + 3) * 16, v[3]);
-                            tmem_ld_wait();
-                            if (prm.resid) {
-                                const int t0 = c * Tc, tn = min(Tc, T - t0);
-                                if (in) {
-                                    for (int bb = 0; bb < 4 && b0 + bb < nblk; ++bb)
-#pragma unroll
-                                        for (int jj = 0; jj < 16; ++jj) {
-                                            const int t = (b0 + bb) * 16 + jj;
-                                            if (t < tn)
-                                                prm.resid[((size_t)p * F + f + j) * T + t0 + t] = -v[bb][jj] * unscale;
-                                        }
-                                }
-                            } else {
-#pragma unroll
-                                for (int bb = 0; bb < 4; ++bb) {
-                                    if (b0 + bb < nblk) {
-#pragma unroll
-                                        for (int jj = 0; jj < 16; jj += 2) {
-                                            const uint64_t x = pk2(v[bb][jj], v[bb][jj + 1]);
-                                            q2[(jj >> 1) & 3] = fma2(x, x, q2[(jj >> 1) & 3]);
-                                        }
-                                    }
-                                }
-                            }
-                        }
-                        float qa, qb, qc2, qd;
-                        upk2(add2(q2[0], q2[1]), qa, qb);
-                        upk2(add2(q2[2], q2[3]), qc2, qd);
-                        qf[j] += ((qa + qb) + (qc2 + qd)) * unscale * unscale;
-                    }
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&S->full[slot]);      // accumulators free for stage + RING
-                    ++stage;
-                }
-#pragma unroll
-                for (int j = 0; j < CPS; ++j)
-                    if (j < nf) kahan_add_dev(qs, qc, qf[j]);
-            }
-            if (ok && !prm.resid && in) r.partials[(size_t)p * r.G + it.g] = make_float2(qs, -qc);
+            ok = epi_item<RESID>(prm, S, rg, reqs[it.req], it, lane_addr, half, m);
         }
-    } else if (warp == 8) {
+    } else if (warp == WARP_TMA) {
         // ====================================================== TMA producer
         bool ok = true;
-        uint32_t stage = 0;
+        Ring rg;
         if (lane == 0) {
             for (int64_t item = blockIdx.x; item < prm.n_items && ok; item += gridDim.x) {
                 const Item it = decode_item(reqs, prm.n_reqs, item);
                 const ReqDesc &r = reqs[it.req];
-                const int rows = (int)r.tile_rows, nch_all = r.n_tchunks, nch = CPS == 1 ? nch_all : 1;
-                for (int f = it.f0; f < it.f1 && ok; f += CPS) {
-                    const int nf = min(CPS, it.f1 - f);
+                const int rows = (int)r.tile_rows, nch = r.n_tchunks;
+                const int64_t tile_row0 = r.tile_row0;
+                for (int f = it.f0; f < it.f1 && ok; ++f) {
                     for (int c = 0; c < nch; ++c) {
-                        const uint32_t slot = stage % RING, ph = (stage / RING) & 1;
-                        if (!mbar_wait(&S->done[slot], ph ^ 1, S, prm.status, STATUS_TIMEOUT_TMA)) { ok = false; break; }
-                        mbar_arrive_expect_tx(&S->full[slot], (uint32_t)(nf * rows * 128));
-                        for (int j = 0; j < nf; ++j) {
-                            const int64_t row0 = r.tile_row0 + (int64_t)((f + j) * nch_all + c) * rows;
-                            char *dst = b_slots + (slot * CPS + j) * prm.b_stage_bytes;
-                            for (int jr = 0; jr < rows; jr += prm.box_rows)
-                                tma_load_2d(dst + jr * 128, &tmap, 0, (int)(row0 + jr), &S->full[slot]);
-                        }
-                        ++stage;
+                        // the operand slot is free once the MMAs of stage - ring are done
+                        if (!mbar_wait(&S->done[rg.slot], rg.ph ^ 1, S, prm.status, STATUS_TIMEOUT_TMA)) { ok = false; break; }
+                        mbar_arrive_expect_tx(&S->full[rg.slot], (uint32_t)(rows * 128));
+                        const int64_t row0 = tile_row0 + (int64_t)(f * nch + c) * rows;
+                        char *dst = b_slots + rg.slot * prm.b_stage_bytes;
+                        for (int jr = 0; jr < rows; jr += prm.box_rows)
+                            tma_load_2d(dst + jr * 128, &tmap, 0, (int)(row0 + jr), &S->full[rg.slot]);
+                        rg.next(ring);
                     }
                 }
             }
@@ -596,7 +657,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     } else {
         // ========================================================= MMA issuer
         bool ok = true;
-        uint32_t stage = 0;
+        Ring rg;
         if (lane == 0) {
             for (int64_t item = blockIdx.x; item < prm.n_items && ok; item += gridDim.x) {
                 const Item it = decode_item(reqs, prm.n_reqs, item);
@@ -604,29 +665,23 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 const uint32_t idesc = instr_desc(128, r.Tc_pad, BF16);
                 const uint32_t b_lbo = (uint32_t)r.Tc_pad * 16;
                 const uint32_t b_split = (uint32_t)(r.Kp / 8) * b_lbo;
-                const int ksteps = r.Kp / 16, nch = CPS == 1 ? r.n_tchunks : 1;
-                for (int f = it.f0; f < it.f1 && ok; f += CPS) {
-                    const int nf = min(CPS, it.f1 - f);
+                const int Kr = r.Kp, ksteps = Kr / 16, nch = r.n_tchunks;
+                for (int f = it.f0; f < it.f1 && ok; ++f) {
                     for (int c = 0; c < nch; ++c) {
-                        const uint32_t slot = stage % RING, ph = (stage / RING) & 1;
-                        if (!mbar_wait(&S->full[slot], ph, S, prm.status, STATUS_TIMEOUT_MMA)) { ok = false; break; }
+                        if (!mbar_wait(&S->full[rg.slot], rg.ph, S, prm.status, STATUS_TIMEOUT_MMA)) { ok = false; break; }
                         tc_fence_after();
-                        for (int j = 0; j < nf; ++j) {
-                            const uint32_t w_addr = smem_u32(w_slots + (slot * CPS + j) * W_CH_BYTES);
-                            const uint32_t b_addr = smem_u32(b_slots + (slot * CPS + j) * prm.b_stage_bytes);
-                            const uint32_t d_tmem = tmem + (slot * CPS + j) * prm.acc_cols;
-                            for (int ks = 0; ks < ksteps; ++ks) {
-                                const uint64_t a_hi = smem_desc(w_addr + ks * 4096, 2048, 128);
-                                const uint64_t a_mid = smem_desc(w_addr + (KP / 8) * 2048 + ks * 4096, 2048, 128);
-                                const uint64_t b_hi = smem_desc(b_addr + ks * 2 * b_lbo, b_lbo, 128);
-                                const uint64_t b_mid = smem_desc(b_addr + b_split + ks * 2 * b_lbo, b_lbo, 128);
-                                mma_f16(d_tmem, a_hi, b_hi, idesc, ks > 0 ? 1u : 0u);
-                                mma_f16(d_tmem, a_hi, b_mid, idesc, 1u);
-                                mma_f16(d_tmem, a_mid, b_hi, idesc, 1u);
-                            }
+                        const uint32_t w_hi = tmem + w_col0 + rg.slot * KP, w_mid = w_hi + Kr / 2;
+                        const uint32_t b_addr = smem_u32(b_slots + rg.slot * prm.b_stage_bytes);
+                        const uint32_t d_tmem = tmem + rg.slot * prm.acc_cols;
+                        for (int ks = 0; ks < ksteps; ++ks) {
+                            const uint64_t b_hi = smem_desc(b_addr + ks * 2 * b_lbo, b_lbo, 128);
+                            const uint64_t b_mid = smem_desc(b_addr + b_split + ks * 2 * b_lbo, b_lbo, 128);
+                            mma_f16_ts(d_tmem, w_hi + ks * 8, b_hi, idesc, ks > 0 ? 1u : 0u);
+                            mma_f16_ts(d_tmem, w_hi + ks * 8, b_mid, idesc, 1u);
+                            mma_f16_ts(d_tmem, w_mid + ks * 8, b_hi, idesc, 1u);
                         }
-                        mma_commit(&S->done[slot]);
-                        ++stage;
+                        mma_commit(&S->done[rg.slot]);
+                        rg.next(ring);
                     }
                 }
             }
@@ -644,7 +699,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 9) {
+    if (warp == WARP_MMA) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(prm.tmem_cols)
                      : "memory");
@@ -659,31 +714,32 @@ EncodeTiledFn g_encode = nullptr;
 std::once_flag g_encode_once;
 int g_encode_rc = FG21_OK;
 
-size_t smem_bytes(int kp, int cps, int b_stage_bytes) {
-    return 1024 + (size_t)RING * cps * (2 * kp * 128 * 2 + (size_t)b_stage_bytes) + sizeof(Barriers) + 64;
+size_t smem_bytes(int ring, int b_stage_bytes) {
+    return 1024 + (size_t)ring * b_stage_bytes + sizeof(Barriers) + 64;
 }
 
-template <int KP, bool BF16, int CPS>
-cudaError_t launch_kp(const CUtensorMap &map, const Params &prm, int grid, size_t sm, cudaStream_t stream) {
+template <int KP, bool BF16, bool RESID>
+cudaError_t launch_kpr(const CUtensorMap &map, const Params &prm, int grid, size_t sm, cudaStream_t stream) {
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(tc_loglike_kernel<KP, BF16, CPS>,
+        cudaError_t e = cudaFuncSetAttribute(tc_loglike_kernel<KP, BF16, RESID>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    tc_loglike_kernel<KP, BF16, CPS><<<grid, NUM_THREADS, sm, stream>>>(map, prm);
+    tc_loglike_kernel<KP, BF16, RESID><<<grid, NUM_THREADS, sm, stream>>>(map, prm);
     return cudaGetLastError();
 }
 
 template <int KP, bool BF16>
-cudaError_t launch_cps(int cps, const CUtensorMap &map, const Params &prm, int grid, size_t sm, cudaStream_t stream) {
-    return cps == 2 ? launch_kp<KP, BF16, 2>(map, prm, grid, sm, stream) : launch_kp<KP, BF16, 1>(map, prm, grid, sm, stream);
+cudaError_t launch_kp(const CUtensorMap &map, const Params &prm, int grid, size_t sm, cudaStream_t stream) {
+    return prm.resid ? launch_kpr<KP, BF16, true>(map, prm, grid, sm, stream)
+                     : launch_kpr<KP, BF16, false>(map, prm, grid, sm, stream);
 }
 
 cudaError_t launch_common(const ReqDesc *d_reqs, int n_reqs, int64_t n_items, int kp_max, int tc_pad_max,
-                          bool single_chunk, int precision, void *arena, int64_t arena_rows, unsigned *status,
-                          float *resid, int box_rows, int num_sms, cudaStream_t stream) {
+                          int precision, void *arena, int64_t arena_rows, unsigned *status, float *resid,
+                          int box_rows, int num_sms, cudaStream_t stream) {
     if (n_items == 0) return cudaSuccess;
     if (tc_map_init() != FG21_OK) return cudaErrorNotSupported;
     CUtensorMap map;
@@ -696,32 +752,38 @@ cudaError_t launch_common(const ReqDesc *d_reqs, int n_reqs, int64_t n_items, in
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    const int kp = kp_max <= 16 ? 16 : kp_max <= 32 ? 32 : 64;
+    if (tc_pad_max < 16 || tc_pad_max > TC_MAX || tc_pad_max % 16) return cudaErrorInvalidValue;
     Params prm;
     prm.reqs = d_reqs;
     prm.n_reqs = n_reqs;
     prm.n_items = n_items;
     prm.b_stage_bytes = ((4 * kp_max * tc_pad_max) + 1023) & ~1023;
     prm.acc_cols = tc_pad_max;
-    const int kp = kp_max <= 16 ? 16 : kp_max <= 32 ? 32 : 64;
-    // two channels per stage when every request fits one t-chunk and the
-    // doubled slots fit shared and tensor memory
-    const int cps = (single_chunk && kp <= 32 && RING * 2 * tc_pad_max <= 512) ? 2 : 1;
+    // as many stage slots (accumulator + weights in tensor memory) as fit, 2..4
+    const int per_slot = tc_pad_max + kp;
+    int ring = 512 / per_slot;
+    if (ring > MAX_RING) ring = MAX_RING;
+    if (ring < 2) return cudaErrorInvalidValue;
+    // ... and as fit shared memory next to the barriers
+    while (ring > 2 && smem_bytes(ring, prm.b_stage_bytes) > 227 * 1024) --ring;
+    prm.ring = ring;
     uint32_t cols = 32;
-    while (cols < (uint32_t)(RING * cps * tc_pad_max)) cols *= 2;
+    while (cols < (uint32_t)(ring * per_slot)) cols *= 2;
     if (cols > 512) return cudaErrorInvalidValue;
     prm.tmem_cols = cols;
     prm.status = status;
     prm.resid = resid;
     prm.box_rows = box_rows;
     // at least ~120 KB so that a single CTA (and its tensor memory) owns each SM
-    size_t sm = smem_bytes(kp, cps, prm.b_stage_bytes);
+    size_t sm = smem_bytes(ring, prm.b_stage_bytes);
     if (sm < 120 * 1024) sm = 120 * 1024;
     if (sm > 227 * 1024) return cudaErrorInvalidValue;
     const int grid = (int)(n_items < num_sms ? n_items : num_sms);
     const bool bf16 = precision == FG21_PREC_BF16X3;
-    if (kp == 16) return bf16 ? launch_cps<16, true>(cps, map, prm, grid, sm, stream) : launch_cps<16, false>(cps, map, prm, grid, sm, stream);
-    if (kp == 32) return bf16 ? launch_cps<32, true>(cps, map, prm, grid, sm, stream) : launch_cps<32, false>(cps, map, prm, grid, sm, stream);
-    return bf16 ? launch_cps<64, true>(cps, map, prm, grid, sm, stream) : launch_cps<64, false>(cps, map, prm, grid, sm, stream);
+    if (kp == 16) return bf16 ? launch_kp<16, true>(map, prm, grid, sm, stream) : launch_kp<16, false>(map, prm, grid, sm, stream);
+    if (kp == 32) return bf16 ? launch_kp<32, true>(map, prm, grid, sm, stream) : launch_kp<32, false>(map, prm, grid, sm, stream);
+    return bf16 ? launch_kp<64, true>(map, prm, grid, sm, stream) : launch_kp<64, false>(map, prm, grid, sm, stream);
 }
 
 }  // namespace
@@ -762,8 +824,8 @@ int tc_box_rows(const int64_t *tile_rows, int n) {
 }
 
 cudaError_t launch_tc(const TcLaunch &L, int num_sms, cudaStream_t stream) {
-    return launch_common(L.d_reqs, L.n_reqs, L.n_items, L.kp_max, L.tc_pad_max, L.single_chunk, L.precision,
-                         L.arena, L.arena_rows, L.status, nullptr, L.box_rows, num_sms, stream);
+    return launch_common(L.d_reqs, L.n_reqs, L.n_items, L.kp_max, L.tc_pad_max, L.precision, L.arena,
+                         L.arena_rows, L.status, nullptr, L.box_rows, num_sms, stream);
 }
 
 cudaError_t launch_tc_residuals(const ReqDesc *h_req, const ReqDesc *d_req, int precision, float *resid,
@@ -777,8 +839,8 @@ cudaError_t launch_tc_residuals(const ReqDesc *h_req, const ReqDesc *d_req, int 
     char *arena = h_req->tiles - h_req->tile_row0 * 128;
     const int64_t rows = h_req->tile_row0 + (int64_t)h_req->F * h_req->n_tchunks * h_req->tile_rows;
     const int64_t items = (int64_t)h_req->n_tiles * h_req->G;
-    return launch_common(d_req, 1, items, h_req->Kp, h_req->Tc_pad, h_req->n_tchunks == 1, precision, arena, rows,
-                         h_req->status, resid, tc_box_rows(&h_req->tile_rows, 1), sms, stream);
+    return launch_common(d_req, 1, items, h_req->Kp, h_req->Tc_pad, precision, arena, rows, h_req->status, resid,
+                         tc_box_rows(&h_req->tile_rows, 1), sms, stream);
 }
 
 }  // namespace fg21
