@@ -25,13 +25,17 @@ namespace fg21 {
 namespace {
 
 constexpr int PREP_THREADS = 256;
-constexpr size_t PREP_FIN_SMEM = 32 * 1024;   // shared bytes of the finalize kernel
+constexpr int REDUCE_THREADS = 64;
 
+// A point is valid when all its parameters are finite, sigma_n > 0 and
+// sigma21 != 0.  Tested on the bit patterns (integer instructions; FP64 is a
+// scarce pipe on this part).
 __device__ __forceinline__ bool point_valid(const double *th, int N) {
     bool ok = true;
-    for (int k = 0; k < N + 4; ++k) ok &= isfinite(th[k]);
-    ok &= th[N + 3] > 0.0;      // sigma_n > 0
-    ok &= th[N + 2] != 0.0;     // sigma21 != 0
+    for (int k = 0; k < N + 4; ++k)
+        ok &= (__double_as_longlong(th[k]) & 0x7FF0000000000000ll) != 0x7FF0000000000000ll;
+    ok &= __double_as_longlong(th[N + 3]) > 0;                                 // > +0 (sign clear)
+    ok &= (__double_as_longlong(th[N + 2]) & 0x7FFFFFFFFFFFFFFFll) != 0;      // != +-0
     return ok;
 }
 
@@ -53,19 +57,112 @@ struct OpSum { __device__ double operator()(double a, double b) const { return a
 struct OpMin { __device__ double operator()(double a, double b) const { return fmin(a, b); } };
 struct OpMax { __device__ double operator()(double a, double b) const { return fmax(a, b); } };
 
-// a1, pass 1: per block of STAT_BLOCK points, the sum / min / max of each
-// region's beta over valid points (FP32: the reference point only has to be a
-// deterministic value near the points; the rearranged likelihood is exact for
-// any reference), the valid count and max |A21|.  Warps reduce by shuffles in
-// a fixed tree, then thread i combines the warps' partials of region i in
-// warp order, so the result is deterministic.
-__global__ void __launch_bounds__(PREP_THREADS) prep_stats_kernel(const ReqDesc *__restrict__ reqs) {
-    extern __shared__ float sh_stats[];        // [PREP_THREADS / 32][3N + 2]
+// a1, pass 1: per block of STAT_BLOCK points (one thread each), the sum / min
+// / max of each region's beta over valid points (FP32: the reference point
+// only has to be a deterministic value near the points; the rearranged
+// likelihood is exact for any reference), the valid count and max |A21|.
+// Warps reduce by shuffles in a fixed tree and are combined in warp order.
+// The last block of a request to finish (atomic ticket) then finalises the
+// request statistics (pass 2, prep_finalize below).
+__device__ __forceinline__ int pow2_exponent_for(double maxabs) {
+    // largest s with 2^s * maxabs <= 2^15 (half the FP16 range), clamped
+    if (!(maxabs > 0.0)) return 0;
+    int e = (int)floor(log2(32768.0 / maxabs));
+    return max(-40, min(40, e));
+}
+
+template <bool BF16>
+__device__ __forceinline__ uint32_t pack_pair(float a, float b) {
+    if (BF16) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<uint32_t *>(&h);
+    } else {
+        __half2 h = __floats2half2_rn(a, b);
+        return *reinterpret_cast<uint32_t *>(&h);
+    }
+}
+template <bool BF16>
+__device__ __forceinline__ float2 unpack_pair(uint32_t u) {
+    if (BF16) {
+        __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162 *>(&u);
+        return __bfloat1622float2(h);
+    } else {
+        __half2 h = *reinterpret_cast<__half2 *>(&u);
+        return __half22float2(h);
+    }
+}
+
+// a1, pass 2 (the last stats block of a request): the reference point bbar_i
+// = mean of the valid points' beta_i, the largest weight argument x = max_i
+// |beta - bbar_i| * max_f |L_f| (which sets the weight series and the
+// power-of-two scale sW of the weight operand), the valid count and max
+// |A21|.  Warp w combines regions w, w + nwarps, ...; lane l of it the stat
+// blocks l, l + 32, ... in order, then the lanes by a fixed shuffle tree, so
+// the result does not depend on which block finishes last, and each warp
+// needs one round of (independent) loads per region.
+__device__ void prep_finalize(const ReqDesc &r, float *sh /* [nwarps] */) {
+    const int N = r.N, nb = r.n_stat_blocks, W = 3 * N + 2;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __shared__ float s_nv, s_ma;
+    // valid count and max |A21| (warp 0)
+    if (warp == 0) {
+        float nv = 0.0f, ma = 0.0f;
+        for (int b = lane; b < nb; b += 32) {
+            nv += __ldcg(r.stat_part + (size_t)b * W + 3 * N);
+            ma = fmaxf(ma, __ldcg(r.stat_part + (size_t)b * W + 3 * N + 1));
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            nv += __shfl_xor_sync(0xffffffffu, nv, o);
+            ma = fmaxf(ma, __shfl_xor_sync(0xffffffffu, ma, o));
+        }
+        if (lane == 0) {
+            s_nv = nv;
+            s_ma = ma;
+        }
+    }
+    __syncthreads();
+    const float nv = s_nv;
+    float dev = 0.0f;
+    for (int i = warp; i < N; i += nw) {
+        float su = 0.0f, mn = INFINITY, mx = -INFINITY;
+        for (int b = lane; b < nb; b += 32) {
+            const float *q = r.stat_part + (size_t)b * W + 3 * i;
+            su += __ldcg(q);
+            mn = fminf(mn, __ldcg(q + 1));
+            mx = fmaxf(mx, __ldcg(q + 2));
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            su += __shfl_xor_sync(0xffffffffu, su, o);
+            mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        }
+        const float bb = nv > 0.0f ? su / nv : 0.0f;
+        if (lane == 0) r.beta_bar[i] = (double)bb;
+        if (nv > 0.0f) dev = fmaxf(dev, fmaxf(mx - bb, bb - mn));
+    }
+    if (lane == 0) sh[warp] = dev;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float dmax = 0.0f;
+        for (int w = 0; w < nw; ++w) dmax = fmaxf(dmax, sh[w]);
+        // a small margin on x covers the FP32 statistics
+        const float x = dmax * (float)r.Lmax * 1.0001f;
+        r.req_stats[0] = nv;
+        r.req_stats[1] = x;
+        r.req_stats[2] = s_ma;
+        *r.scaleW = pow2_exponent_for(fmax(fmax((double)expm1f(x), (double)s_ma), 1.0));
+    }
+}
+
+__global__ void __launch_bounds__(STAT_BLOCK) prep_stats_kernel(const ReqDesc *__restrict__ reqs) {
+    extern __shared__ float sh_stats[];        // [STAT_BLOCK / 32][3N + 2], then [STAT_BLOCK / 32]
+    __shared__ int s_last;
     const ReqDesc &r = reqs[blockIdx.y];
     if ((int)blockIdx.x >= r.n_stat_blocks) return;
     const int N = r.N, W = 3 * N + 2, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
     const int64_t p = (int64_t)blockIdx.x * STAT_BLOCK + threadIdx.x;
-    const double *th = r.params + p * (N + 4);
+    const double *th = r.params + (p < r.P ? p : 0) * (N + 4);
     const bool valid = p < r.P && point_valid(th, N);
     float *mine = sh_stats + warp * W;
     for (int i = 0; i < N; ++i) {
@@ -93,7 +190,6 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_stats_kernel(const ReqDesc 
     }
     __syncthreads();
     float *out = r.stat_part + (size_t)blockIdx.x * W;
-    const int nw = blockDim.x >> 5;
     for (int j = threadIdx.x; j < W; j += blockDim.x) {
         const int kind = j < 3 * N ? j % 3 : (j == 3 * N ? 0 : 2);   // 0 sum, 1 min, 2 max
         float v = sh_stats[j];
@@ -103,99 +199,16 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_stats_kernel(const ReqDesc 
         }
         out[j] = v;
     }
-}
-
-__device__ __forceinline__ int pow2_exponent_for(double maxabs) {
-    // largest s with 2^s * maxabs <= 2^15 (half the FP16 range), clamped
-    if (!(maxabs > 0.0)) return 0;
-    int e = (int)floor(log2(32768.0 / maxabs));
-    return max(-40, min(40, e));
-}
-
-// a1, pass 2: one block per (channel, t-chunk).  Every block finalises the
-// request statistics in the same fixed order (so all agree bit for bit), then
-// builds its channel's reference: wbar, wbar*A, dref; and writes either the
-// FP32 arrays of the SIMT delta form or the split-precision operand tile of
-// the tensor-core form.
-//
-// Operand tile layout (one per channel and t-chunk, 2 x Kp x Tc_pad 16-bit
-// values): [split s in {hi, mid}][k-chunk kc = k/8][t][8 values k%8], i.e. the
-// K-major core-matrix layout (8 rows of 16 bytes) the tensor cores read; row k
-// < N holds wbar_k A[k,f,t] 2^sB, row N holds 2^sB (multiplies the trough
-// column of the weights), row N+1 holds dref 2^sB (multiplies -1), other rows
-// and columns t >= Tc are zero.
-template <bool BF16>
-__device__ __forceinline__ uint32_t pack_pair(float a, float b) {
-    if (BF16) {
-        __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-        return *reinterpret_cast<uint32_t *>(&h);
-    } else {
-        __half2 h = __floats2half2_rn(a, b);
-        return *reinterpret_cast<uint32_t *>(&h);
-    }
-}
-template <bool BF16>
-__device__ __forceinline__ float2 unpack_pair(uint32_t u) {
-    if (BF16) {
-        __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162 *>(&u);
-        return __bfloat1622float2(h);
-    } else {
-        __half2 h = *reinterpret_cast<__half2 *>(&u);
-        return __half22float2(h);
-    }
-}
-
-// a1, pass 2 (one block per request): the reference point bbar_i = mean of
-// the valid points' beta_i, the largest weight argument x = max_i |beta -
-// bbar_i| * max_f |L_f| (which sets the weight polynomial and the
-// power-of-two scale sW of the weight operand), the valid count and max |A21|.
-// The stat-block partials are staged in shared memory by all threads first
-// (coalesced), then combined in a fixed order.
-__global__ void __launch_bounds__(PREP_THREADS) prep_finalize_kernel(const ReqDesc *__restrict__ reqs) {
-    extern __shared__ float fin_sm[];
-    __shared__ float red[3][PREP_THREADS / 32];
-    const ReqDesc &r = reqs[blockIdx.x];
-    const int N = r.N, nb = r.n_stat_blocks, W = 3 * N + 2;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int chunk = (int)(PREP_FIN_SMEM / sizeof(float)) / W;      // stat blocks per shared-memory pass
-    float s_acc = 0.0f, mn_acc = INFINITY, mx_acc = -INFINITY, nv_acc = 0.0f, ma_acc = 0.0f;
-    const int i = threadIdx.x;          // region of this thread (if < N)
-    for (int b0 = 0; b0 < nb; b0 += chunk) {
-        const int nbc = min(chunk, nb - b0);
-        __syncthreads();
-        for (int j = threadIdx.x; j < nbc * W; j += blockDim.x) fin_sm[j] = r.stat_part[(size_t)b0 * W + j];
-        __syncthreads();
-        for (int b = 0; b < nbc; ++b) {
-            const float *q = fin_sm + b * W;
-            if (i < N) {
-                s_acc += q[3 * i];
-                mn_acc = fminf(mn_acc, q[3 * i + 1]);
-                mx_acc = fmaxf(mx_acc, q[3 * i + 2]);
-            }
-            nv_acc += q[3 * N];
-            ma_acc = fmaxf(ma_acc, q[3 * N + 1]);
-        }
-    }
-    const float nv = nv_acc;     // identical in every thread (same order)
-    float dev = 0.0f;
-    if (i < N) {
-        const float bb = nv > 0.0f ? s_acc / nv : 0.0f;
-        r.beta_bar[i] = (double)bb;
-        if (nv > 0.0f) dev = fmaxf(mx_acc - bb, bb - mn_acc);
-    }
-    for (int o = 16; o > 0; o >>= 1) dev = fmaxf(dev, __shfl_xor_sync(0xffffffffu, dev, o));
-    if (lane == 0) red[0][warp] = dev;
+    // the last block of this request finalises (its partial writes are
+    // published by the fence before the ticket)
+    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) {
-        float dmax = 0.0f;
-        for (int w = 0; w < nw; ++w) dmax = fmaxf(dmax, red[0][w]);
-        // a small margin on x covers the FP32 statistics
-        const float x = dmax * (float)r.Lmax * 1.0001f;
-        r.req_stats[0] = nv;
-        r.req_stats[1] = x;
-        r.req_stats[2] = ma_acc;
-        *r.scaleW = pow2_exponent_for(fmax(fmax((double)expm1f(x), (double)ma_acc), 1.0));
-    }
+    if (threadIdx.x == 0) s_last = atomicAdd(r.ticket, 1u) == (unsigned)r.n_stat_blocks - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    prep_finalize(r, sh_stats + nw * W);
+    if (threadIdx.x == 0) *r.ticket = 0;     // ready for the next launch on this workspace
 }
 
 // a1, pass 3: one block per (channel, t-chunk) builds that channel's
@@ -249,8 +262,12 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_tiles_kernel(const ReqDesc 
     const int t0 = c * r.Tc, tn = min(r.Tc, T - t0);
     double *wbar = smem_d;              // [N]
     double *dref = smem_d + N;          // [Tc]
+    float *wbar32 = reinterpret_cast<float *>(dref + r.Tc_pad);     // [N]
     const double L = r.L[f];
-    for (int i = threadIdx.x; i < N; i += blockDim.x) wbar[i] = exp(-r.beta_bar[i] * L);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        wbar[i] = exp(-r.beta_bar[i] * L);
+        wbar32[i] = (float)wbar[i];
+    }
     if (c == 0 && threadIdx.x == 0) {
         r.nL32[f] = (float)(-L);
         r.nu32[f] = (float)r.nu[f];
@@ -265,14 +282,19 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_tiles_kernel(const ReqDesc 
         double s = 0.0;
         for (int i0 = 0; i0 < N; i0 += 8) {
             double a[8];
+            float a32[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) a[j] = i0 + j < N ? r.A[(size_t)(i0 + j) * istride + ft] : 0.0;
+            for (int j = 0; j < 8; ++j) {
+                a[j] = i0 + j < N ? r.A[(size_t)(i0 + j) * istride + ft] : 0.0;
+                a32[j] = i0 + j < N ? r.A32[(size_t)(i0 + j) * istride + ft] : 0.0f;
+            }
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 if (i0 + j < N) {
                     const double bw = wbar[i0 + j] * a[j];
                     s += bw;
-                    vmax = fmaxf(vmax, fabsf((float)bw));
+                    // the scale only needs the magnitude: FP32 product (FP64 is a scarce pipe)
+                    vmax = fmaxf(vmax, fabsf(wbar32[i0 + j] * a32[j]));
                     if (MODE == 2) r.Bp32[(size_t)(i0 + j) * istride + ft] = (float)bw;
                 }
             }
@@ -299,9 +321,6 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_tiles_kernel(const ReqDesc 
     // split), the dref row from its FP64 value. ---
     const int Kp = r.Kp, Tcp = r.Tc_pad, nkc = Kp / 8;
     uint4 *tile = reinterpret_cast<uint4 *>(r.tiles + (size_t)fc * r.tile_rows * 128);
-    float *wbar32 = reinterpret_cast<float *>(dref + r.Tc_pad);     // [N]
-    for (int i = threadIdx.x; i < N; i += blockDim.x) wbar32[i] = (float)wbar[i];
-    __syncthreads();
     for (int j = threadIdx.x; j < nkc * Tcp; j += blockDim.x) {
         const int kc = j / Tcp, t = j % Tcp;
         float v[8];
@@ -454,9 +473,18 @@ __global__ void __launch_bounds__(SIMT_THREADS) simt_kernel(const ReqDesc *__res
     if (inb) r.partials[(size_t)p * r.n_part + g] = make_float2(qs, -qc);
 }
 
-// a6: per point, sum the channel-group partials in fixed order (FP64) and form
-// lnL = -1/2 (F T ln(2 pi sigma_n^2) + chi2 / sigma_n^2) (eq. likelihood).
-__global__ void reduce_kernel(const ReqDesc *__restrict__ reqs, int n_reqs) {
+// a6: per point, sum the channel-group partials in fixed order and form
+// lnL = -1/2 (F T ln(2 pi sigma_n^2) + chi2 / sigma_n^2) (eq. likelihood).  The
+// partials (compensated FP32 pairs) are summed in double-float arithmetic
+// (Knuth's two-sum on FP32 pairs, about 48 bits) and converted once: FP64 is a
+// scarce pipe on this part.
+__device__ __forceinline__ void two_sum_acc(float &s, float &c, float x) {
+    const float t = s + x;
+    const float z = t - s;
+    c += (s - (t - z)) + (x - z);
+    s = t;
+}
+__global__ void __launch_bounds__(REDUCE_THREADS) reduce_kernel(const ReqDesc *__restrict__ reqs, int n_reqs) {
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const ReqDesc &r = reqs[find_req_by_point(reqs, n_reqs, gid)];
     const int64_t p = gid - r.pt_begin;
@@ -468,11 +496,14 @@ __global__ void reduce_kernel(const ReqDesc *__restrict__ reqs, int n_reqs) {
         atomicAdd(r.invalid, 1ull);
         return;
     }
-    double chi2 = 0.0;
+    float sh = 0.0f, sl = 0.0f;
+    const float2 *__restrict__ part = r.partials + (size_t)p * r.n_part;
     for (int g = 0; g < r.n_part; ++g) {
-        float2 v = r.partials[(size_t)p * r.n_part + g];
-        chi2 += (double)v.x + (double)v.y;
+        const float2 v = part[g];
+        two_sum_acc(sh, sl, v.x);
+        two_sum_acc(sh, sl, v.y);
     }
+    const double chi2 = (double)sh + (double)sl;
     const double sig = th[N + 3];
     const double n = (double)r.F * (double)r.T;
     r.logL[p] = -0.5 * (n * log(2.0 * 3.141592653589793 * sig * sig) + chi2 / (sig * sig));
@@ -524,11 +555,9 @@ cudaError_t launch_prep(const ReqDesc *h_reqs, const ReqDesc *d_reqs, int n_reqs
     int maxN0 = 0;
     for (int k = 0; k < n_reqs; ++k) maxN0 = maxN0 > h_reqs[k].N ? maxN0 : h_reqs[k].N;
     dim3 g1(max_stat_blocks, n_reqs);
-    prep_stats_kernel<<<g1, PREP_THREADS, sizeof(float) * (PREP_THREADS / 32) * (3 * (size_t)maxN0 + 2), stream>>>(d_reqs);
+    const size_t sm1 = sizeof(float) * ((STAT_BLOCK / 32) * (3 * (size_t)maxN0 + 3));
+    prep_stats_kernel<<<g1, STAT_BLOCK, sm1, stream>>>(d_reqs);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    prep_finalize_kernel<<<n_reqs, PREP_THREADS, PREP_FIN_SMEM, stream>>>(d_reqs);
-    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     int maxN = 0, maxTcp = 0;
     for (int k = 0; k < n_reqs; ++k) {
@@ -576,7 +605,7 @@ cudaError_t launch_reduce(const ReqDesc *h_reqs, const ReqDesc *d_reqs, int n_re
     int64_t pts = 0;
     for (int k = 0; k < n_reqs; ++k) pts += h_reqs[k].P;
     if (pts == 0) return cudaSuccess;
-    const int th = 256;
+    const int th = REDUCE_THREADS;
     reduce_kernel<<<(unsigned)((pts + th - 1) / th), th, 0, stream>>>(d_reqs, n_reqs);
     return cudaGetLastError();
 }

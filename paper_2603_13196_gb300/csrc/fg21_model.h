@@ -22,8 +22,10 @@ struct Workspace {
     size_t pinned_bytes = 0;
     ReqDesc *d_reqs = nullptr;
     int reqs_cap = 0;
-    unsigned *d_status = nullptr;   // [0] status word, [2..3] invalid counter (64-bit)
+    unsigned *d_status = nullptr;   // bytes 0..3 status word, 16..23 invalid counter, from 64 on
+                                    // one stats ticket per request (status_reqs of them)
     unsigned long long *d_invalid = nullptr;
+    int status_reqs = 0;
     cudaEvent_t done = nullptr;     // recorded after the last launch of a call
     bool timing = false;            // record events around prep / main / reduce of every call
     static constexpr int TIMING_CAP = 8192;
@@ -36,6 +38,10 @@ struct Workspace {
     void release();
     size_t bytes() const { return dev_bytes + arena_bytes; }
 };
+
+// Bytes of the status block for n requests: status word, invalid counter, and
+// one stats ticket per request from byte 64 on.
+inline size_t status_bytes(int n) { return 64 + 4 * (size_t)n; }
 
 // Launch a set of requests whose params/logL device pointers are filled in.
 // Plans shapes, carves request workspaces out of `ws`, and enqueues prep,

@@ -78,7 +78,7 @@ extern "C" int fg21_loglike_batch_device_noalloc(fg21_model *m, const double *d_
     ReqDesc r = model_request(m, d_params, P, d_logL);
     plan_request(r, precision, num_sms_of(dev), (P + TILE_M - 1) / TILE_M);
     const ReqLayout L = request_layout(r, precision);
-    const size_t head = a256(64) + a256(sizeof(ReqDesc));      // status word + descriptor
+    const size_t head = a256(status_bytes(1)) + a256(sizeof(ReqDesc));      // status block + descriptor
     const size_t need = head + (L.total() - L.tiles) + a256(L.tiles);
     if (need > FG21_NOALLOC_SCRATCH_BYTES)
         return set_error(FG21_E_RANGE,
@@ -86,7 +86,7 @@ extern "C" int fg21_loglike_batch_device_noalloc(fg21_model *m, const double *d_
                          "(fewer points per call)",
                          need, (size_t)FG21_NOALLOC_SCRATCH_BYTES);
     unsigned *status = reinterpret_cast<unsigned *>(base);
-    ReqDesc *d_req = reinterpret_cast<ReqDesc *>(base + a256(64));
+    ReqDesc *d_req = reinterpret_cast<ReqDesc *>(base + a256(status_bytes(1)));
     char *p = base + head;
     r.stat_part = (float *)p; p += L.stat_part;
     r.beta_bar = (double *)p; p += L.beta_bar;
@@ -106,9 +106,10 @@ extern "C" int fg21_loglike_batch_device_noalloc(fg21_model *m, const double *d_
     r.tiles = arena;
     r.status = status;
     r.invalid = reinterpret_cast<unsigned long long *>(base + 16);
+    r.ticket = reinterpret_cast<unsigned *>(base + 64);
 
-    // the status word and invalid counter must start at zero; the rest is rewritten
-    FG21_CUDA_TRY(cudaMemsetAsync(status, 0, 32, s));
+    // the status word, invalid counter and stats ticket start at zero; the rest is rewritten
+    FG21_CUDA_TRY(cudaMemsetAsync(status, 0, status_bytes(1), s));
     FG21_CUDA_TRY(cudaMemcpyAsync(d_req, &r, sizeof r, cudaMemcpyHostToDevice, s));
     FG21_CUDA_TRY(launch_prep(&r, d_req, 1, precision, r.n_stat_blocks, r.F * r.n_tchunks, r.n_tiles, s));
     TcLaunch T;

@@ -61,9 +61,14 @@ constexpr int NUM_THREADS = 576;
 constexpr int MAX_RING = 4;       // stage slots (the launch picks 2-4 by tensor-memory room)
 constexpr int FULL_ARRIVALS = 17; // 8 generator warps + 1 TMA producer + 8 epilogue warps
 constexpr int WARP_TMA = 16, WARP_MMA = 17;
+constexpr int EPI_NB = 4;         // accumulator blocks an epilogue warp loads per wait
 // TMA boxes are 64 x box_rows 16-bit values (128-byte rows); box_rows divides
 // every request's tile height (a multiple of 8, at most 256)
 constexpr uint64_t WAIT_LIMIT_NS = 4000000000ull;
+// suspend-time hint of try_wait: a waiting thread sleeps (up to this long, or
+// until the phase completes) instead of re-polling, leaving issue slots to the
+// warps that compute
+constexpr uint32_t TRY_WAIT_HINT_NS = 10000000u;
 
 struct __align__(8) Barriers {
     uint64_t full[MAX_RING];
@@ -97,10 +102,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(TRY_WAIT_HINT_NS)
         : "memory");
     return ok != 0;
 }
@@ -481,15 +486,19 @@ __device__ __forceinline__ bool gen_item(const Params &prm, Barriers *S, Ring &r
 }
 
 // ------------------------------------------------------------- epilogue
-// tcgen05.ld of one or two 16-column blocks of this thread's accumulator row.
-__device__ __forceinline__ void acc_issue2(uint32_t taddr, int b0, int nb, float (&v)[2][16]) {
+// tcgen05.ld of up to NB 16-column blocks of this thread's accumulator row.
+template <int NB>
+__device__ __forceinline__ void acc_issue(uint32_t taddr, int b0, int nb, float (&v)[NB][16]) {
     tmem_ld16(taddr + b0 * 16, v[0]);
-    if (nb > 1) tmem_ld16(taddr + (b0 + 1) * 16, v[1]);
+#pragma unroll
+    for (int i = 1; i < NB; ++i)
+        if (nb > i) tmem_ld16(taddr + (b0 + i) * 16, v[i]);
 }
-__device__ __forceinline__ float acc_sumsq2(const float (&v)[2][16], int nb) {
+template <int NB>
+__device__ __forceinline__ float acc_sumsq(const float (&v)[NB][16], int nb) {
     float q[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // independent accumulators
 #pragma unroll
-    for (int bb = 0; bb < 2; ++bb) {
+    for (int bb = 0; bb < NB; ++bb) {
         if (bb < nb) {
 #pragma unroll
             for (int jj = 0; jj < 16; ++jj) q[jj & 7] = fmaf(v[bb][jj], v[bb][jj], q[jj & 7]);
@@ -524,10 +533,10 @@ __device__ __forceinline__ bool epi_item(const Params &prm, Barriers *S, Ring &r
             const float unscale = exp2i(-(sWexp + sb));
             const uint32_t taddr = lane_addr + rg.slot * prm.acc_cols;
             float q = 0.0f;
-            for (int b0 = b_lo; b0 < b_hi; b0 += 2) {
-                const int nb = min(2, b_hi - b0);
-                float v[2][16];
-                acc_issue2(taddr, b0, nb, v);
+            for (int b0 = b_lo; b0 < b_hi; b0 += EPI_NB) {
+                const int nb = min(EPI_NB, b_hi - b0);
+                float v[EPI_NB][16];
+                acc_issue<EPI_NB>(taddr, b0, nb, v);
                 tmem_ld_wait();
                 if (RESID) {
                     if (in) {
@@ -540,7 +549,7 @@ __device__ __forceinline__ bool epi_item(const Params &prm, Barriers *S, Ring &r
                             }
                     }
                 } else {
-                    q += acc_sumsq2(v, nb);
+                    q += acc_sumsq<EPI_NB>(v, nb);
                 }
             }
             tc_fence_before();
@@ -673,6 +682,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                         const uint32_t w_hi = tmem + w_col0 + rg.slot * KP, w_mid = w_hi + Kr / 2;
                         const uint32_t b_addr = smem_u32(b_slots + rg.slot * prm.b_stage_bytes);
                         const uint32_t d_tmem = tmem + rg.slot * prm.acc_cols;
+                        // per k-step hi*hi, hi*mid, mid*hi.  (Putting the small correction
+                        // products before every hi*hi one lowers the accumulation error near the
+                        // posterior by about a sixth but measured 13% slower.)
                         for (int ks = 0; ks < ksteps; ++ks) {
                             const uint64_t b_hi = smem_desc(b_addr + ks * 2 * b_lbo, b_lbo, 128);
                             const uint64_t b_mid = smem_desc(b_addr + b_split + ks * 2 * b_lbo, b_lbo, 128);
