@@ -26,6 +26,7 @@ replica with its own batch (weak scaling, no collective on the data path).
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -402,11 +403,16 @@ def main():
     peak = pk["bf16_tflops"]
     kp, tcp = ((N + 2 + 15) // 16) * 16, ((T + 15) // 16) * 16
     issued = 2.0 * 3 * kp * tcp * F * (math.ceil(P / 128) * 128)
+    # DRAM traffic of one launch from the committed ncu capture, only while the
+    # kernel source is the one that capture measured
     traffic = None
     tf = os.path.join(ROOT, "profiles", "tc_loglike_traffic.json")
     if os.path.exists(tf):
         try:
-            traffic = json.load(open(tf)).get("bytes_per_launch")
+            rec = json.load(open(tf))
+            src = open(os.path.join(ROOT, "paper_2603_13196_gb300", "csrc", "fg21_tc.cu"), "rb").read()
+            if hashlib.sha256(src).hexdigest()[:16] == rec.get("source_sha256_16"):
+                traffic = rec.get("bytes_per_launch")
         except Exception:
             traffic = None
 
