@@ -32,7 +32,7 @@ constexpr int TILE_M = 128;         // points per MMA tile (tcgen05 M)
 constexpr int TC_MAX = 192;         // max t-columns per MMA (tcgen05 N): two stage slots of
                                     // accumulators (<= 192 columns) plus weights (<= 64 columns)
                                     // fit the 512 tensor-memory columns of an SM
-constexpr int STAT_BLOCK = 128;     // points (threads) per statistics block of the per-request prep
+constexpr int STAT_BLOCK = 256;     // points (threads) per statistics block of the per-request prep
 constexpr int KP_MAX = 64;          // max padded K on the tensor path
 
 // Per-request descriptor, laid out identically on host and device.
@@ -78,7 +78,6 @@ struct ReqDesc {
     float *pts32;          // [n_tiles][Kp + 4][128] per point: beta - bbar (rows < Kp-2, zero
                            // beyond N), then A21, nu21, 1/(2 sigma21^2) (rows Kp-2..Kp); tensor path
     unsigned *status;      // device status word (shared by a launch)
-    unsigned *ticket;      // stats blocks finished (the last one finalises); zero between launches
     unsigned long long *invalid;  // invalid-point counter
 };
 

@@ -62,13 +62,17 @@ struct OpMax { __device__ double operator()(double a, double b) const { return f
 // only has to be a deterministic value near the points; the rearranged
 // likelihood is exact for any reference), the valid count and max |A21|.
 // Warps reduce by shuffles in a fixed tree and are combined in warp order.
-// The last block of a request to finish (atomic ticket) then finalises the
-// request statistics (pass 2, prep_finalize below).
-__device__ __forceinline__ int pow2_exponent_for(double maxabs) {
-    // largest s with 2^s * maxabs <= 2^15 (half the FP16 range), clamped
-    if (!(maxabs > 0.0)) return 0;
-    int e = (int)floor(log2(32768.0 / maxabs));
-    return max(-40, min(40, e));
+// Largest s with 2^s * maxabs <= 2^15 (half the FP16 range), clamped to
+// [-40, 40]; exact, from the exponent and mantissa bits (no FP64 log).
+__device__ __forceinline__ int pow2_exponent_for(float maxabs) {
+    if (!(maxabs > 0.0f)) return 0;
+    const unsigned u = __float_as_uint(maxabs);
+    const int eb = (int)((u >> 23) & 0xFFu), mant = (int)(u & 0x7FFFFFu);
+    if (eb == 0) return 40;                       // subnormal: far below the range
+    if (eb == 0xFF) return -40;
+    // maxabs in (2^(eb-128), 2^(eb-127)] ... ceil(log2 maxabs) = eb - 127 + (mant != 0)
+    const int s = 15 - (eb - 127) - (mant != 0 ? 1 : 0);
+    return max(-40, min(40, s));
 }
 
 template <bool BF16>
@@ -92,71 +96,69 @@ __device__ __forceinline__ float2 unpack_pair(uint32_t u) {
     }
 }
 
-// a1, pass 2 (the last stats block of a request): the reference point bbar_i
-// = mean of the valid points' beta_i, the largest weight argument x = max_i
-// |beta - bbar_i| * max_f |L_f| (which sets the weight series and the
-// power-of-two scale sW of the weight operand), the valid count and max
-// |A21|.  Warp w combines regions w, w + nwarps, ...; lane l of it the stat
-// blocks l, l + 32, ... in order, then the lanes by a fixed shuffle tree, so
-// the result does not depend on which block finishes last, and each warp
-// needs one round of (independent) loads per region.
-__device__ void prep_finalize(const ReqDesc &r, float *sh /* [nwarps] */) {
+// a1, pass 2, run by every block of the second prep kernel: the reference
+// point bbar_i = mean of the valid points' beta_i, the largest weight argument
+// x = max_i |beta - bbar_i| * max_f |L_f| (which sets the weight series and the
+// power-of-two scale sW of the weight operand), the valid count and max |A21|.
+// Thread j combines field j of every stat block in block order (one round of
+// independent loads per 16 blocks), so every block computes the same values
+// bit for bit; bbar goes to shared memory (`bbar_sh`), and block 0 of the
+// request publishes the results for the later kernels.
+struct Fin {
+    float nv, ma, x;
+    int sW;
+};
+__device__ Fin prep_finalize(const ReqDesc &r, float *sh /* [3N + 2 + nwarps] */, double *bbar_sh, bool publish) {
     const int N = r.N, nb = r.n_stat_blocks, W = 3 * N + 2;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    __shared__ float s_nv, s_ma;
-    // valid count and max |A21| (warp 0)
-    if (warp == 0) {
-        float nv = 0.0f, ma = 0.0f;
-        for (int b = lane; b < nb; b += 32) {
-            nv += __ldcg(r.stat_part + (size_t)b * W + 3 * N);
-            ma = fmaxf(ma, __ldcg(r.stat_part + (size_t)b * W + 3 * N + 1));
+    for (int j = threadIdx.x; j < W; j += blockDim.x) {
+        const int kind = j < 3 * N ? j % 3 : (j == 3 * N ? 0 : 2);   // 0 sum, 1 min, 2 max
+        const float *q = r.stat_part + j;
+        float v = kind == 0 ? 0.0f : kind == 1 ? INFINITY : -INFINITY;
+        // 16 independent loads in flight per round, combined in block order
+        for (int b0 = 0; b0 < nb; b0 += 16) {
+            float x[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) x[u] = b0 + u < nb ? __ldg(q + (size_t)(b0 + u) * W) : 0.0f;
+#pragma unroll
+            for (int u = 0; u < 16; ++u)
+                if (b0 + u < nb) v = kind == 0 ? v + x[u] : kind == 1 ? fminf(v, x[u]) : fmaxf(v, x[u]);
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            nv += __shfl_xor_sync(0xffffffffu, nv, o);
-            ma = fmaxf(ma, __shfl_xor_sync(0xffffffffu, ma, o));
-        }
-        if (lane == 0) {
-            s_nv = nv;
-            s_ma = ma;
-        }
+        sh[j] = v;
     }
     __syncthreads();
-    const float nv = s_nv;
+    const float nv = sh[3 * N], ma = sh[3 * N + 1];
     float dev = 0.0f;
-    for (int i = warp; i < N; i += nw) {
-        float su = 0.0f, mn = INFINITY, mx = -INFINITY;
-        for (int b = lane; b < nb; b += 32) {
-            const float *q = r.stat_part + (size_t)b * W + 3 * i;
-            su += __ldcg(q);
-            mn = fminf(mn, __ldcg(q + 1));
-            mx = fmaxf(mx, __ldcg(q + 2));
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            su += __shfl_xor_sync(0xffffffffu, su, o);
-            mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        }
-        const float bb = nv > 0.0f ? su / nv : 0.0f;
-        if (lane == 0) r.beta_bar[i] = (double)bb;
-        if (nv > 0.0f) dev = fmaxf(dev, fmaxf(mx - bb, bb - mn));
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const float bb = nv > 0.0f ? sh[3 * i] / nv : 0.0f;
+        bbar_sh[i] = (double)bb;
+        if (publish) r.beta_bar[i] = (double)bb;
+        if (nv > 0.0f) dev = fmaxf(dev, fmaxf(sh[3 * i + 2] - bb, bb - sh[3 * i + 1]));
     }
-    if (lane == 0) sh[warp] = dev;
+    for (int o = 16; o > 0; o >>= 1) dev = fmaxf(dev, __shfl_xor_sync(0xffffffffu, dev, o));
+    float *wred = sh + W;
+    if (lane == 0) wred[warp] = dev;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        float dmax = 0.0f;
-        for (int w = 0; w < nw; ++w) dmax = fmaxf(dmax, sh[w]);
-        // a small margin on x covers the FP32 statistics
-        const float x = dmax * (float)r.Lmax * 1.0001f;
+    float dmax = 0.0f;
+    for (int w = 0; w < nw; ++w) dmax = fmaxf(dmax, wred[w]);
+    Fin f;
+    // a small margin on x covers the FP32 statistics
+    f.x = dmax * (float)r.Lmax * 1.0001f;
+    f.nv = nv;
+    f.ma = ma;
+    f.sW = pow2_exponent_for(fmaxf(fmaxf(expm1f(f.x), ma), 1.0f));
+    if (publish && threadIdx.x == 0) {
         r.req_stats[0] = nv;
-        r.req_stats[1] = x;
-        r.req_stats[2] = s_ma;
-        *r.scaleW = pow2_exponent_for(fmax(fmax((double)expm1f(x), (double)s_ma), 1.0));
+        r.req_stats[1] = f.x;
+        r.req_stats[2] = ma;
+        *r.scaleW = f.sW;
     }
+    __syncthreads();
+    return f;
 }
 
 __global__ void __launch_bounds__(STAT_BLOCK) prep_stats_kernel(const ReqDesc *__restrict__ reqs) {
-    extern __shared__ float sh_stats[];        // [STAT_BLOCK / 32][3N + 2], then [STAT_BLOCK / 32]
-    __shared__ int s_last;
+    extern __shared__ float sh_stats[];        // [STAT_BLOCK / 32][3N + 2]
     const ReqDesc &r = reqs[blockIdx.y];
     if ((int)blockIdx.x >= r.n_stat_blocks) return;
     const int N = r.N, W = 3 * N + 2, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -199,16 +201,6 @@ __global__ void __launch_bounds__(STAT_BLOCK) prep_stats_kernel(const ReqDesc *_
         }
         out[j] = v;
     }
-    // the last block of this request finalises (its partial writes are
-    // published by the fence before the ticket)
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(r.ticket, 1u) == (unsigned)r.n_stat_blocks - 1;
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    prep_finalize(r, sh_stats + nw * W);
-    if (threadIdx.x == 0) *r.ticket = 0;     // ready for the next launch on this workspace
 }
 
 // a1, pass 3: one block per (channel, t-chunk) builds that channel's
@@ -229,7 +221,7 @@ __global__ void __launch_bounds__(STAT_BLOCK) prep_stats_kernel(const ReqDesc *_
 // thread per point reads them coalesced: rows k < Kp-2 hold beta_{p,k} - bbar_k
 // in FP32 (zero for k >= N), then A21, nu21 and 1/(2 sigma21^2).
 template <int MODE>
-__device__ __forceinline__ void prep_points(const ReqDesc &r, int tile) {
+__device__ __forceinline__ void prep_points(const ReqDesc &r, int tile, const double *bbar) {
     const int64_t p = (int64_t)tile * TILE_M + threadIdx.x;
     if (threadIdx.x >= TILE_M) return;
     const int N = r.N, R = r.Kp + 4;
@@ -237,7 +229,7 @@ __device__ __forceinline__ void prep_points(const ReqDesc &r, int tile) {
     const bool in = p < r.P;
     const double *th = r.params + (in ? p : 0) * (N + 4);
     for (int k = 0; k < r.Kp - 2; ++k)
-        out[(size_t)k * TILE_M] = (in && k < N) ? (float)(th[k] - r.beta_bar[k]) : 0.0f;
+        out[(size_t)k * TILE_M] = (in && k < N) ? (float)(th[k] - bbar[k]) : 0.0f;
     out[(size_t)(r.Kp - 2) * TILE_M] = in ? (float)th[N] : 0.0f;
     out[(size_t)(r.Kp - 1) * TILE_M] = in ? (float)th[N + 1] : 0.0f;
     const float s21 = in ? (float)th[N + 2] : 1.0f;
@@ -251,21 +243,26 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_tiles_kernel(const ReqDesc 
     __shared__ int s_scaleB;
     const ReqDesc &r = reqs[blockIdx.y];
     const int nfc = r.F * r.n_tchunks;
+    const int N = r.N, T = r.T;
+    if ((int)blockIdx.x >= nfc + (MODE <= 1 ? r.n_tiles : 0)) return;
+    // shared memory: bbar [N] FP64, finalise scratch [3N + 2 + 8] FP32 (rounded to
+    // doubles), wbar [N] FP64, dref [Tc_pad] FP64, wbar32 [N] FP32
+    double *bbar = smem_d;
+    float *fin_sh = reinterpret_cast<float *>(bbar + N);
+    double *wbar = bbar + N + (3 * N + 2 + 8 + 1) / 2;
+    double *dref = wbar + N;
+    float *wbar32 = reinterpret_cast<float *>(dref + r.Tc_pad);
+    prep_finalize(r, fin_sh, bbar, blockIdx.x == 0);
     if (MODE <= 1 && (int)blockIdx.x >= nfc) {
-        if ((int)blockIdx.x - nfc < r.n_tiles) prep_points<MODE>(r, blockIdx.x - nfc);
+        prep_points<MODE>(r, blockIdx.x - nfc, bbar);
         return;
     }
     const int fc = blockIdx.x;
-    if (fc >= nfc) return;
     const int f = fc / r.n_tchunks, c = fc % r.n_tchunks;
-    const int N = r.N, T = r.T;
     const int t0 = c * r.Tc, tn = min(r.Tc, T - t0);
-    double *wbar = smem_d;              // [N]
-    double *dref = smem_d + N;          // [Tc]
-    float *wbar32 = reinterpret_cast<float *>(dref + r.Tc_pad);     // [N]
     const double L = r.L[f];
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        wbar[i] = exp(-r.beta_bar[i] * L);
+        wbar[i] = exp(-bbar[i] * L);
         wbar32[i] = (float)wbar[i];
     }
     if (c == 0 && threadIdx.x == 0) {
@@ -311,7 +308,7 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_tiles_kernel(const ReqDesc 
     if (threadIdx.x == 0) {
         float v = sh[0];
         for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = fmaxf(v, (float)sh[w]);
-        s_scaleB = pow2_exponent_for((double)v);
+        s_scaleB = pow2_exponent_for(v);
         r.scaleB[fc] = s_scaleB;
     }
     __syncthreads();
@@ -555,7 +552,7 @@ cudaError_t launch_prep(const ReqDesc *h_reqs, const ReqDesc *d_reqs, int n_reqs
     int maxN0 = 0;
     for (int k = 0; k < n_reqs; ++k) maxN0 = maxN0 > h_reqs[k].N ? maxN0 : h_reqs[k].N;
     dim3 g1(max_stat_blocks, n_reqs);
-    const size_t sm1 = sizeof(float) * ((STAT_BLOCK / 32) * (3 * (size_t)maxN0 + 3));
+    const size_t sm1 = sizeof(float) * (STAT_BLOCK / 32) * (3 * (size_t)maxN0 + 2);
     prep_stats_kernel<<<g1, STAT_BLOCK, sm1, stream>>>(d_reqs);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -564,7 +561,8 @@ cudaError_t launch_prep(const ReqDesc *h_reqs, const ReqDesc *d_reqs, int n_reqs
         maxN = maxN > h_reqs[k].N ? maxN : h_reqs[k].N;
         maxTcp = maxTcp > h_reqs[k].Tc_pad ? maxTcp : h_reqs[k].Tc_pad;
     }
-    const size_t sm = sizeof(double) * ((size_t)maxN + maxTcp) + sizeof(float) * (size_t)maxN;
+    const size_t sm = sizeof(double) * (2 * (size_t)maxN + (3 * (size_t)maxN + 2 + 8 + 1) / 2 + maxTcp) +
+                      sizeof(float) * (size_t)maxN;
     const bool tc = precision == FG21_PREC_FP16X3 || precision == FG21_PREC_BF16X3;
     dim3 g2(max_F_chunks + (tc ? max_tiles : 0), n_reqs);
     switch (precision) {

@@ -38,17 +38,11 @@ int Workspace::ensure(size_t dev_need, size_t arena_need, size_t pinned_need, in
     if (!done) FG21_CUDA_TRY(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
     // staging and scratch may still be in use by the previous call on this workspace
     FG21_CUDA_TRY(cudaEventSynchronize(done));
-    if (!d_status || n_reqs > status_reqs) {
-        if (d_status) cudaFree(d_status);
-        d_status = nullptr;
-        status_reqs = 0;
-        const int want = std::max(n_reqs, 48);
+    if (!d_status) {
         void *p = nullptr;
-        FG21_CUDA_TRY(cudaMalloc(&p, status_bytes(want)));
-        FG21_CUDA_TRY(cudaMemset(p, 0, status_bytes(want)));
+        FG21_CUDA_TRY(cudaMalloc(&p, 256));
         d_status = (unsigned *)p;
         d_invalid = (unsigned long long *)((char *)p + 16);
-        status_reqs = want;
     }
     if (dev_need > dev_bytes) {
         if (dev) cudaFree(dev);
@@ -246,7 +240,6 @@ int enqueue_requests(Workspace &ws, std::vector<ReqDesc> &reqs, int precision, c
         row += (int64_t)(L.tiles / 128);
         r.status = ws.d_status;
         r.invalid = ws.d_invalid;
-        r.ticket = ws.d_status + 16 + k;
         kp_max = std::max(kp_max, r.Kp);
         tc_max = std::max(tc_max, r.Tc_pad);
         max_blocks = std::max(max_blocks, r.n_stat_blocks);
@@ -257,7 +250,7 @@ int enqueue_requests(Workspace &ws, std::vector<ReqDesc> &reqs, int precision, c
         return set_error(FG21_E_RANGE, "N = %d regions exceeds the tensor-core limit %d", kp_max - 2,
                          FG21_MAX_REGIONS_TC);
     std::memcpy(ws.pinned, reqs.data(), sizeof(ReqDesc) * n);
-    FG21_CUDA_TRY(cudaMemsetAsync(ws.d_status, 0, status_bytes(n), stream));   // status, counters, tickets
+    FG21_CUDA_TRY(cudaMemsetAsync(ws.d_status, 0, status_bytes(n), stream));   // status word, invalid counter
     FG21_CUDA_TRY(cudaMemcpyAsync(ws.d_reqs, ws.pinned, sizeof(ReqDesc) * n, cudaMemcpyHostToDevice, stream));
     cudaEvent_t *ev = ws.timing_slot();
     if (ev) FG21_CUDA_TRY(cudaEventRecord(ev[0], stream));

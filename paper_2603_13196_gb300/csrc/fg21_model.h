@@ -22,10 +22,8 @@ struct Workspace {
     size_t pinned_bytes = 0;
     ReqDesc *d_reqs = nullptr;
     int reqs_cap = 0;
-    unsigned *d_status = nullptr;   // bytes 0..3 status word, 16..23 invalid counter, from 64 on
-                                    // one stats ticket per request (status_reqs of them)
+    unsigned *d_status = nullptr;   // bytes 0..3 status word, 16..23 invalid counter
     unsigned long long *d_invalid = nullptr;
-    int status_reqs = 0;
     cudaEvent_t done = nullptr;     // recorded after the last launch of a call
     bool timing = false;            // record events around prep / main / reduce of every call
     static constexpr int TIMING_CAP = 8192;
@@ -39,9 +37,8 @@ struct Workspace {
     size_t bytes() const { return dev_bytes + arena_bytes; }
 };
 
-// Bytes of the status block for n requests: status word, invalid counter, and
-// one stats ticket per request from byte 64 on.
-inline size_t status_bytes(int n) { return 64 + 4 * (size_t)n; }
+// Bytes of the status block cleared per call: status word and invalid counter.
+inline size_t status_bytes(int) { return 32; }
 
 // Launch a set of requests whose params/logL device pointers are filled in.
 // Plans shapes, carves request workspaces out of `ws`, and enqueues prep,

@@ -106,9 +106,8 @@ extern "C" int fg21_loglike_batch_device_noalloc(fg21_model *m, const double *d_
     r.tiles = arena;
     r.status = status;
     r.invalid = reinterpret_cast<unsigned long long *>(base + 16);
-    r.ticket = reinterpret_cast<unsigned *>(base + 64);
 
-    // the status word, invalid counter and stats ticket start at zero; the rest is rewritten
+    // the status word and invalid counter start at zero; the rest is rewritten
     FG21_CUDA_TRY(cudaMemsetAsync(status, 0, status_bytes(1), s));
     FG21_CUDA_TRY(cudaMemcpyAsync(d_req, &r, sizeof r, cudaMemcpyHostToDevice, s));
     FG21_CUDA_TRY(launch_prep(&r, d_req, 1, precision, r.n_stat_blocks, r.F * r.n_tchunks, r.n_tiles, s));
