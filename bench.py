@@ -9,8 +9,10 @@ contraction, trough, residual and square (a2-a5), per-point reduction and logL
 (a6).
 
   value        logL evals/s of the split-FP16 tensor-core path, params and
-               logL device-resident (CUDA events on the launch stream, L2
-               flushed by a 256 MiB write between timed steps)
+               logL device-resident, the step replayed from a CUDA graph
+               captured once (fg21_graph_launch; CUDA events on the launch
+               stream, L2 flushed by a 256 MiB write between timed steps)
+  direct_call  the same step through fg21_loglike_batch_device every time
   e2e          the same through the host-buffer C-ABI call (params H2D and
                logL D2H inside the timed region)
   fp32_direct  the plain FP32 SIMT kernel on the same device and protocol
@@ -362,20 +364,49 @@ def main():
         return dict(ms_per_step=dev_ms / K, main_ms=main_ms / calls, prep_ms=prep_ms / calls,
                     reduce_ms=red_ms / calls, wall=(w0, w1), invalid=inv)
 
+    def timed_graph(K, W):
+        """The step replayed from a CUDA graph captured once (fg21_graph_create / _launch):
+        the same kernels on the same device buffers, without the per-call host work."""
+        g = fg21.fg21_graph_create(model, d_params.data_ptr(), P, d_logL.data_ptr(), args.precision)
+        for _ in range(W):
+            flush.zero_()
+            g.launch(sptr)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        w0 = time.time()
+        for k in range(K):
+            flush.zero_()
+            evs[k][0].record(stream)
+            g.launch(sptr)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        w1 = time.time()
+        inv = g.sync_status(sptr)
+        g.close()
+        return dict(ms_per_step=sum(a.elapsed_time(b) for a, b in evs) / K, wall=(w0, w1), invalid=inv)
+
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     time.sleep(0.3)
-    res = timed(args.precision, args.steps, max(3, args.warmup))
-    clk = clocks.summary(*res["wall"])
+    # the headline: K graph replays of the step; then the direct device call (per-kernel
+    # times) and the plain FP32 comparator
+    gres = timed_graph(args.steps, max(3, args.warmup))
+    clk = clocks.summary(*gres["wall"])
+    res = timed(args.precision, max(3, args.steps // 4), max(3, args.warmup))
     direct = timed("fp32_direct", max(3, args.steps // 4), 3)
     clocks.stop()
 
     # the max over ranks of the per-step device time
-    step_ms = res["ms_per_step"]
+    step_ms, call_ms = gres["ms_per_step"], res["ms_per_step"]
     if ws > 1:
-        t = torch.tensor([step_ms, direct["ms_per_step"]], dtype=torch.float64, device=dev)
+        t = torch.tensor([step_ms, call_ms, direct["ms_per_step"]], dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        step_ms, direct_ms = float(t[0]), float(t[1])
+        step_ms, call_ms, direct_ms = float(t[0]), float(t[1]), float(t[2])
     else:
         direct_ms = direct["ms_per_step"]
     value = P * ws / (step_ms * 1e-3)
@@ -423,11 +454,16 @@ def main():
         "data": "synthetic (seeded sky, beam, data and prior draws; random-init equivalent)",
         "config": {"workload": WORKLOAD, "N": N, "F": F, "T": T, "P_per_gpu": P, "npix": wl.npix,
                    "precision": args.precision, "parallelism": f"replicas x{ws}",
+                   "path": "fg21_graph_launch: the step (status clear, prep, tensor-core, reduce kernels) "
+                           "replayed from a CUDA graph captured once on the device buffers",
                    "l2": "flushed by a 256 MiB write between timed steps (not timed)",
                    "build_regions_s": round(build_s, 3)},
         "fp32_direct": {"value": P * ws / (direct_ms * 1e-3), "unit": "logL evals/s", "ms_per_step": direct_ms,
                         "speedup_of_value": (P * ws / (step_ms * 1e-3)) / (P * ws / (direct_ms * 1e-3))},
         "kernels_ms": {"prep": res["prep_ms"], "tc_loglike": res["main_ms"], "reduce": res["reduce_ms"]},
+        "direct_call": {"value": P * ws / (call_ms * 1e-3), "unit": "logL evals/s", "ms_per_step": call_ms,
+                        "what": "the same step through fg21_loglike_batch_device each time (plan, descriptor "
+                                "upload and four launches per call)"},
         "e2e": {"value": P * ws / e2e_s, "unit": "logL evals/s", "h2d_bytes_per_step": int(params.nbytes),
                 "d2h_bytes_per_step": int(P * 8)},
         "gpu_launches": 4 * args.steps,

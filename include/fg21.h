@@ -71,6 +71,7 @@ extern "C" {
 /* ------------------------------------------------------------------ types */
 typedef struct fg21_model fg21_model;     /* opaque: resident A, B, data of one observation + partition */
 typedef struct fg21_server fg21_server;   /* opaque: serving loop */
+typedef struct fg21_graph fg21_graph;     /* opaque: a captured evaluation of a fixed batch */
 
 /* Pixelised sky (Sec. 2.1).  dirs: unit vectors in the frame of `zenith`;
  * t230: the 230 MHz template [K]; beta: per-pixel spectral index. */
@@ -249,6 +250,32 @@ int fg21_model_eval(fg21_model *m, const double *params, int64_t P, double *T_mo
  * the SIMT precisions run per model).  Same invalid-point rules. */
 int fg21_loglike_multi(fg21_model *const *models, const double *const *params, const int64_t *P,
                        double *const *logL, int n_models, int precision, void *stream);
+
+/* CUDA-graph evaluation of a fixed batch (eq. likelihood, Sec. 2.3.1, over
+ * eq. fast_forward_model, Sec. 2.2, for the points a nested sampler proposes,
+ * Sec. 3).  fg21_graph_create_multi plans the batch of n_models requests
+ * (model k, P[k] points, DEVICE buffers d_params[k] [P[k]][N_k+4] and
+ * d_logL[k] [P[k]] on the current device), sizes a workspace owned by the
+ * graph, uploads the request descriptors and captures one evaluation (status
+ * clear, prep, tensor-core or SIMT kernel, reduction) into a CUDA graph.
+ * fg21_graph_launch replays it on `stream`; each replay reads the parameter
+ * buffers as they are when it runs and writes the logL buffers, with the same
+ * arithmetic (and the same results, bit for bit) as fg21_loglike_multi /
+ * fg21_loglike_batch_device on that batch.  The models and the buffers must
+ * outlive the graph; replays of one graph must be ordered (one stream, or
+ * events) since they share its workspace.  fg21_graph_sync_status waits for
+ * `stream` and returns the status and invalid-point count of the last replay.
+ * Errors: FG21_E_ARG (bad arguments, wrong device, no points), FG21_E_RANGE
+ * (N above the tensor-core limit for FP16X3 / BF16X3), FG21_E_NOMEM,
+ * FG21_E_CUDA (capture failed); FG21_E_DEVICE from sync_status as for the
+ * other calls. */
+int fg21_graph_create(fg21_model *m, const double *d_params, int64_t P, double *d_logL, int precision,
+                      fg21_graph **out);
+int fg21_graph_create_multi(fg21_model *const *models, const double *const *d_params, const int64_t *P,
+                            double *const *d_logL, int n_models, int precision, fg21_graph **out);
+int fg21_graph_launch(fg21_graph *g, void *stream);
+int fg21_graph_sync_status(fg21_graph *g, void *stream, int64_t *invalid_count);
+int fg21_graph_destroy(fg21_graph *g);
 
 /* ---------------------------------------------------------------- serving */
 /* Continuous-batching likelihood server for many concurrent nested-sampling

@@ -195,19 +195,22 @@ ReqLayout request_layout(const ReqDesc &r, int precision) {
     return L;
 }
 
-int enqueue_requests(Workspace &ws, std::vector<ReqDesc> &reqs, int precision, cudaStream_t stream) {
+int prepare_requests(Workspace &ws, std::vector<ReqDesc> &reqs, int precision, Prepared &pp) {
     const int n = (int)reqs.size();
+    pp = Prepared{};
+    pp.n = n;
+    pp.precision = precision;
     if (n == 0) return FG21_OK;
     const bool tc = precision == FG21_PREC_FP16X3 || precision == FG21_PREC_BF16X3;
     int dev = 0;
     FG21_CUDA_TRY(cudaGetDevice(&dev));
-    const int num_sms = num_sms_of(dev);
+    pp.num_sms = num_sms_of(dev);
     size_t dev_need = 0, arena_need = 0;
     std::vector<ReqLayout> lay(n);
     for (int k = 0; k < n; ++k) {
         // each request is planned as if alone, so its work split (and with it
         // every rounding) does not depend on what it is batched with
-        plan_request(reqs[k], precision, num_sms, (reqs[k].P + TILE_M - 1) / TILE_M);
+        plan_request(reqs[k], precision, pp.num_sms, (reqs[k].P + TILE_M - 1) / TILE_M);
         lay[k] = request_layout(reqs[k], precision);
         arena_need += lay[k].tiles;
         dev_need += lay[k].total() - lay[k].tiles;
@@ -216,7 +219,8 @@ int enqueue_requests(Workspace &ws, std::vector<ReqDesc> &reqs, int precision, c
     if (rc) return rc;
     char *p = ws.dev;
     int64_t item = 0, row = 0, pts = 0;
-    int kp_max = 16, tc_max = 16, max_blocks = 1, max_fchunks = 1, max_tiles = 1;
+    int kp_max = 16, tc_max = 16;
+    pp.max_blocks = pp.max_fchunks = pp.max_tiles = 1;
     for (int k = 0; k < n; ++k) {
         ReqDesc &r = reqs[k];
         const ReqLayout &L = lay[k];
@@ -242,22 +246,16 @@ int enqueue_requests(Workspace &ws, std::vector<ReqDesc> &reqs, int precision, c
         r.invalid = ws.d_invalid;
         kp_max = std::max(kp_max, r.Kp);
         tc_max = std::max(tc_max, r.Tc_pad);
-        max_blocks = std::max(max_blocks, r.n_stat_blocks);
-        max_fchunks = std::max(max_fchunks, r.F * r.n_tchunks);
-        max_tiles = std::max(max_tiles, r.n_tiles);
+        pp.max_blocks = std::max(pp.max_blocks, r.n_stat_blocks);
+        pp.max_fchunks = std::max(pp.max_fchunks, r.F * r.n_tchunks);
+        pp.max_tiles = std::max(pp.max_tiles, r.n_tiles);
     }
     if (tc && kp_max > KP_MAX)
         return set_error(FG21_E_RANGE, "N = %d regions exceeds the tensor-core limit %d", kp_max - 2,
                          FG21_MAX_REGIONS_TC);
-    std::memcpy(ws.pinned, reqs.data(), sizeof(ReqDesc) * n);
-    FG21_CUDA_TRY(cudaMemsetAsync(ws.d_status, 0, status_bytes(n), stream));   // status word, invalid counter
-    FG21_CUDA_TRY(cudaMemcpyAsync(ws.d_reqs, ws.pinned, sizeof(ReqDesc) * n, cudaMemcpyHostToDevice, stream));
-    cudaEvent_t *ev = ws.timing_slot();
-    if (ev) FG21_CUDA_TRY(cudaEventRecord(ev[0], stream));
-    FG21_CUDA_TRY(launch_prep(reqs.data(), ws.d_reqs, n, precision, max_blocks, max_fchunks, max_tiles, stream));
-    if (ev) FG21_CUDA_TRY(cudaEventRecord(ev[1], stream));
+    pp.tc = tc;
     if (tc) {
-        TcLaunch L;
+        TcLaunch &L = pp.tcl;
         L.d_reqs = ws.d_reqs;
         L.n_reqs = n;
         L.n_items = item;
@@ -270,14 +268,41 @@ int enqueue_requests(Workspace &ws, std::vector<ReqDesc> &reqs, int precision, c
         L.arena = ws.arena;
         L.arena_rows = row;
         L.status = ws.d_status;
-        cudaError_t e = launch_tc(L, num_sms, stream);
+    }
+    std::memcpy(ws.pinned, reqs.data(), sizeof(ReqDesc) * n);
+    return FG21_OK;
+}
+
+int launch_requests(Workspace &ws, const std::vector<ReqDesc> &reqs, const Prepared &pp, cudaStream_t stream,
+                    bool upload, bool timing) {
+    const int n = pp.n;
+    if (n == 0) return FG21_OK;
+    FG21_CUDA_TRY(cudaMemsetAsync(ws.d_status, 0, status_bytes(n), stream));   // status word, invalid counter
+    if (upload)
+        FG21_CUDA_TRY(cudaMemcpyAsync(ws.d_reqs, ws.pinned, sizeof(ReqDesc) * n, cudaMemcpyHostToDevice, stream));
+    cudaEvent_t *ev = timing ? ws.timing_slot() : nullptr;
+    if (ev) FG21_CUDA_TRY(cudaEventRecord(ev[0], stream));
+    FG21_CUDA_TRY(launch_prep(reqs.data(), ws.d_reqs, n, pp.precision, pp.max_blocks, pp.max_fchunks, pp.max_tiles,
+                              stream));
+    if (ev) FG21_CUDA_TRY(cudaEventRecord(ev[1], stream));
+    if (pp.tc) {
+        cudaError_t e = launch_tc(pp.tcl, pp.num_sms, stream);
         if (e != cudaSuccess) return cuda_error(e, "tensor-core likelihood launch");
     } else {
-        FG21_CUDA_TRY(launch_simt(reqs.data(), ws.d_reqs, n, precision, stream));
+        FG21_CUDA_TRY(launch_simt(reqs.data(), ws.d_reqs, n, pp.precision, stream));
     }
     if (ev) FG21_CUDA_TRY(cudaEventRecord(ev[2], stream));
     FG21_CUDA_TRY(launch_reduce(reqs.data(), ws.d_reqs, n, stream));
     if (ev) FG21_CUDA_TRY(cudaEventRecord(ev[3], stream));
+    return FG21_OK;
+}
+
+int enqueue_requests(Workspace &ws, std::vector<ReqDesc> &reqs, int precision, cudaStream_t stream) {
+    Prepared pp;
+    int rc = prepare_requests(ws, reqs, precision, pp);
+    if (rc || pp.n == 0) return rc;
+    rc = launch_requests(ws, reqs, pp, stream, true, true);
+    if (rc) return rc;
     FG21_CUDA_TRY(cudaEventRecord(ws.done, stream));
     return FG21_OK;
 }

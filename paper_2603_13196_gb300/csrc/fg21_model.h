@@ -46,6 +46,21 @@ inline size_t status_bytes(int) { return 32; }
 // are cleared first.  Returns FG21_OK or an error code.
 int enqueue_requests(Workspace &ws, std::vector<ReqDesc> &reqs, int precision, cudaStream_t stream);
 
+// The two halves of enqueue_requests: plan, size the workspace, carve and fill
+// the descriptors (staged in ws.pinned) ...
+struct Prepared {
+    int n = 0, precision = 0, num_sms = 1;
+    int max_blocks = 1, max_fchunks = 1, max_tiles = 1;
+    bool tc = false;
+    TcLaunch tcl{};
+};
+int prepare_requests(Workspace &ws, std::vector<ReqDesc> &reqs, int precision, Prepared &pp);
+// ... and enqueue the status clear, the descriptor upload (if `upload`) and
+// the kernels.  Nothing here allocates or synchronises, so it can be captured
+// into a CUDA graph.
+int launch_requests(Workspace &ws, const std::vector<ReqDesc> &reqs, const Prepared &pp, cudaStream_t stream,
+                    bool upload, bool timing);
+
 int num_sms_of(int device);
 
 }  // namespace fg21

@@ -86,6 +86,11 @@ _SIGS = {
     "fg21_model_timing": (C.c_int, [_P, C.c_int]),
     "fg21_model_timing_totals": (C.c_int, [_P, _P, _P, _P, _P]),
     "fg21_loglike_multi": (C.c_int, [_P, _P, _P, _P, C.c_int, C.c_int, _P]),
+    "fg21_graph_create": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int, _P]),
+    "fg21_graph_create_multi": (C.c_int, [_P, _P, _P, _P, C.c_int, C.c_int, _P]),
+    "fg21_graph_launch": (C.c_int, [_P, _P]),
+    "fg21_graph_sync_status": (C.c_int, [_P, _P, _P]),
+    "fg21_graph_destroy": (C.c_int, [_P]),
     "fg21_serve_create": (C.c_int, [_P, _P]),
     "fg21_serve_destroy": (C.c_int, [_P]),
     "fg21_serve_register_run": (C.c_int, [_P, _P, _P]),
@@ -300,6 +305,68 @@ def fg21_loglike_multi(models: Sequence[Model], params: Sequence[np.ndarray], pr
     LL = (C.c_void_p * n)(*[_ptr(o) for o in outs])
     _check(lib().fg21_loglike_multi(H, PP, NP, LL, n, _prec(precision), stream or None), "fg21_loglike_multi")
     return outs
+
+
+# ------------------------------------------------------------ CUDA graphs
+class Graph:
+    """A captured likelihood evaluation of a fixed batch on fixed device buffers
+    (fg21_graph_*); `launch` replays it.  The models and buffers must outlive it."""
+
+    def __init__(self, handle: int, models, buffers):
+        self.handle = C.c_void_p(handle)
+        self._keep = (list(models), list(buffers))
+
+    def launch(self, stream: int = 0):
+        fg21_graph_launch(self, stream)
+
+    def sync_status(self, stream: int = 0) -> int:
+        return fg21_graph_sync_status(self, stream)
+
+    def close(self):
+        if self.handle.value:
+            lib().fg21_graph_destroy(self.handle)
+            self.handle = C.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fg21_graph_create(m: Model, d_params: int, P: int, d_logL: int, precision="fp16x3") -> Graph:
+    """Device buffers given as integer addresses (e.g. torch tensor data_ptr())."""
+    out = C.c_void_p()
+    _check(lib().fg21_graph_create(m.handle, d_params, int(P), d_logL, _prec(precision), C.byref(out)),
+           "fg21_graph_create")
+    return Graph(out.value, [m], [])
+
+
+def fg21_graph_create_multi(models: Sequence[Model], d_params: Sequence[int], P: Sequence[int],
+                            d_logL: Sequence[int], precision="fp16x3") -> Graph:
+    n = len(models)
+    H = (C.c_void_p * n)(*[m.handle.value for m in models])
+    PP = (C.c_void_p * n)(*[int(x) for x in d_params])
+    NP = (C.c_int64 * n)(*[int(x) for x in P])
+    LL = (C.c_void_p * n)(*[int(x) for x in d_logL])
+    out = C.c_void_p()
+    _check(lib().fg21_graph_create_multi(H, PP, NP, LL, n, _prec(precision), C.byref(out)),
+           "fg21_graph_create_multi")
+    return Graph(out.value, models, [])
+
+
+def fg21_graph_launch(g: Graph, stream: int = 0):
+    _check(lib().fg21_graph_launch(g.handle, stream or None), "fg21_graph_launch")
+
+
+def fg21_graph_sync_status(g: Graph, stream: int = 0) -> int:
+    inv = C.c_int64(0)
+    _check(lib().fg21_graph_sync_status(g.handle, stream or None, C.byref(inv)), "fg21_graph_sync_status")
+    return inv.value
+
+
+def fg21_graph_destroy(g: Graph):
+    g.close()
 
 
 # ------------------------------------------------------------------ serving

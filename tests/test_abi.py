@@ -53,6 +53,10 @@ def test_argument_errors_without_device(L):
     assert L.fg21_serve_wait(nul, 1, 0) == fg21.FG21_E_ARG
     assert L.fg21_model_destroy(nul) == fg21.FG21_OK
     assert L.fg21_serve_destroy(nul) == fg21.FG21_OK
+    assert L.fg21_graph_create_multi(nul, nul, nul, nul, 1, 0, nul) == fg21.FG21_E_ARG
+    assert L.fg21_graph_launch(nul, nul) == fg21.FG21_E_ARG
+    assert L.fg21_graph_sync_status(nul, nul, nul) == fg21.FG21_E_ARG
+    assert L.fg21_graph_destroy(nul) == fg21.FG21_OK
     assert "NULL" in L.fg21_last_error().decode()
 
 
