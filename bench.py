@@ -334,6 +334,9 @@ def main():
     sptr = stream.cuda_stream
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
+    # the library's measured work split for this model and batch size
+    cpg, tune_ms = fg21.fg21_autotune(model, d_params.data_ptr(), P, d_logL.data_ptr(), args.precision, sptr)
+
     def step(prec):
         fg21.fg21_loglike_batch_device(model, d_params.data_ptr(), P, d_logL.data_ptr(), prec, sptr)
 
@@ -454,6 +457,7 @@ def main():
         "data": "synthetic (seeded sky, beam, data and prior draws; random-init equivalent)",
         "config": {"workload": WORKLOAD, "N": N, "F": F, "T": T, "P_per_gpu": P, "npix": wl.npix,
                    "precision": args.precision, "parallelism": f"replicas x{ws}",
+                   "channels_per_item": cpg, "channels_per_item_from": "fg21_autotune (measured)",
                    "path": "fg21_graph_launch: the step (status clear, prep, tensor-core, reduce kernels) "
                            "replayed from a CUDA graph captured once on the device buffers",
                    "l2": "flushed by a 256 MiB write between timed steps (not timed)",

@@ -226,6 +226,21 @@ int fg21_loglike_batch_device_noalloc(fg21_model *m, const double *d_params, int
  * reported an internal failure. */
 int fg21_model_sync_status(fg21_model *m, void *stream, int64_t *invalid_count);
 
+/* Measured choice of the work split of requests of P points of model m at
+ * `precision` (the number of channels per work item of the batched
+ * evaluation of eq. likelihood over eq. fast_forward_model): runs one
+ * evaluation per candidate split (every distinct channels-per-item value that
+ * cuts the F channels into 1..32 groups) five times on the caller's DEVICE
+ * buffers d_params [P][N+4] / d_logL [P] (d_logL is overwritten with valid
+ * results), times the last four with CUDA events on `stream`, keeps the split
+ * with the smallest median in the model and returns it (and its time in ms).
+ * Every later plan of model m at `precision` for the same number of 128-point
+ * tiles (alone, batched, served or captured in a graph) uses it, so a
+ * request's results still depend only on its own model and size.  Blocks
+ * until the timings are done.  Errors as fg21_loglike_batch_device. */
+int fg21_autotune(fg21_model *m, const double *d_params, int64_t P, double *d_logL, int precision, void *stream,
+                  int32_t *best_cpg, double *best_ms);
+
 /* Kernel timing of a model's calls: with enable != 0 (which also clears the
  * record), every later likelihood call on m records CUDA events on its launch
  * stream around the per-request preparation (a1), the main likelihood kernel

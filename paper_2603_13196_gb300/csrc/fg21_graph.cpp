@@ -64,7 +64,7 @@ int fg21_graph_create_multi(fg21_model *const *models, const double *const *d_pa
             graph_free(g);
             return set_error(FG21_E_RANGE, "model %d: N = %d above the tensor-core limit", k, m->N);
         }
-        if (P[k] > 0) g->reqs.push_back(model_request(m, d_params[k], P[k], d_logL[k]));
+        if (P[k] > 0) g->reqs.push_back(model_request(m, d_params[k], P[k], d_logL[k], precision));
     }
     if (g->reqs.empty()) {
         graph_free(g);

@@ -56,6 +56,7 @@ struct ReqDesc {
     int Kp;                // K = N + 2 padded to a multiple of 16 (tensor path)
     int Tc, Tc_pad, n_tchunks;   // t-chunks: Tc columns each (last may be shorter), padded to 16
     int G, ch_per_group;         // channel groups per 128-point tile
+    int cpg_hint;                // channels per group chosen by the autotuner for this size (0 = model)
     int n_part;                  // partial sums per point (G on the SIMT forms, 2G on the tensor path)
     int n_tiles;                 // ceil(P / 128)
     int n_stat_blocks;           // ceil(P / STAT_BLOCK)

@@ -168,7 +168,7 @@ void plan_request(ReqDesc &r, int precision, int num_sms, int64_t total_tiles) {
     r.Tc_pad = round16(r.Tc);
     r.n_tiles = (int)((r.P + TILE_M - 1) / TILE_M);
     r.n_stat_blocks = (int)((r.P + STAT_BLOCK - 1) / STAT_BLOCK);
-    int cpg = choose_channels_per_group(total_tiles, r.F, num_sms);
+    int cpg = r.cpg_hint > 0 ? std::min(r.F, r.cpg_hint) : choose_channels_per_group(total_tiles, r.F, num_sms);
     r.G = (r.F + cpg - 1) / cpg;
     r.ch_per_group = (r.F + r.G - 1) / r.G;
     const bool tc = precision == FG21_PREC_FP16X3 || precision == FG21_PREC_BF16X3;
@@ -349,9 +349,14 @@ int model_upload(fg21_model *m) {
     return FG21_OK;
 }
 
-ReqDesc model_request(const fg21_model *m, const double *d_params, int64_t P, double *d_logL) {
+ReqDesc model_request(fg21_model *m, const double *d_params, int64_t P, double *d_logL, int precision) {
     ReqDesc r;
     std::memset(&r, 0, sizeof r);
+    {
+        std::lock_guard<std::mutex> lk(m->tune_mu);
+        const auto it = m->tuned_cpg.find({precision, (int)((P + TILE_M - 1) / TILE_M)});
+        r.cpg_hint = it == m->tuned_cpg.end() ? 0 : it->second;
+    }
     r.A = m->d_A;
     r.B = m->d_B;
     r.data = m->d_data;
@@ -410,7 +415,7 @@ static int run_host(fg21_model *m, const double *params, int64_t P, double *logL
     auto *io = &iob;
     std::memcpy(io->h, params, pbytes);
     FG21_CUDA_TRY(cudaMemcpyAsync(io->d_params, io->h, pbytes, cudaMemcpyHostToDevice, stream));
-    std::vector<ReqDesc> reqs{model_request(m, io->d_params, P, io->d_logL)};
+    std::vector<ReqDesc> reqs{model_request(m, io->d_params, P, io->d_logL, precision)};
     int rc = enqueue_requests(m->ws, reqs, precision, stream);
     if (rc) return rc;
     char *h_log = io->h + align256(pbytes);
@@ -505,8 +510,69 @@ int fg21_loglike_batch_device(fg21_model *m, const double *d_params, int64_t P, 
     std::lock_guard<std::mutex> lk(m->mu);
     rc = device_guard(m);
     if (rc) return rc;
-    std::vector<ReqDesc> reqs{model_request(m, d_params, P, d_logL)};
+    std::vector<ReqDesc> reqs{model_request(m, d_params, P, d_logL, precision)};
     return enqueue_requests(m->ws, reqs, precision, (cudaStream_t)stream);
+}
+
+int fg21_autotune(fg21_model *m, const double *d_params, int64_t P, double *d_logL, int precision, void *stream,
+                  int32_t *best_cpg, double *best_ms) {
+    if (!m) return set_error(FG21_E_ARG, "NULL model");
+    if (P <= 0 || !d_params || !d_logL) return set_error(FG21_E_ARG, "bad params/logL/P");
+    int rc = check_precision(m, precision);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(m->mu);
+    rc = device_guard(m);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    // candidates: every distinct channels-per-group value that splits the
+    // channels into 1..32 groups, plus the planner's model choice
+    std::vector<int> cand;
+    for (int G = 1; G <= std::min(m->F, 32); ++G) {
+        const int cpg = (m->F + G - 1) / G;
+        if (std::find(cand.begin(), cand.end(), cpg) == cand.end()) cand.push_back(cpg);
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    FG21_CUDA_TRY(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_error(cudaGetLastError(), "cudaEventCreate");
+    }
+    const bool was_timing = m->ws.timing;
+    m->ws.timing = false;
+    int best = 0;
+    double best_t = 1e300;
+    for (int cpg : cand) {
+        float ms[4];
+        for (int rep = 0; rep < 5 && rc == FG21_OK; ++rep) {
+            std::vector<ReqDesc> reqs{model_request(m, d_params, P, d_logL, precision)};
+            reqs[0].cpg_hint = cpg;
+            if (rep > 0 && cudaEventRecord(e0, s) != cudaSuccess) rc = cuda_error(cudaGetLastError(), "event");
+            if (rc == FG21_OK) rc = enqueue_requests(m->ws, reqs, precision, s);
+            if (rc == FG21_OK && rep > 0) {
+                if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                    cudaEventElapsedTime(&ms[rep - 1], e0, e1) != cudaSuccess)
+                    rc = cuda_error(cudaGetLastError(), "autotune timing");
+            }
+        }
+        if (rc) break;
+        std::sort(ms, ms + 4);
+        const double t = 0.5 * (ms[1] + ms[2]);      // median of 4 (one warm-up run discarded)
+        if (t < best_t) {
+            best_t = t;
+            best = cpg;
+        }
+    }
+    m->ws.timing = was_timing;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    {
+        std::lock_guard<std::mutex> tl(m->tune_mu);
+        m->tuned_cpg[{precision, (int)((P + TILE_M - 1) / TILE_M)}] = best;
+    }
+    if (best_cpg) *best_cpg = best;
+    if (best_ms) *best_ms = best_t;
+    return FG21_OK;
 }
 
 int fg21_model_sync_status(fg21_model *m, void *stream, int64_t *invalid_count) {
@@ -591,7 +657,7 @@ int fg21_model_eval(fg21_model *m, const double *params, int64_t P, double *T_mo
             out = cuda_error(cudaGetLastError(), "model_eval H2D");
             break;
         }
-        std::vector<ReqDesc> reqs{model_request(m, d_params, P, d_logL)};
+        std::vector<ReqDesc> reqs{model_request(m, d_params, P, d_logL, precision)};
         out = enqueue_requests(m->ws, reqs, precision, s);
         if (out) break;
         cudaError_t e = launch_model_eval(&reqs[0], m->ws.d_reqs, precision, d_out, s);
@@ -661,7 +727,7 @@ int fg21_loglike_multi(fg21_model *const *models, const double *const *params, c
         const size_t pb = sizeof(double) * (size_t)P[k] * (models[k]->N + 4);
         std::memcpy(h_io + poff[k], params[k], pb);
         reqs.push_back(model_request(models[k], (const double *)((char *)d_io + poff[k]), P[k],
-                                     (double *)((char *)d_io + loff[k])));
+                                     (double *)((char *)d_io + loff[k]), precision));
         map.push_back(k);
     }
     if (reqs.empty()) return FG21_OK;

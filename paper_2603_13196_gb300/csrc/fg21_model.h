@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -78,11 +79,14 @@ struct fg21_model {
     char *io_d = nullptr, *io_h = nullptr;   // params/logL staging of the host-buffer calls
     size_t io_cap = 0;
     fg21::Workspace ws;
+    std::map<std::pair<int, int>, int> tuned_cpg;   // (precision, 128-point tiles) -> channels per group
+    std::mutex tune_mu;                              // guards tuned_cpg
     std::mutex mu;
 };
 
 namespace fg21 {
 int model_upload(fg21_model *m);
-// A request descriptor of model m (params/logL device pointers left for the caller).
-ReqDesc model_request(const fg21_model *m, const double *d_params, int64_t P, double *d_logL);
+// A request descriptor of model m for `precision` (carrying the autotuned work
+// split for its size, if any).
+ReqDesc model_request(fg21_model *m, const double *d_params, int64_t P, double *d_logL, int precision);
 }  // namespace fg21

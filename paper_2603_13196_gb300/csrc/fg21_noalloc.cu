@@ -75,7 +75,7 @@ extern "C" int fg21_loglike_batch_device_noalloc(fg21_model *m, const double *d_
     if (rc) return rc;
 
     // plan and lay out exactly as the regular call does, then carve the array
-    ReqDesc r = model_request(m, d_params, P, d_logL);
+    ReqDesc r = model_request(m, d_params, P, d_logL, precision);
     plan_request(r, precision, num_sms_of(dev), (P + TILE_M - 1) / TILE_M);
     const ReqLayout L = request_layout(r, precision);
     const size_t head = a256(status_bytes(1)) + a256(sizeof(ReqDesc));      // status block + descriptor

@@ -170,7 +170,7 @@ bool launch_batch(fg21_server *s, int k, std::unique_lock<std::mutex> &lk) {
             Ticket *t = work[j].first;
             std::memcpy(sl.h_io + poff[j], t->params.data(), sizeof(double) * t->params.size());
             reqs.push_back(model_request(work[j].second, (const double *)(sl.d_io + poff[j]), t->P,
-                                         (double *)(sl.d_io + sl.loff[j])));
+                                         (double *)(sl.d_io + sl.loff[j]), s->opts.precision));
         }
         if (cudaMemcpyAsync(sl.d_io, sl.h_io, lbase, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess) {
             rc = cuda_error(cudaGetLastError(), "serve H2D");

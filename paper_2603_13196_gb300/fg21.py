@@ -82,6 +82,7 @@ _SIGS = {
     "fg21_loglike_batch_device": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int, _P]),
     "fg21_loglike_batch_device_noalloc": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int, _P]),
     "fg21_model_sync_status": (C.c_int, [_P, _P, _P]),
+    "fg21_autotune": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int, _P, _P, _P]),
     "fg21_model_eval": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int, _P]),
     "fg21_model_timing": (C.c_int, [_P, C.c_int]),
     "fg21_model_timing_totals": (C.c_int, [_P, _P, _P, _P, _P]),
@@ -305,6 +306,14 @@ def fg21_loglike_multi(models: Sequence[Model], params: Sequence[np.ndarray], pr
     LL = (C.c_void_p * n)(*[_ptr(o) for o in outs])
     _check(lib().fg21_loglike_multi(H, PP, NP, LL, n, _prec(precision), stream or None), "fg21_loglike_multi")
     return outs
+
+
+def fg21_autotune(m: Model, d_params: int, P: int, d_logL: int, precision="fp16x3", stream: int = 0):
+    """Measured work split for (m, precision, P); returns (channels per item, ms)."""
+    cpg, ms = C.c_int32(0), C.c_double(0.0)
+    _check(lib().fg21_autotune(m.handle, d_params, int(P), d_logL, _prec(precision), stream or None,
+                               C.byref(cpg), C.byref(ms)), "fg21_autotune")
+    return cpg.value, ms.value
 
 
 # ------------------------------------------------------------ CUDA graphs
