@@ -129,6 +129,35 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def composite_bound(N, F, T, P, kp, tcp, cpg, kernel_ms, pk, sm_count=152, clock_ghz=2.07):
+    """The tensor kernel's lower bound as the largest of three floors, against its
+    measured time.  Per-SM rates from microbenchmarks on this GPU: one M = 128,
+    K = 16 MMA per 128 * N * 16 / 4096 cycles when issued back to back; the FMA
+    pipe takes 128 FP32 lane-operations per cycle (a packed FP32x2 instruction
+    is two).  Work: the busiest CTA's stages x 3 split MMAs per 16-wide K step;
+    weights: (degree-8 series + split) = 20 FMA-pipe lane-operations per
+    evaluated region pair per point per channel; epilogue: one FFMA per
+    accumulator column; HBM: operand tiles + point operands once."""
+    tiles = -(-P // 128)
+    G = -(-F // cpg)
+    items = tiles * G
+    max_items = -(-items // sm_count)
+    ch = -(-F // G)
+    stages = max_items * ch
+    mma_cycles = stages * 3 * (kp // 16) * (128 * tcp * 16 / 4096)
+    t_mma = mma_cycles / (clock_ghz * 1e9)
+    pairs = min(kp // 2, ((N + 1) // 2 + 3) // 4 * 4)
+    lane_ops = P * F * (pairs * 20 + tcp)
+    t_fma = lane_ops / (128 * sm_count * clock_ghz * 1e9)
+    bytes_ = F * 2 * kp * tcp * 2 + tiles * (kp + 4) * 128 * 4
+    t_hbm = bytes_ / (pk["hbm_gbs"] * 1e9)
+    t_bound = max(t_mma, t_fma, t_hbm)
+    return {"t_bound_us": t_bound * 1e6, "t_measured_us": kernel_ms * 1e3, "frac": t_bound / (kernel_ms * 1e-3),
+            "terms_us": {"tensor": t_mma * 1e6, "fma_pipe": t_fma * 1e6, "hbm": t_hbm * 1e6},
+            "rates": "MMA 4096 MAC/cycle/SM (128x112x16 every 56 cycles, measured), FMA pipe 128 lane-ops/"
+                     "cycle/SM, clock 2.07 GHz, hbm_gbs measured"}
+
+
 def cpu_baseline(sky, obs, N, params, seconds):
     """Time the FP64 oracle's likelihood on a bounded sample of the batch."""
     import numpy as np
@@ -475,7 +504,8 @@ def main():
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": f"{pk_kind} dense bf16 burst (fp16 same nominal rate)",
                      "issued_mma_tflops": issued / (res["main_ms"] * 1e-3) / 1e12,
-                     "issued_frac": issued / (res["main_ms"] * 1e-3) / 1e12 / peak},
+                     "issued_frac": issued / (res["main_ms"] * 1e-3) / 1e12 / peak,
+                     "composite": composite_bound(N, F, T, P, kp, tcp, cpg, res["main_ms"], pk)},
         "clocks": clk,
         "macs_per_s": N * F * T * P * ws / (step_ms * 1e-3),
     }
