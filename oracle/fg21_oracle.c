@@ -30,7 +30,14 @@
  *    and then level 2^m - 1 is not contained in level 2^m);
  *  - ties: recursive -> largest mass, then lowest beta_a; hierarchical ->
  *    widest, then lowest beta_a;
- *  - N_alpha = 1 (alpha = 1): the paper fits spectral-index masks only.
+ *  - N_alpha = 1 (alpha = 1) in the routines without the _ab suffix: the
+ *    paper fits spectral-index masks only.  The _ab routines add amplitude
+ *    masks M_alpha,i and scale factors alpha_i (eqs. forward_model,
+ *    chromatic_function, fast_forward_model); their regions partition a
+ *    per-pixel field that the caller supplies (the paper leaves the amplitude
+ *    masks' field open; the tests use ln T230), with the same Algorithms and
+ *    conventions as the spectral-index masks, and their parameter rows are
+ *    [beta_1..beta_Nb, alpha_1..alpha_Na, A21, nu21, sigma21, sigma_n].
  */
 #include <math.h>
 #include <stdint.h>
@@ -463,6 +470,141 @@ void orc_chi2(int N, int F, int T, const double *A, const double *B, const doubl
                 for (int i = 0; i < N; ++i)
                     fg += A[((size_t)i * F + f) * T + t] * pow(nu[f] / nu0, -th[i]);
                 double r = data[(size_t)f * T + t] - (fg + t_cmb * B[(size_t)f * T + t] + s21);
+                sum += r * r;
+            }
+        }
+        chi2[p] = sum;
+    }
+}
+
+/* ------------------------------------------------------- amplitude masks */
+
+/* Chromatic response functions with both sets of masks (Sec. 2.2, eq.
+ * chromatic_function, dOmega = 4 pi / Npix):
+ *   K[i,j,f,t] = (1/Npix) sum_pix M_alpha,i(pix) M_beta,j(pix) (T230 - T_CMB) D(pix,f,t)
+ * with M_alpha,i(pix) = [lab_a(pix) == i] and M_beta,j(pix) = [lab_b(pix) == j].
+ * K is [Na][Nb][F][T].  B[f,t] = (1/Npix) sum_pix D as in orc_precompute.
+ * Each (i, j, f, t) sums over all pixels in index order. */
+int orc_precompute_ab(int64_t npix, const double *dirs, const double *t230, const int32_t *lab_a, int Na,
+                      const int32_t *lab_b, int Nb, int F, int T, const double *zenith,
+                      const double *beam_p, double t_cmb, double *K, double *B)
+{
+#pragma omp parallel for schedule(dynamic)
+    for (int ft = 0; ft < F * T; ++ft) {
+        int f = ft / T, t = ft % T;
+        for (int i = 0; i < Na; ++i) {
+            for (int j = 0; j < Nb; ++j) {
+                double s = 0.0;
+                for (int64_t q = 0; q < npix; ++q) {
+                    double ma = lab_a[q] == i ? 1.0 : 0.0;
+                    double mb = lab_b[q] == j ? 1.0 : 0.0;
+                    s += ma * mb * (t230[q] - t_cmb) * orc_beam(dirs + 3 * q, zenith + 3 * t, beam_p[f]);
+                }
+                K[(((size_t)i * Nb + j) * F + f) * T + t] = s / (double)npix;
+            }
+        }
+        double b = 0.0;
+        for (int64_t q = 0; q < npix; ++q) b += orc_beam(dirs + 3 * q, zenith + 3 * t, beam_p[f]);
+        B[(size_t)f * T + t] = b / (double)npix;
+    }
+    return 0;
+}
+
+/* Foreground of eq. fast_forward_model for one parameter row at (f, t):
+ *   sum_i sum_j alpha_i K[i,j,f,t] (nu_f/nu0)^-beta_j. */
+static double orc_fg_ab(int Na, int Nb, int F, int T, const double *K, const double *nu, double nu0,
+                        const double *th, int f, int t)
+{
+    double fg = 0.0;
+    for (int i = 0; i < Na; ++i)
+        for (int j = 0; j < Nb; ++j)
+            fg += th[Nb + i] * K[(((size_t)i * Nb + j) * F + f) * T + t] * pow(nu[f] / nu0, -th[j]);
+    return fg;
+}
+
+/* Fast forward model with amplitude masks (eq. fast_forward_model with the
+ * discrete B) plus the trough:
+ *   M[p,f,t] = sum_i sum_j alpha_i K[i,j,f,t] (nu_f/nu0)^-beta_j + T_CMB B[f,t] + T21(nu_f).
+ * params rows: [beta_1..beta_Nb, alpha_1..alpha_Na, A21, nu21, sigma21, sigma_n]. */
+void orc_fast_model_ab(int Na, int Nb, int F, int T, const double *K, const double *B, const double *nu,
+                       double nu0, double t_cmb, const double *params, int64_t P, double *M)
+{
+    const int NP = Nb + Na;
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < P; ++p) {
+        const double *th = params + (size_t)p * (NP + 4);
+        for (int f = 0; f < F; ++f) {
+            double s21 = orc_t21(nu[f], th[NP], th[NP + 1], th[NP + 2]);
+            for (int t = 0; t < T; ++t)
+                M[((size_t)p * F + f) * T + t] =
+                    orc_fg_ab(Na, Nb, F, T, K, nu, nu0, th, f, t) + t_cmb * B[(size_t)f * T + t] + s21;
+        }
+    }
+}
+
+/* Per-pixel forward model with amplitude masks (eq. forward_model) integrated
+ * against the beam (eq. simantenna's integral), without K:
+ *   M[p,f,t] = (1/Npix) sum_pix D [alpha_{lab_a(pix)} (T230 - T_CMB)(nu/nu0)^-beta_{lab_b(pix)}
+ *              + T_CMB] + T21(nu_f). */
+void orc_pixel_model_ab(int64_t npix, const double *dirs, const double *t230, const int32_t *lab_a, int Na,
+                        const int32_t *lab_b, int Nb, int F, const double *nu, double nu0, int T,
+                        const double *zenith, const double *beam_p, double t_cmb, const double *params,
+                        int64_t P, double *M)
+{
+    const int NP = Nb + Na;
+#pragma omp parallel for schedule(dynamic)
+    for (int64_t pft = 0; pft < P * F * T; ++pft) {
+        int64_t p = pft / ((int64_t)F * T);
+        int f = (int)((pft / T) % F), t = (int)(pft % T);
+        const double *th = params + (size_t)p * (NP + 4);
+        double s = 0.0;
+        for (int64_t q = 0; q < npix; ++q) {
+            double d = orc_beam(dirs + 3 * q, zenith + 3 * t, beam_p[f]);
+            double tm = th[Nb + lab_a[q]] * (t230[q] - t_cmb) * pow(nu[f] / nu0, -th[lab_b[q]]) + t_cmb;
+            s += d * tm;
+        }
+        M[pft] = s / (double)npix + orc_t21(nu[f], th[NP], th[NP + 1], th[NP + 2]);
+    }
+}
+
+/* Gaussian log-likelihood (Sec. 2.3.1, eq. likelihood) over the model of
+ * orc_fast_model_ab:
+ *   lnL = -1/2 sum_{f,t} [ ln(2 pi sigma_n^2) + (D - M)^2 / sigma_n^2 ]. */
+void orc_loglike_ab(int Na, int Nb, int F, int T, const double *K, const double *B, const double *data,
+                    const double *nu, double nu0, double t_cmb, const double *params, int64_t P, double *logL)
+{
+    const int NP = Nb + Na;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t p = 0; p < P; ++p) {
+        const double *th = params + (size_t)p * (NP + 4);
+        double sig = th[NP + 3];
+        double sum = 0.0;
+        for (int f = 0; f < F; ++f) {
+            double s21 = orc_t21(nu[f], th[NP], th[NP + 1], th[NP + 2]);
+            for (int t = 0; t < T; ++t) {
+                double m = orc_fg_ab(Na, Nb, F, T, K, nu, nu0, th, f, t) + t_cmb * B[(size_t)f * T + t] + s21;
+                double r = data[(size_t)f * T + t] - m;
+                sum += log(2.0 * 3.14159265358979323846 * sig * sig) + r * r / (sig * sig);
+            }
+        }
+        logL[p] = -0.5 * sum;
+    }
+}
+
+/* Chi-square part only, sum (D - M)^2 over the model of orc_fast_model_ab. */
+void orc_chi2_ab(int Na, int Nb, int F, int T, const double *K, const double *B, const double *data,
+                 const double *nu, double nu0, double t_cmb, const double *params, int64_t P, double *chi2)
+{
+    const int NP = Nb + Na;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t p = 0; p < P; ++p) {
+        const double *th = params + (size_t)p * (NP + 4);
+        double sum = 0.0;
+        for (int f = 0; f < F; ++f) {
+            double s21 = orc_t21(nu[f], th[NP], th[NP + 1], th[NP + 2]);
+            for (int t = 0; t < T; ++t) {
+                double r = data[(size_t)f * T + t] -
+                           (orc_fg_ab(Na, Nb, F, T, K, nu, nu0, th, f, t) + t_cmb * B[(size_t)f * T + t] + s21);
                 sum += r * r;
             }
         }

@@ -49,6 +49,20 @@ def lib():
         L.orc_simulate_data.restype = None
         L.orc_simulate_data.argtypes = [C.c_int64, _D, _D, _D, C.c_int, _D, C.c_double, C.c_int,
                                         _D, _D, C.c_double, _D, C.c_double, C.c_void_p, _D]
+        L.orc_precompute_ab.restype = C.c_int
+        L.orc_precompute_ab.argtypes = [C.c_int64, _D, _D, _I32, C.c_int, _I32, C.c_int, C.c_int, C.c_int,
+                                        _D, _D, C.c_double, _D, _D]
+        L.orc_fast_model_ab.restype = None
+        L.orc_fast_model_ab.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _D, _D, _D, C.c_double,
+                                        C.c_double, _D, C.c_int64, _D]
+        L.orc_pixel_model_ab.restype = None
+        L.orc_pixel_model_ab.argtypes = [C.c_int64, _D, _D, _I32, C.c_int, _I32, C.c_int, C.c_int, _D,
+                                         C.c_double, C.c_int, _D, _D, C.c_double, _D, C.c_int64, _D]
+        for name in ("orc_loglike_ab", "orc_chi2_ab"):
+            fn = getattr(L, name)
+            fn.restype = None
+            fn.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _D, _D, _D, _D, C.c_double, C.c_double,
+                           _D, C.c_int64, _D]
         for name in ("orc_loglike", "orc_chi2"):
             fn = getattr(L, name)
             fn.restype = None
@@ -163,6 +177,100 @@ def chi2(A, B, data, obs, params):
     lib().orc_chi2(N, F, T, _c(A), _c(B), _c(data), _c(obs.nu), obs.nu0, obs.t_cmb, params, P,
                    out)
     return out
+
+
+# ------------------------------------------------------ amplitude masks
+# Models with N_alpha amplitude regions as well (eqs. forward_model,
+# chromatic_function, fast_forward_model of Sec. 2.2).  K[Na, Nb, F, T];
+# params[P, Nb+Na+4] = [beta_1..beta_Nb, alpha_1..alpha_Na, A21, nu21,
+# sigma21, sigma_n].
+
+def precompute_ab(sky, obs, labels_a, Na, labels_b, Nb):
+    """K[i,j,f,t] over the intersections of amplitude region i and
+    spectral-index region j (eq. chromatic_function), and B[f,t]."""
+    K = np.empty((Na, Nb, obs.F, obs.T))
+    B = np.empty((obs.F, obs.T))
+    rc = lib().orc_precompute_ab(sky.npix, _c(sky.dirs), _c(sky.t230), _c(labels_a, np.int32), Na,
+                                 _c(labels_b, np.int32), Nb, obs.F, obs.T, _c(obs.zenith),
+                                 _c(obs.beam_p), obs.t_cmb, K, B)
+    assert rc == 0
+    return K, B
+
+
+def fast_model_ab(K, B, obs, params):
+    """eq. fast_forward_model with amplitude masks + T21 -> M[P, F, T]."""
+    params = _c(np.atleast_2d(params))
+    Na, Nb, F, T = K.shape
+    P = params.shape[0]
+    assert params.shape[1] == Nb + Na + 4
+    M = np.empty((P, F, T))
+    lib().orc_fast_model_ab(Na, Nb, F, T, _c(K), _c(B), _c(obs.nu), obs.nu0, obs.t_cmb, params, P, M)
+    return M
+
+
+def pixel_model_ab(sky, obs, labels_a, Na, labels_b, Nb, params):
+    """eq. forward_model with amplitude masks, integrated per pixel -> M[P, F, T]."""
+    params = _c(np.atleast_2d(params))
+    P = params.shape[0]
+    assert params.shape[1] == Nb + Na + 4
+    M = np.empty((P, obs.F, obs.T))
+    lib().orc_pixel_model_ab(sky.npix, _c(sky.dirs), _c(sky.t230), _c(labels_a, np.int32), Na,
+                             _c(labels_b, np.int32), Nb, obs.F, _c(obs.nu), obs.nu0, obs.T,
+                             _c(obs.zenith), _c(obs.beam_p), obs.t_cmb, params, P, M)
+    return M
+
+
+def loglike_ab(K, B, data, obs, params):
+    """Sec. 2.3.1 eq. likelihood over the amplitude-mask model -> logL[P]."""
+    params = _c(np.atleast_2d(params))
+    Na, Nb, F, T = K.shape
+    P = params.shape[0]
+    assert params.shape[1] == Nb + Na + 4
+    out = np.empty(P)
+    lib().orc_loglike_ab(Na, Nb, F, T, _c(K), _c(B), _c(data), _c(obs.nu), obs.nu0, obs.t_cmb, params,
+                         P, out)
+    return out
+
+
+def chi2_ab(K, B, data, obs, params):
+    params = _c(np.atleast_2d(params))
+    Na, Nb, F, T = K.shape
+    P = params.shape[0]
+    out = np.empty(P)
+    lib().orc_chi2_ab(Na, Nb, F, T, _c(K), _c(B), _c(data), _c(obs.nu), obs.nu0, obs.t_cmb, params, P,
+                      out)
+    return out
+
+
+@dataclasses.dataclass
+class OracleModelAB:
+    Nb: int
+    Na: int
+    w_b: np.ndarray
+    w_a: np.ndarray
+    edges_b: np.ndarray
+    labels_b: np.ndarray
+    edges_a: np.ndarray
+    labels_a: np.ndarray
+    margin: float
+    K: np.ndarray          # [Na, Nb, F, T]
+    B: np.ndarray
+
+    @property
+    def N(self) -> int:    # components (rows of the flattened K)
+        return self.Na * self.Nb
+
+
+def build_model_ab(sky, obs, Nb, scheme, weighting, Na, field_a, scheme_a, weighting_a):
+    """The oracle's fg21_build_regions_ab: spectral-index regions partition
+    beta, amplitude regions partition the per-pixel `field_a`, each with its
+    own scheme and importance weighting; then K over the intersections."""
+    w_b = weights(sky, obs, weighting)
+    edges_b, labels_b, m_b = partition(sky.beta, w_b, Nb, scheme)
+    w_a = w_b if weighting_a == weighting else weights(sky, obs, weighting_a)
+    edges_a, labels_a, m_a = partition(field_a, w_a, Na, scheme_a)
+    K, B = precompute_ab(sky, obs, labels_a, Na, labels_b, Nb)
+    return OracleModelAB(Nb, Na, w_b, w_a, edges_b, labels_b, edges_a, labels_a, min(m_b, m_a), K, B)
 
 
 @dataclasses.dataclass

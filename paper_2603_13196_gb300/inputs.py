@@ -10,7 +10,10 @@ likelihood.  It only draws the raw inputs the method consumes:
 * the observation (channel frequencies, the beam's chromatic exponent p(nu),
   the zenith direction for each LST bin);
 * parameter vectors theta_p = [beta_1..beta_N, A21, nu21, sigma21, sigma_n]
-  drawn from the prior, or scattered around a chosen point;
+  (with amplitude scale factors alpha_1..alpha_Na after the betas for the
+  joint amplitude / spectral-index model) drawn from the prior, or scattered
+  around a chosen point;
+* the per-pixel field the amplitude regions partition (ln T230);
 * standard-normal noise draws.
 
 The paper's own inputs (the 2008 Global Sky Model at N_side = 512, an
@@ -153,6 +156,26 @@ def prior_draws(P: int, N: int, seed: int, extra: int = 0, prior: dict = PRIOR) 
     lo, hi = prior["sigma_n"]
     out[:, N + 3] = np.exp(g.uniform(math.log(lo), math.log(hi), size=P))
     return out
+
+
+# Amplitude scale factors alpha_i of the joint amplitude / spectral-index model
+# (a gain correction of the template; the paper gives no prior for them).
+PRIOR_ALPHA = (0.9, 1.1)
+
+
+def amplitude_field(sky: Sky) -> np.ndarray:
+    """The per-pixel value the amplitude regions partition: ln T230 (regions of
+    similar template brightness share one scale factor)."""
+    return np.log(sky.t230)
+
+
+def prior_draws_ab(P: int, Nb: int, Na: int, seed: int, extra: int = 0, prior: dict = PRIOR,
+                   alpha: tuple = PRIOR_ALPHA) -> np.ndarray:
+    """[P, Nb+Na+4] rows [beta_1..beta_Nb, alpha_1..alpha_Na, A21, nu21, sigma21,
+    sigma_n]; alpha uniform in `alpha`, the rest as prior_draws."""
+    base = prior_draws(P, Nb, seed, extra, prior)
+    a = rng(seed, SUB_PARAMS, 500 + extra).uniform(*alpha, size=(P, Na))
+    return np.concatenate([base[:, :Nb], a, base[:, Nb:]], axis=1)
 
 
 def scatter_around(theta: np.ndarray, P: int, dbeta: float, seed: int, extra: int = 0,

@@ -45,6 +45,19 @@ MUTANTS = {
     "noise_unscaled": ("if (noise) v += sigma_noise * noise[ft];", "if (noise) v += noise[ft];"),
     "sky_weight_no_horizon": ("num = c > 0.0 ? orc_tsky(t230[q], beta[q], nu[f], nu0, t_cmb) : 0.0;",
                               "num = orc_tsky(t230[q], beta[q], nu[f], nu0, t_cmb);"),
+    "ab_alpha_dropped": ("fg += th[Nb + i] * K[(((size_t)i * Nb + j) * F + f) * T + t] * pow(nu[f] / nu0, -th[j]);",
+                         "fg += K[(((size_t)i * Nb + j) * F + f) * T + t] * pow(nu[f] / nu0, -th[j]);"),
+    "ab_alpha_beta_swapped": ("fg += th[Nb + i] * K[(((size_t)i * Nb + j) * F + f) * T + t] * pow(nu[f] / nu0, -th[j]);",
+                              "fg += th[Nb + j % Na] * K[(((size_t)i * Nb + j) * F + f) * T + t] * pow(nu[f] / nu0, -th[i % Nb]);"),
+    "ab_K_transposed": ("fg += th[Nb + i] * K[(((size_t)i * Nb + j) * F + f) * T + t] * pow(nu[f] / nu0, -th[j]);",
+                        "fg += th[Nb + i] * K[(((size_t)j * Na + i) * F + f) * T + t] * pow(nu[f] / nu0, -th[j]);"),
+    "ab_alpha_mask_ignored": ("double ma = lab_a[q] == i ? 1.0 : 0.0;", "double ma = 1.0;"),
+    "ab_pixel_alpha_label": ("double tm = th[Nb + lab_a[q]] * (t230[q] - t_cmb) * pow(nu[f] / nu0, -th[lab_b[q]]) + t_cmb;",
+                             "double tm = th[Nb + lab_b[q] % Na] * (t230[q] - t_cmb) * pow(nu[f] / nu0, -th[lab_b[q]]) + t_cmb;"),
+    "ab_sigma_index": ("double sig = th[NP + 3];\n        double sum = 0.0;\n        for (int f = 0; f < F; ++f) {\n            double s21 = orc_t21(nu[f], th[NP], th[NP + 1], th[NP + 2]);\n            for (int t = 0; t < T; ++t) {\n                double m = orc_fg_ab",
+                       "double sig = th[NP + 2];\n        double sum = 0.0;\n        for (int f = 0; f < F; ++f) {\n            double s21 = orc_t21(nu[f], th[NP], th[NP + 1], th[NP + 2]);\n            for (int t = 0; t < T; ++t) {\n                double m = orc_fg_ab"),
+    "ab_trough_params": ("M[((size_t)p * F + f) * T + t] =\n                    orc_fg_ab(Na, Nb, F, T, K, nu, nu0, th, f, t) + t_cmb * B[(size_t)f * T + t] + s21;",
+                         "M[((size_t)p * F + f) * T + t] =\n                    orc_fg_ab(Na, Nb, F, T, K, nu, nu0, th, f, t) + t_cmb * B[(size_t)f * T + t];"),
 }
 
 PINS = [
@@ -66,6 +79,12 @@ PINS = [
     lambda: pins.test_hierarchical_base_regions_have_equal_mass(4),
     pins.test_recursive_edges_are_dyadic_midpoints,
     lambda: pins.test_embedding_identity("recursive"),
+    lambda: pins.test_ab_fast_model_equals_pixel_model("recursive", "hierarchical", 4, 3),
+    pins.test_ab_unit_amplitudes_reduce_to_beta_model,
+    pins.test_ab_scaled_template_reproduces_simulated_data,
+    pins.test_ab_flat_beam_closed_form,
+    pins.test_ab_noiseless_identity_and_gaussian_logpdf,
+    lambda: pins.test_ab_amplitude_embedding_identity("hierarchical"),
 ]
 
 

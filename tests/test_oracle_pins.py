@@ -369,3 +369,141 @@ def test_partition_margin_reported():
     wl = I.workload(1)
     m = O.build_model(wl.sky(), wl.obs(), wl.N, wl.scheme)
     assert 1e-9 < m.margin <= 1.0
+
+
+# ------------------------------------------------------------ amplitude masks
+# The joint model of eqs. forward_model / chromatic_function /
+# fast_forward_model with N_alpha amplitude regions (partitioning a per-pixel
+# field, here ln T230 or a direction coordinate) besides the N_beta
+# spectral-index regions.
+
+def _ab_model(sky, obs, Nb, Na, scheme="recursive", scheme_a="hierarchical", field=None):
+    field = I.amplitude_field(sky) if field is None else field
+    return O.build_model_ab(sky, obs, Nb, scheme, "beam", Na, field, scheme_a, "beam")
+
+
+@pytest.mark.parametrize("scheme,scheme_a,Nb,Na", [("recursive", "hierarchical", 4, 3),
+                                                  ("hierarchical", "recursive", 3, 5),
+                                                  ("linear", "percentile", 2, 2)])
+def test_ab_fast_model_equals_pixel_model(scheme, scheme_a, Nb, Na):
+    """eq. fast_forward_model over K (both masks) equals eq. forward_model
+    integrated per pixel, for arbitrary alpha and beta."""
+    sky, obs = small_case(npix=1024, F=7, T=3)
+    m = _ab_model(sky, obs, Nb, Na, scheme, scheme_a)
+    th = I.prior_draws_ab(4, Nb, Na, seed=7)
+    th[1, Nb:Nb + Na] = [3.0 if i == 1 else 0.0 for i in range(Na)]     # one amplitude region alone
+    np.testing.assert_allclose(O.fast_model_ab(m.K, m.B, obs, th),
+                               O.pixel_model_ab(sky, obs, m.labels_a, Na, m.labels_b, Nb, th), rtol=1e-11)
+
+
+def test_ab_unit_amplitudes_reduce_to_beta_model():
+    """The amplitude masks partition the template, so sum_i K_ij = A_j of the
+    spectral-index model with the same beta regions, and alpha = 1 gives its
+    forward model and likelihood."""
+    sky, obs = small_case(npix=1536, F=9, T=2)
+    m = _ab_model(sky, obs, 5, 3)
+    mb = O.build_model(sky, obs, 5, "recursive")
+    np.testing.assert_array_equal(m.labels_b, mb.labels)
+    np.testing.assert_allclose(m.K.sum(axis=0), mb.A, rtol=1e-12, atol=1e-12 * np.abs(mb.A).max())
+    thb = I.prior_draws(3, 5, seed=2)
+    thab = np.concatenate([thb[:, :5], np.ones((3, 3)), thb[:, 5:]], axis=1)
+    np.testing.assert_allclose(O.fast_model_ab(m.K, m.B, obs, thab), O.fast_model(mb.A, mb.B, obs, thb),
+                               rtol=1e-12)
+    data = O.simulate_data(sky, obs, np.array(I.FIDUCIAL_T21), 0.025, I.noise_draws(obs.F, obs.T, 4))
+    np.testing.assert_allclose(O.loglike_ab(m.K, m.B, data, obs, thab), O.loglike(mb.A, mb.B, data, obs, thb),
+                               rtol=1e-12)
+
+
+def test_ab_scaled_template_reproduces_simulated_data():
+    """A constant-beta sky whose template is scaled by a_i on amplitude region i
+    (T230' - T_CMB = a_i (T230 - T_CMB)) is exactly the joint model at
+    alpha = a, beta_j = beta0: eq. simantenna on the scaled sky (noise-free)
+    equals eq. fast_forward_model over the unscaled K."""
+    beta0 = 2.58
+    sky, obs = small_case(npix=2048, F=9, T=3, beta_const=beta0)
+    Na, Nb = 4, 2
+    m = _ab_model(sky, obs, Nb, Na, scheme="percentile", scheme_a="recursive", field=sky.dirs[:, 0].copy())
+    a = np.array([0.8, 1.25, 1.0, 0.5])
+    scaled = I.Sky(dirs=sky.dirs, t230=I.T_CMB + a[m.labels_a] * (sky.t230 - I.T_CMB), beta=sky.beta)
+    t21p = np.array(I.FIDUCIAL_T21)
+    data = O.simulate_data(scaled, obs, t21p)
+    th = np.concatenate([[beta0] * Nb, a, t21p, [0.025]])[None, :]
+    np.testing.assert_allclose(O.fast_model_ab(m.K, m.B, obs, th)[0], data, rtol=1e-12)
+
+
+def test_ab_flat_beam_closed_form():
+    """Flat beam (p = 0), constant template T0, T = 1: K[i,j] = (T0 - T_CMB)
+    2 n_ij / Npix with n_ij the visible pixels of both regions, so the
+    foreground is (T0 - T_CMB)(2/Npix) sum_ij alpha_i n_ij (nu/nu0)^-beta_j."""
+    T0 = 600.0
+    sky, obs = small_case(npix=1024, F=5, T=1, achromatic_p=0.0, t230_const=T0)
+    Na, Nb = 3, 2
+    m = _ab_model(sky, obs, Nb, Na, scheme="percentile", scheme_a="linear", field=sky.dirs[:, 1].copy())
+    up = sky.dirs @ obs.zenith[0] > 0
+    th = np.array([[2.5, 2.9, 0.7, 1.1, 1.4, 0.0, 100.0, 10.0, 0.01]])
+    fg = np.zeros(obs.F)
+    for i in range(Na):
+        for j in range(Nb):
+            n_ij = int(np.sum(up & (m.labels_a == i) & (m.labels_b == j)))
+            fg += th[0, Nb + i] * (T0 - I.T_CMB) * 2.0 * n_ij / sky.npix * (obs.nu / I.NU0_MHZ) ** (-th[0, j])
+    M = O.fast_model_ab(m.K, m.B, obs, th)[0, :, 0]
+    np.testing.assert_allclose(M - I.T_CMB * m.B[:, 0], fg, rtol=1e-12)
+
+
+def test_ab_noiseless_identity_and_gaussian_logpdf():
+    """Data = the joint model at theta*: lnL(theta*) = -1/2 F T ln(2 pi sigma^2);
+    elsewhere lnL is scipy's sum of normal log-densities about the model."""
+    sky, obs = small_case(npix=1024, F=11, T=3)
+    Nb, Na = 3, 2
+    m = _ab_model(sky, obs, Nb, Na)
+    th = np.concatenate([O.region_truth(sky, m.labels_b, Nb), [1.02, 0.97], [0.155, 85.0, 15.0, 0.025]])[None, :]
+    data = O.fast_model_ab(m.K, m.B, obs, th)[0]
+    L = O.loglike_ab(m.K, m.B, data, obs, th)[0]
+    expect = -0.5 * obs.F * obs.T * math.log(2 * math.pi * 0.025 ** 2)
+    assert abs(L - expect) <= 1e-12 * abs(expect)
+    ths = I.prior_draws_ab(4, Nb, Na, seed=8)
+    ths[:, :Nb] = th[0, :Nb] + 1e-4
+    Ls = O.loglike_ab(m.K, m.B, data, obs, ths)
+    Ms = O.fast_model_ab(m.K, m.B, obs, ths)
+    for p in range(4):
+        ref = scipy.stats.norm.logpdf(data, loc=Ms[p], scale=ths[p, -1]).sum()
+        assert abs(Ls[p] - ref) <= 1e-10 * abs(ref)
+    np.testing.assert_allclose(O.chi2_ab(m.K, m.B, data, obs, ths), ((data[None] - Ms) ** 2).sum(axis=(1, 2)),
+                               rtol=1e-12)
+
+
+@pytest.mark.parametrize("scheme_a", ["recursive", "hierarchical"])
+def test_ab_amplitude_embedding_identity(scheme_a):
+    """Nested amplitude regions: giving both children of the split amplitude
+    region the parent's alpha reproduces T_model and lnL at N_alpha + 1."""
+    sky, obs = small_case(npix=2048, F=7, T=2)
+    data = O.simulate_data(sky, obs, np.array(I.FIDUCIAL_T21), 0.025, I.noise_draws(obs.F, obs.T, 5))
+    Nb = 3
+    for Na in (2, 3, 5):
+        m = _ab_model(sky, obs, Nb, Na, scheme_a=scheme_a)
+        m1 = _ab_model(sky, obs, Nb, Na + 1, scheme_a=scheme_a)
+        th = I.prior_draws_ab(5, Nb, Na, seed=Na)
+        parent_of = np.array([int(np.sum(m.edges_a[1:-1] < m1.edges_a[i + 1])) for i in range(Na + 1)])
+        th1 = np.concatenate([th[:, :Nb], th[:, Nb + parent_of], th[:, Nb + Na:]], axis=1)
+        np.testing.assert_allclose(O.fast_model_ab(m1.K, m1.B, obs, th1), O.fast_model_ab(m.K, m.B, obs, th),
+                                   rtol=1e-12)
+        np.testing.assert_allclose(O.loglike_ab(m1.K, m1.B, data, obs, th1),
+                                   O.loglike_ab(m.K, m.B, data, obs, th), rtol=1e-12)
+
+
+def test_ab_amplitude_partition_nested_on_log_template():
+    """The partition Algorithms applied to the amplitude field stay nested."""
+    sky, obs = small_case(npix=3072, F=5, T=2)
+    w = O.weights(sky, obs, "beam")
+    field = I.amplitude_field(sky)
+    for scheme in ("recursive", "hierarchical"):
+        prev = None
+        for N in range(1, 10):
+            edges, labels, _ = O.partition(field, w, N, scheme)
+            if prev is not None:
+                assert set(prev[0].tolist()) <= set(edges.tolist())
+                for j in range(N):
+                    sel = labels == j
+                    if sel.any():
+                        assert len(np.unique(prev[1][sel])) == 1
+            prev = (edges, labels)
