@@ -611,3 +611,101 @@ void orc_chi2_ab(int Na, int Nb, int F, int T, const double *K, const double *B,
         chi2[p] = sum;
     }
 }
+
+/* ------------------------------------------ noise-only likelihood (q_i) */
+
+/* Philox4x32-10 (Salmon, Moraes, Dror and Shaw, SC'11, "Parallel random
+ * numbers: as easy as 1, 2, 3"): ten rounds of two 32x32 -> 64-bit products
+ * with multipliers 0xD2511F53 and 0xCD9E8D57, the Feistel-like mixing
+ *   (c0, c1, c2, c3) -> (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)),
+ * and the key bumped by the Weyl constants (0x9E3779B9, 0xBB67AE85) between
+ * rounds.  The counter-based generator both sides implement from this
+ * definition; the noise realisations of the accuracy criterion are drawn
+ * from it. */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)p0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Standard-normal draws z[cell] of noise realisation k: cells are taken in
+ * pairs (2j, 2j+1); pair j of realisation k uses Philox4x32-10 with counter
+ * (j, k mod 2^32, k / 2^32, 0) and key (seed mod 2^32, seed / 2^32), its
+ * first two outputs as uniforms u = (x + 1) / 2^32 in (0, 1], and the
+ * Box-Muller transform z_2j = sqrt(-2 ln u1) cos(2 pi u2),
+ * z_2j+1 = sqrt(-2 ln u1) sin(2 pi u2) (the second is dropped for an odd last
+ * cell).  z [n_cells]. */
+static void orc_noise_draws_one(int64_t n_cells, int64_t k, uint64_t seed, double *z)
+{
+    const double two_pi = 6.28318530717958647692;
+    for (int64_t j = 0; 2 * j < n_cells; ++j) {
+        uint32_t ctr[4] = {(uint32_t)j, (uint32_t)k, (uint32_t)((uint64_t)k >> 32), 0u};
+        uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+        uint32_t x[4];
+        orc_philox4x32_10(ctr, key, x);
+        double u1 = ((double)x[0] + 1.0) / 4294967296.0;
+        double u2 = ((double)x[1] + 1.0) / 4294967296.0;
+        double r = sqrt(-2.0 * log(u1));
+        z[2 * j] = r * cos(two_pi * u2);
+        if (2 * j + 1 < n_cells) z[2 * j + 1] = r * sin(two_pi * u2);
+    }
+}
+
+/* The draws of realisations 0..K-1: out [K][n_cells]. */
+void orc_noise_draws(int64_t n_cells, int64_t K, uint64_t seed, double *out)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < K; ++k) orc_noise_draws_one(n_cells, k, seed, out + k * n_cells);
+}
+
+/* The likelihood distribution of the accuracy criterion (Sec. 5.2.2: data
+ * described perfectly by the model up to noise realisations): for each
+ * realisation k the residual D - M is the noise itself, sigma_noise z[k], so
+ * eq. likelihood gives
+ *   L_noise[k] = -1/2 sum_cells [ ln(2 pi sigma_n^2) + (sigma_noise z[k,cell])^2 / sigma_n^2 ],
+ * summed over cells in order. */
+void orc_noise_loglike(int64_t n_cells, double sigma_noise, double sigma_n, int64_t K, uint64_t seed,
+                       double *L_noise)
+{
+    const double lnorm = log(2.0 * 3.14159265358979323846 * sigma_n * sigma_n);
+#pragma omp parallel
+    {
+        double *z = (double *)malloc(sizeof(double) * (size_t)n_cells);
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t k = 0; k < K; ++k) {
+            orc_noise_draws_one(n_cells, k, seed, z);
+            double sum = 0.0;
+            for (int64_t c = 0; c < n_cells; ++c) {
+                double res = sigma_noise * z[c];
+                sum += lnorm + res * res / (sigma_n * sigma_n);
+            }
+            L_noise[k] = -0.5 * sum;
+        }
+        free(z);
+    }
+}
+
+/* q = P(L_noise <= L_bar) of Sec. 5.2.2: the fraction of the K realisations
+ * whose likelihood does not exceed L_bar (the lower-tail probability of the
+ * fitted likelihood under the ideal noise distribution), for each of n_bar
+ * values L_bar. */
+void orc_noise_q(const double *L_noise, int64_t K, const double *L_bar, int64_t n_bar, double *q)
+{
+    for (int64_t i = 0; i < n_bar; ++i) {
+        int64_t c = 0;
+        for (int64_t k = 0; k < K; ++k) c += L_noise[k] <= L_bar[i];
+        q[i] = (double)c / (double)K;
+    }
+}

@@ -63,6 +63,15 @@ def lib():
             fn.restype = None
             fn.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _D, _D, _D, _D, C.c_double, C.c_double,
                            _D, C.c_int64, _D]
+        _U32 = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")
+        L.orc_philox4x32_10.restype = None
+        L.orc_philox4x32_10.argtypes = [_U32, _U32, _U32]
+        L.orc_noise_draws.restype = None
+        L.orc_noise_draws.argtypes = [C.c_int64, C.c_int64, C.c_uint64, _D]
+        L.orc_noise_loglike.restype = None
+        L.orc_noise_loglike.argtypes = [C.c_int64, C.c_double, C.c_double, C.c_int64, C.c_uint64, _D]
+        L.orc_noise_q.restype = None
+        L.orc_noise_q.argtypes = [_D, C.c_int64, _D, C.c_int64, _D]
         for name in ("orc_loglike", "orc_chi2"):
             fn = getattr(L, name)
             fn.restype = None
@@ -271,6 +280,41 @@ def build_model_ab(sky, obs, Nb, scheme, weighting, Na, field_a, scheme_a, weigh
     edges_a, labels_a, m_a = partition(field_a, w_a, Na, scheme_a)
     K, B = precompute_ab(sky, obs, labels_a, Na, labels_b, Nb)
     return OracleModelAB(Nb, Na, w_b, w_a, edges_b, labels_b, edges_a, labels_a, min(m_b, m_a), K, B)
+
+
+# ------------------------------------------- noise-only likelihood (q_i)
+# The accuracy criterion of Sec. 5.2.2: the likelihood distribution of data
+# that the model describes up to Gaussian noise, and the lower-tail
+# probability q of a fitted likelihood under it.
+
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 (Salmon et al. 2011) of one 128-bit counter and 64-bit key."""
+    out = np.empty(4, dtype=np.uint32)
+    lib().orc_philox4x32_10(np.ascontiguousarray(ctr, dtype=np.uint32), np.ascontiguousarray(key, dtype=np.uint32),
+                            out)
+    return out
+
+
+def noise_draws(n_cells, K, seed):
+    """Standard-normal draws [K, n_cells] of the noise realisations (Philox + Box-Muller)."""
+    out = np.empty((K, n_cells))
+    lib().orc_noise_draws(n_cells, K, seed, out)
+    return out
+
+
+def noise_loglike(n_cells, sigma_noise, sigma_n, K, seed):
+    """L_noise[k] = -1/2 sum_cells [ln(2 pi sigma_n^2) + (sigma_noise z_k)^2 / sigma_n^2]."""
+    out = np.empty(K)
+    lib().orc_noise_loglike(n_cells, sigma_noise, sigma_n, K, seed, out)
+    return out
+
+
+def noise_q(L_noise, L_bar):
+    """q_i = P(L_noise <= L_bar_i) for each L_bar_i."""
+    L_bar = np.atleast_1d(np.asarray(L_bar, dtype=np.float64))
+    q = np.empty(L_bar.shape[0])
+    lib().orc_noise_q(_c(L_noise), len(L_noise), _c(L_bar), L_bar.shape[0], q)
+    return q
 
 
 @dataclasses.dataclass

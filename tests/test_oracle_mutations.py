@@ -58,6 +58,14 @@ MUTANTS = {
                        "double sig = th[NP + 2];\n        double sum = 0.0;\n        for (int f = 0; f < F; ++f) {\n            double s21 = orc_t21(nu[f], th[NP], th[NP + 1], th[NP + 2]);\n            for (int t = 0; t < T; ++t) {\n                double m = orc_fg_ab"),
     "ab_trough_params": ("M[((size_t)p * F + f) * T + t] =\n                    orc_fg_ab(Na, Nb, F, T, K, nu, nu0, th, f, t) + t_cmb * B[(size_t)f * T + t] + s21;",
                          "M[((size_t)p * F + f) * T + t] =\n                    orc_fg_ab(Na, Nb, F, T, K, nu, nu0, th, f, t) + t_cmb * B[(size_t)f * T + t];"),
+    "noise_sigma_not_squared": ("sum += lnorm + res * res / (sigma_n * sigma_n);", "sum += lnorm + res * res / sigma_n;"),
+    "boxmuller_radius": ("double r = sqrt(-2.0 * log(u1));", "double r = sqrt(-log(u1));"),
+    "boxmuller_same_angle": ("if (2 * j + 1 < n_cells) z[2 * j + 1] = r * sin(two_pi * u2);",
+                             "if (2 * j + 1 < n_cells) z[2 * j + 1] = r * cos(two_pi * u2);"),
+    "philox_key_dropped": ("uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;", "uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1;"),
+    "philox_two_rounds": ("for (int r = 0; r < 10; ++r) {", "for (int r = 0; r < 2; ++r) {"),
+    "philox_low_half": ("uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;", "uint32_t n2 = (uint32_t)p0 ^ c3 ^ k1;"),
+    "noise_q_strict": ("c += L_noise[k] <= L_bar[i];", "c += L_noise[k] < L_bar[i];"),
 }
 
 PINS = [
@@ -85,6 +93,11 @@ PINS = [
     pins.test_ab_flat_beam_closed_form,
     pins.test_ab_noiseless_identity_and_gaussian_logpdf,
     lambda: pins.test_ab_amplitude_embedding_identity("hierarchical"),
+    pins.test_noise_loglike_is_a_scaled_chi_square,
+    pins.test_noise_draws_are_standard_normal_and_independent,
+    pins.test_philox_mixing,
+    lambda: pins.test_philox_matches_library_engine(__import__("pathlib").Path(__import__("tempfile").mkdtemp())),
+    pins.test_noise_q_special_values,
 ]
 
 

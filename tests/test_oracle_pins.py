@@ -507,3 +507,113 @@ def test_ab_amplitude_partition_nested_on_log_template():
                     if sel.any():
                         assert len(np.unique(prev[1][sel])) == 1
             prev = (edges, labels)
+
+
+# ------------------------------------------------- noise-only likelihood (q_i)
+# Sec. 5.2.2: L_noise is the likelihood of data the model describes up to
+# Gaussian noise; -2 L_noise - n ln(2 pi sigma_n^2) = (sigma_noise / sigma_n)^2
+# chi^2_n exactly, whatever the model.
+
+def test_noise_loglike_is_a_scaled_chi_square():
+    """KS test of the oracle's L_noise against the chi-square law (n cells, odd
+    and even counts, sigma_noise != sigma_n)."""
+    for n, s_noise, s_n in ((51, 0.025, 0.025), (200, 0.025, 0.03), (1, 0.02, 0.01)):
+        L = O.noise_loglike(n, s_noise, s_n, 3000, seed=12345 + n)
+        x = (-2.0 * L - n * math.log(2 * math.pi * s_n ** 2)) * (s_n / s_noise) ** 2
+        p = scipy.stats.kstest(x, scipy.stats.chi2(df=n).cdf).pvalue
+        assert p > 1e-3, (n, p)
+
+
+def test_noise_draws_are_standard_normal_and_independent():
+    """Both members of each Box-Muller pair are N(0, 1) (KS), uncorrelated with
+    each other and across realisations and cells."""
+    z = O.noise_draws(64, 400, seed=7)
+    for part in (z[:, 0::2].ravel(), z[:, 1::2].ravel()):
+        assert scipy.stats.kstest(part, "norm").pvalue > 1e-3
+    assert abs(np.corrcoef(z[:, 0::2].ravel(), z[:, 1::2].ravel())[0, 1]) < 0.02
+    assert abs(np.corrcoef(z[:-1].ravel(), z[1:].ravel())[0, 1]) < 0.02
+    assert abs(np.corrcoef(z[:, :-1].ravel(), z[:, 1:].ravel())[0, 1]) < 0.02
+    # different seeds give different streams; the same seed the same stream
+    assert not np.array_equal(O.noise_draws(8, 2, seed=1), O.noise_draws(8, 2, seed=2))
+    np.testing.assert_array_equal(O.noise_draws(8, 2, seed=3), O.noise_draws(8, 2, seed=3))
+
+
+_PHILOX_SHIM = r"""
+#include <ATen/core/PhiloxRNGEngine.h>
+#include <cstdint>
+extern "C" void ref_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out) {
+    const uint64_t seed = (uint64_t)key[0] | ((uint64_t)key[1] << 32);
+    const uint64_t offset = (uint64_t)ctr[0] | ((uint64_t)ctr[1] << 32);
+    const uint64_t subseq = (uint64_t)ctr[2] | ((uint64_t)ctr[3] << 32);
+    at::Philox4_32 e(seed, subseq, offset);
+    for (int i = 0; i < 4; ++i) out[i] = e();
+}
+"""
+
+
+def test_philox_matches_library_engine(tmp_path):
+    """The oracle's Philox4x32-10 equals PyTorch's independent header-only
+    engine (at::Philox4_32: key = seed, counter = (offset, subsequence)) word
+    for word, on random and extreme counters and keys."""
+    import ctypes
+    import subprocess
+    torch_ext = pytest.importorskip("torch.utils.cpp_extension")
+    src = tmp_path / "ref.cpp"
+    so = tmp_path / "libref.so"
+    src.write_text(_PHILOX_SHIM)
+    inc = [f"-I{p}" for p in torch_ext.include_paths()]
+    subprocess.check_call(["g++", "-O1", "-std=c++17", "-shared", "-fPIC", *inc, str(src), "-o", str(so)])
+    ref = ctypes.CDLL(str(so))
+    U = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")
+    ref.ref_philox.argtypes = [U, U, U]
+    ref.ref_philox.restype = None
+    g = np.random.default_rng(17)
+    cases = [(np.zeros(4), np.zeros(2)), (np.full(4, 2 ** 32 - 1), np.full(2, 2 ** 32 - 1))]
+    cases += [(g.integers(0, 2 ** 32, 4, dtype=np.uint64), g.integers(0, 2 ** 32, 2, dtype=np.uint64))
+              for _ in range(300)]
+    for ctr, key in cases:
+        ctr = np.asarray(ctr, dtype=np.uint64).astype(np.uint32)
+        key = np.asarray(key, dtype=np.uint64).astype(np.uint32)
+        want = np.empty(4, dtype=np.uint32)
+        ref.ref_philox(ctr, key, want)
+        np.testing.assert_array_equal(O.philox4x32_10(ctr, key), want)
+
+
+def test_philox_mixing():
+    """Philox4x32-10 avalanche: flipping any single bit of the counter or key
+    flips about half of the 128 output bits (a dropped key injection, a
+    missing round or a wrong product half would not), and the outputs of
+    consecutive counters are uniform (KS on their 32-bit words)."""
+    g = np.random.default_rng(3)
+    flips = []
+    for trial in range(60):
+        ctr = g.integers(0, 2 ** 32, 4, dtype=np.uint64).astype(np.uint32)
+        key = g.integers(0, 2 ** 32, 2, dtype=np.uint64).astype(np.uint32)
+        base = O.philox4x32_10(ctr, key)
+        for word, bit in ((trial % 4, trial % 32), (None, trial % 32)):
+            c2, k2 = ctr.copy(), key.copy()
+            if word is None:
+                k2[trial % 2] ^= np.uint32(1 << bit)
+            else:
+                c2[word] ^= np.uint32(1 << bit)
+            out = O.philox4x32_10(c2, k2)
+            flips.append(sum(bin(int(a) ^ int(b)).count("1") for a, b in zip(base, out)))
+    flips = np.array(flips)
+    assert abs(flips.mean() - 64) < 3 and flips.min() > 30
+    words = np.concatenate([O.philox4x32_10(np.array([j, 0, 0, 0]), np.array([9, 0])) for j in range(2000)])
+    assert scipy.stats.kstest(words / 2.0 ** 32, "uniform").pvalue > 1e-3
+
+
+def test_noise_q_special_values():
+    """q is a lower-tail fraction: 0 below every realisation, 1 above all, and
+    at the analytic p-quantile of the scaled chi-square law it is p within
+    binomial error."""
+    n, s = 101, 0.025
+    L = O.noise_loglike(n, s, s, 4000, seed=99)
+    assert O.noise_q(L, [L.min() - 1.0])[0] == 0.0 and O.noise_q(L, [L.max()])[0] == 1.0
+    for p in (0.01, 0.1, 0.5):
+        # L <= L_bar  <=>  chi2 >= c:  P = 1 - F(c) = p
+        c = scipy.stats.chi2(df=n).ppf(1.0 - p)
+        L_bar = -0.5 * (n * math.log(2 * math.pi * s * s) + c)
+        q = O.noise_q(L, [L_bar])[0]
+        assert abs(q - p) < 4 * math.sqrt(p * (1 - p) / 4000) + 1e-3, (p, q)
