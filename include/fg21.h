@@ -12,6 +12,11 @@
  *    likelihood and the table of priors):
  *        theta_p = [beta_1 .. beta_N, A21 (K), nu21 (MHz), sigma21 (MHz), sigma_n (K)]
  *    with regions in ascending spectral-index order, so params is P x (N+4).
+ *    Models with amplitude regions (fg21_build_regions_ab, Sec. 2.2 eqs.
+ *    forward_model / fast_forward_model with N_alpha > 1) insert the scale
+ *    factors after the spectral indices:
+ *        theta_p = [beta_1 .. beta_Nb, alpha_1 .. alpha_Na, A21, nu21, sigma21, sigma_n]
+ *    (P x (Nb+Na+4); fg21_model_shape gives the row length of any model).
  *  - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
  *    stream.
  *  - The library owns the device memory of a model; handles are not
@@ -101,13 +106,28 @@ typedef struct {
     int32_t weighting;       /* FG21_WEIGHT_* */
 } fg21_partition_opts;
 
+/* Amplitude regions of the joint model (Sec. 2.2: masks M_alpha,i with one
+ * scale factor alpha_i each, besides the spectral-index masks M_beta,j).  The
+ * paper leaves their construction open, noting that the partition Algorithms
+ * apply to them unchanged; here they partition a per-pixel `field` chosen by
+ * the caller (e.g. ln T230, so that regions of similar template brightness
+ * share one gain) with the same schemes, conventions and importance
+ * weightings as the spectral-index regions (field values in place of beta). */
+typedef struct {
+    int32_t n_regions;       /* N_alpha >= 1 */
+    int32_t scheme;          /* FG21_SCHEME_* */
+    int32_t weighting;       /* FG21_WEIGHT_* */
+    const double *field;     /* [npix] finite values to partition */
+} fg21_amplitude_opts;
+
 /* --------------------------------------------------------------- errors */
 /* Message of the calling thread's last failure ("" if none).  The pointer stays
  * valid until the thread's next fg21 call. */
 const char *fg21_last_error(void);
 
 /* Number of points the calling thread's last likelihood call marked invalid
- * (non-finite parameter, sigma_n <= 0 or sigma21 == 0; their logL is -inf). */
+ * (non-finite parameter, sigma_n <= 0, sigma21 == 0 or an amplitude scale
+ * factor alpha_i <= 0; their logL is -inf). */
 int64_t fg21_last_invalid_count(void);
 
 /* Library version string. */
@@ -143,6 +163,37 @@ int fg21_build_regions(const fg21_sky *sky, const fg21_obs *obs, const fg21_part
  * machines without a GPU and for checking the host logic. */
 int fg21_build_regions_host(const fg21_sky *sky, const fg21_obs *obs, const fg21_partition_opts *opt,
                             int32_t *labels_out, double *edges_out, double *A_out, double *B_out);
+
+/* The joint amplitude / spectral-index model (Sec. 2.2, eqs. forward_model,
+ * chromatic_function, fast_forward_model):
+ *   K[i,j,f,t] = (1/Npix) sum_pix M_alpha,i M_beta,j (T230 - T_CMB) D(pix,f,t)
+ *   M[p,f,t]   = sum_i sum_j alpha_{p,i} K[i,j,f,t] (nu_f/nu0)^-beta_{p,j} + T_CMB B[f,t] + T21
+ * Spectral-index regions as fg21_build_regions with beta_opt; amplitude
+ * regions partition alpha_opt->field with alpha_opt's scheme and weighting.
+ * The model's components are the Na x Nb intersections, component c = i Nb + j
+ * (its A row is K[i,j]; fg21_model_get_arrays returns K flattened that way and
+ * fg21_model_info reports N = Na Nb); its parameter rows are
+ * [beta_1..beta_Nb, alpha_1..alpha_Na, A21, nu21, sigma21, sigma_n].  Every
+ * likelihood call accepts it (tensor-core precisions need Na Nb <=
+ * FG21_MAX_REGIONS_TC).  A point with an alpha_i <= 0 is invalid (logL =
+ * -inf, counted): the scale factors are gains.  Optional outputs:
+ * beta_labels [npix], beta_edges [Nb+1], alpha_labels [npix], alpha_edges
+ * [Na+1].  Errors: as fg21_build_regions, plus FG21_E_ARG for a NULL or
+ * non-finite field, Na < 1, Na > npix or Na Nb > FG21_MAX_REGIONS. */
+int fg21_build_regions_ab(const fg21_sky *sky, const fg21_obs *obs, const fg21_partition_opts *beta_opt,
+                          const fg21_amplitude_opts *alpha_opt, fg21_model **out, int32_t *beta_labels,
+                          double *beta_edges, int32_t *alpha_labels, double *alpha_edges);
+
+/* The host half of fg21_build_regions_ab (no device work): labels, edges,
+ * K_out [Na][Nb][F][T] and B_out [F][T] to caller buffers (each may be NULL). */
+int fg21_build_regions_ab_host(const fg21_sky *sky, const fg21_obs *obs, const fg21_partition_opts *beta_opt,
+                               const fg21_amplitude_opts *alpha_opt, int32_t *beta_labels, double *beta_edges,
+                               int32_t *alpha_labels, double *alpha_edges, double *K_out, double *B_out);
+
+/* Parameter layout of a model: spectral-index regions, amplitude parameters
+ * (0 for models of fg21_build_regions) and values per parameter row
+ * (n_beta + n_alpha + 4).  Any output may be NULL. */
+int fg21_model_shape(const fg21_model *m, int32_t *n_beta, int32_t *n_alpha, int32_t *n_params);
 
 /* Release a model and its device memory (NULL is allowed). */
 int fg21_model_destroy(fg21_model *m);
@@ -291,6 +342,31 @@ int fg21_graph_create_multi(fg21_model *const *models, const double *const *d_pa
 int fg21_graph_launch(fg21_graph *g, void *stream);
 int fg21_graph_sync_status(fg21_graph *g, void *stream, int64_t *invalid_count);
 int fg21_graph_destroy(fg21_graph *g);
+
+/* ------------------------------------------------- accuracy criterion (q_i) */
+/* The likelihood distribution of the accuracy criterion (Sec. 5.2.2): K
+ * realisations of data that the model describes perfectly up to uncorrelated
+ * Gaussian noise of amplitude sigma_noise, evaluated with eq. likelihood at
+ * noise level sigma_n over n_cells = F*T cells.  The residual D - M of
+ * realisation k is the noise itself, so
+ *   L_noise[k] = -1/2 sum_cells [ ln(2 pi sigma_n^2) + (sigma_noise z[k,cell])^2 / sigma_n^2 ]
+ * with standard-normal z from Philox4x32-10 (Salmon et al. 2011): cell pair
+ * (2j, 2j+1) of realisation k uses counter (j, k mod 2^32, k / 2^32, 0), key
+ * (seed mod 2^32, seed / 2^32), uniforms u = (x + 1) / 2^32 of the first two
+ * output words and the Box-Muller transform (z_2j = sqrt(-2 ln u1) cos 2 pi u2,
+ * z_2j+1 = sqrt(-2 ln u1) sin 2 pi u2).  d_L_noise [K] is DEVICE memory,
+ * written asynchronously on `stream`; results are reproducible bit for bit.
+ * Errors: FG21_E_ARG (n_cells < 1, K < 0, sigma_n <= 0, sigma_noise < 0),
+ * FG21_E_RANGE (K >= 2^31 or n_cells >= 2^33), FG21_E_CUDA. */
+int fg21_noise_loglike(int64_t n_cells, double sigma_noise, double sigma_n, int64_t K, uint64_t seed,
+                       double *d_L_noise, void *stream);
+
+/* q_i = P(L_noise <= L_bar_i), the lower-tail probability of each fitted
+ * likelihood L_bar_i (HOST [n_bar]) under the K values of d_L_noise (DEVICE):
+ * the fraction counted on the device, written to q (HOST [n_bar]); the call
+ * waits for `stream`.  A fit is consistent with noise when q_i >= 0.01 (the
+ * paper's threshold). */
+int fg21_noise_q(const double *d_L_noise, int64_t K, const double *L_bar, int64_t n_bar, double *q, void *stream);
 
 /* ---------------------------------------------------------------- serving */
 /* Continuous-batching likelihood server for many concurrent nested-sampling

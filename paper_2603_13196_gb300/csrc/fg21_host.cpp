@@ -128,9 +128,10 @@ void importance(const fg21_sky *s, const fg21_obs *o, const Geometry &g, int wei
     }
 }
 
-// Weighted CDF over beta (eq. weighted_cdf): pixels sorted by (beta, index),
-// cum[k] = running importance.  C^-1(c) is the beta of the first sorted pixel
-// with cum >= c.
+// Weighted CDF over a per-pixel field (eq. weighted_cdf; the field is beta
+// for the spectral-index regions, the caller's field for amplitude regions):
+// pixels sorted by (value, index), cum[k] = running importance.  C^-1(c) is
+// the value of the first sorted pixel with cum >= c.
 struct Cdf {
     std::vector<int64_t> order;
     std::vector<double> sorted_beta, cum;
@@ -151,11 +152,9 @@ struct Cdf {
     std::vector<double> wsorted;
 };
 
-void make_cdf(const fg21_sky *s, const std::vector<double> &w, Cdf &c) {
-    const int64_t n = s->npix;
+void make_cdf(int64_t n, const double *beta, const std::vector<double> &w, Cdf &c) {
     c.order.resize(n);
     for (int64_t k = 0; k < n; ++k) c.order[k] = k;
-    const double *beta = s->beta;
     std::sort(c.order.begin(), c.order.end(), [beta](int64_t i, int64_t j) {
         return beta[i] < beta[j] || (beta[i] == beta[j] && i < j);
     });
@@ -328,40 +327,111 @@ int fg21_device_count(void) {
 namespace fg21 {
 namespace {
 struct Built {
-    std::vector<double> edges, A, B;
-    std::vector<int32_t> lab;
-    int n_empty = 0;
+    std::vector<double> edges, edges_a, A, B;
+    std::vector<int32_t> lab, lab_a;
+    int Nb = 0, Na = 0;          // Na = 0: no amplitude regions
+    int n_empty = 0;             // components without a pixel
 };
 
-int build_host(const fg21_sky *sky, const fg21_obs *obs, const fg21_partition_opts *opt, Built &out) {
+int check_opts(const fg21_sky *sky, int N, int scheme, int weighting, const char *what) {
+    if (N < 1 || N > FG21_MAX_REGIONS || (int64_t)N > sky->npix)
+        return set_error(FG21_E_ARG, "%s n_regions=%d must be in [1, min(npix, %d)]", what, N, FG21_MAX_REGIONS);
+    if (scheme < 0 || scheme > 3) return set_error(FG21_E_ARG, "%s: unknown scheme %d", what, scheme);
+    if (weighting < 0 || weighting > 3) return set_error(FG21_E_ARG, "%s: unknown weighting %d", what, weighting);
+    return FG21_OK;
+}
+
+// Split `field` into N regions by the CDF of the importance w and label the
+// pixels: region j holds values in (edges[j], edges[j+1]] (the lowest closed
+// below), found by comparing each value with the edges.
+void partition_field(int64_t npix, const double *field, const std::vector<double> &w, int N, int scheme,
+                     std::vector<double> &edges, std::vector<int32_t> &lab) {
+    Cdf c;
+    make_cdf(npix, field, w, c);
+    split(c, N, scheme, edges);
+    lab.resize(npix);
+    for (int64_t q = 0; q < npix; ++q)
+        lab[q] = (int32_t)(std::lower_bound(edges.begin() + 1, edges.begin() + N, field[q]) - (edges.begin() + 1));
+}
+
+// Spectral-index regions (opt), optionally amplitude regions (aopt), and the
+// response functions of their intersections: component i * Nb + j.
+int build_host(const fg21_sky *sky, const fg21_obs *obs, const fg21_partition_opts *opt,
+               const fg21_amplitude_opts *aopt, Built &out) {
     if (!opt) return set_error(FG21_E_ARG, "NULL opt");
     int rc = check_inputs(sky, obs);
     if (rc) return rc;
-    const int N = opt->n_regions;
-    if (N < 1 || N > FG21_MAX_REGIONS || (int64_t)N > sky->npix)
-        return set_error(FG21_E_ARG, "n_regions=%d must be in [1, min(npix, %d)]", N, FG21_MAX_REGIONS);
-    if (opt->scheme < 0 || opt->scheme > 3) return set_error(FG21_E_ARG, "unknown scheme %d", opt->scheme);
-    if (opt->weighting < 0 || opt->weighting > 3) return set_error(FG21_E_ARG, "unknown weighting %d", opt->weighting);
+    const int Nb = opt->n_regions;
+    rc = check_opts(sky, Nb, opt->scheme, opt->weighting, "spectral-index");
+    if (rc) return rc;
+    int Na = 0;
+    if (aopt) {
+        Na = aopt->n_regions;
+        rc = check_opts(sky, Na, aopt->scheme, aopt->weighting, "amplitude");
+        if (rc) return rc;
+        if (!aopt->field) return set_error(FG21_E_ARG, "NULL amplitude field");
+        for (int64_t q = 0; q < sky->npix; ++q)
+            if (!std::isfinite(aopt->field[q]))
+                return set_error(FG21_E_ARG, "non-finite amplitude field at pixel %lld", (long long)q);
+        if ((int64_t)Na * Nb > FG21_MAX_REGIONS)
+            return set_error(FG21_E_ARG, "Na * Nb = %d components above %d", Na * Nb, FG21_MAX_REGIONS);
+    }
+    const int N = std::max(Na, 1) * Nb;
     try {
         Geometry g;
         build_geometry(sky, obs, g);
         std::vector<double> w;
         importance(sky, obs, g, opt->weighting, w);
-        Cdf c;
-        make_cdf(sky, w, c);
-        split(c, N, opt->scheme, out.edges);
-        out.lab.resize(sky->npix);
-        for (int64_t q = 0; q < sky->npix; ++q)
-            out.lab[q] = (int32_t)(std::lower_bound(out.edges.begin() + 1, out.edges.begin() + N, sky->beta[q]) -
-                                   (out.edges.begin() + 1));
-        precompute(sky, obs, g, out.lab, N, out.A, out.B);
+        partition_field(sky->npix, sky->beta, w, Nb, opt->scheme, out.edges, out.lab);
+        std::vector<int32_t> comp = out.lab;
+        if (Na) {
+            std::vector<double> wa;
+            if (aopt->weighting != opt->weighting) importance(sky, obs, g, aopt->weighting, wa);
+            partition_field(sky->npix, aopt->field, aopt->weighting != opt->weighting ? wa : w, Na, aopt->scheme,
+                            out.edges_a, out.lab_a);
+            for (int64_t q = 0; q < sky->npix; ++q) comp[q] = out.lab_a[q] * Nb + out.lab[q];
+        }
+        precompute(sky, obs, g, comp, N, out.A, out.B);
         std::vector<int64_t> count(N, 0);
-        for (int64_t q = 0; q < sky->npix; ++q) count[out.lab[q]]++;
+        for (int64_t q = 0; q < sky->npix; ++q) count[comp[q]]++;
         out.n_empty = 0;
         for (int i = 0; i < N; ++i) out.n_empty += count[i] == 0;
+        out.Nb = Nb;
+        out.Na = Na;
     } catch (const std::bad_alloc &) {
         return set_error(FG21_E_NOMEM, "host allocation failed while building regions");
     }
+    return FG21_OK;
+}
+
+// The device model of a built partition.
+int make_model(const fg21_sky *sky, const fg21_obs *obs, Built &b, fg21_model **out) {
+    fg21_model *m = nullptr;
+    try {
+        m = new fg21_model();
+    } catch (const std::bad_alloc &) {
+        return set_error(FG21_E_NOMEM, "host allocation failed");
+    }
+    m->n_beta = b.Nb;
+    m->n_alpha = b.Na;
+    m->N = std::max(b.Na, 1) * b.Nb;
+    m->F = obs->F;
+    m->T = obs->T;
+    m->npix = sky->npix;
+    m->n_empty = b.n_empty;
+    m->nu0 = obs->nu0;
+    m->t_cmb = obs->t_cmb;
+    m->nu.assign(obs->nu, obs->nu + obs->F);
+    m->edges = b.edges;
+    m->edges_alpha = b.edges_a;
+    m->A = std::move(b.A);
+    m->B = std::move(b.B);
+    int rc = model_upload(m);
+    if (rc) {
+        fg21_model_destroy(m);
+        return rc;
+    }
+    *out = m;
     return FG21_OK;
 }
 }  // namespace
@@ -373,7 +443,7 @@ int fg21_build_regions_host(const fg21_sky *sky, const fg21_obs *obs, const fg21
                             int32_t *labels_out, double *edges_out, double *A_out, double *B_out) {
     clear_error();
     Built b;
-    int rc = build_host(sky, obs, opt, b);
+    int rc = build_host(sky, obs, opt, nullptr, b);
     if (rc) return rc;
     if (labels_out) std::memcpy(labels_out, b.lab.data(), sizeof(int32_t) * b.lab.size());
     if (edges_out) std::memcpy(edges_out, b.edges.data(), sizeof(double) * b.edges.size());
@@ -388,34 +458,45 @@ int fg21_build_regions(const fg21_sky *sky, const fg21_obs *obs, const fg21_part
     if (!out) return set_error(FG21_E_ARG, "NULL out");
     *out = nullptr;
     Built b;
-    int rc = build_host(sky, obs, opt, b);
+    int rc = build_host(sky, obs, opt, nullptr, b);
     if (rc) return rc;
-    fg21_model *m = nullptr;
-    try {
-        m = new fg21_model();
-    } catch (const std::bad_alloc &) {
-        return set_error(FG21_E_NOMEM, "host allocation failed");
-    }
-    m->N = opt->n_regions;
-    m->F = obs->F;
-    m->T = obs->T;
-    m->npix = sky->npix;
-    m->n_empty = b.n_empty;
-    m->nu0 = obs->nu0;
-    m->t_cmb = obs->t_cmb;
-    m->nu.assign(obs->nu, obs->nu + obs->F);
-    m->edges = b.edges;
-    m->A = std::move(b.A);
-    m->B = std::move(b.B);
-    rc = model_upload(m);
-    if (rc) {
-        fg21_model_destroy(m);
-        return rc;
-    }
     if (labels_out) std::memcpy(labels_out, b.lab.data(), sizeof(int32_t) * sky->npix);
-    if (edges_out) std::memcpy(edges_out, b.edges.data(), sizeof(double) * (m->N + 1));
-    *out = m;
+    if (edges_out) std::memcpy(edges_out, b.edges.data(), sizeof(double) * b.edges.size());
+    return make_model(sky, obs, b, out);
+}
+
+int fg21_build_regions_ab_host(const fg21_sky *sky, const fg21_obs *obs, const fg21_partition_opts *beta_opt,
+                               const fg21_amplitude_opts *alpha_opt, int32_t *beta_labels, double *beta_edges,
+                               int32_t *alpha_labels, double *alpha_edges, double *K_out, double *B_out) {
+    clear_error();
+    if (!alpha_opt) return set_error(FG21_E_ARG, "NULL alpha_opt");
+    Built b;
+    int rc = build_host(sky, obs, beta_opt, alpha_opt, b);
+    if (rc) return rc;
+    if (beta_labels) std::memcpy(beta_labels, b.lab.data(), sizeof(int32_t) * b.lab.size());
+    if (beta_edges) std::memcpy(beta_edges, b.edges.data(), sizeof(double) * b.edges.size());
+    if (alpha_labels) std::memcpy(alpha_labels, b.lab_a.data(), sizeof(int32_t) * b.lab_a.size());
+    if (alpha_edges) std::memcpy(alpha_edges, b.edges_a.data(), sizeof(double) * b.edges_a.size());
+    if (K_out) std::memcpy(K_out, b.A.data(), sizeof(double) * b.A.size());
+    if (B_out) std::memcpy(B_out, b.B.data(), sizeof(double) * b.B.size());
     return FG21_OK;
+}
+
+int fg21_build_regions_ab(const fg21_sky *sky, const fg21_obs *obs, const fg21_partition_opts *beta_opt,
+                          const fg21_amplitude_opts *alpha_opt, fg21_model **out, int32_t *beta_labels,
+                          double *beta_edges, int32_t *alpha_labels, double *alpha_edges) {
+    clear_error();
+    if (!out) return set_error(FG21_E_ARG, "NULL out");
+    *out = nullptr;
+    if (!alpha_opt) return set_error(FG21_E_ARG, "NULL alpha_opt");
+    Built b;
+    int rc = build_host(sky, obs, beta_opt, alpha_opt, b);
+    if (rc) return rc;
+    if (beta_labels) std::memcpy(beta_labels, b.lab.data(), sizeof(int32_t) * b.lab.size());
+    if (beta_edges) std::memcpy(beta_edges, b.edges.data(), sizeof(double) * b.edges.size());
+    if (alpha_labels) std::memcpy(alpha_labels, b.lab_a.data(), sizeof(int32_t) * b.lab_a.size());
+    if (alpha_edges) std::memcpy(alpha_edges, b.edges_a.data(), sizeof(double) * b.edges_a.size());
+    return make_model(sky, obs, b, out);
 }
 
 int fg21_simulate_data(const fg21_sky *sky, const fg21_obs *obs, const double *t21, double sigma_noise,

@@ -47,13 +47,18 @@ struct ReqDesc {
     const float *B32;      // [F][T]
     const float *data32;   // [F][T]
     // request I/O (device)
-    const double *params;  // [P][N+4]
+    const double *params;  // [P][NPF+4]
     double *logL;          // [P]
     double t_cmb;
     double Lmax;           // max_f |ln(nu_f / nu0)|
     int64_t P;
-    int N, F, T;
+    int N, F, T;           // N: components (rows of A, weight columns) = max(Na, 1) * Nb
+    int Nb;                // spectral-index regions; component c has beta index c % Nb
+    int Na;                // amplitude parameters (0: none, alpha = 1); component c has alpha index c / Nb
+    int NPF;               // foreground parameters Nb + Na: a parameter row is [beta.., alpha.., A21, nu21,
+                           // sigma21, sigma_n] of NPF + 4 values
     int Kp;                // K = N + 2 padded to a multiple of 16 (tensor path)
+    int pts_rows;          // rows of 128 floats per point tile of pts32
     int Tc, Tc_pad, n_tchunks;   // t-chunks: Tc columns each (last may be shorter), padded to 16
     int G, ch_per_group;         // channel groups per 128-point tile
     int cpg_hint;                // channels per group chosen by the autotuner for this size (0 = model)
@@ -66,9 +71,10 @@ struct ReqDesc {
     int64_t pt_begin;            // first global point index of this request (reduction)
     char *tiles;                 // this request's operand tiles (arena + tile_row0 * 128)
     // workspace (device)
-    float *stat_part;      // [n_stat_blocks][3N + 2]: sum, min, max per region, n_valid, max|A21|
-    double *beta_bar;      // [N]
-    double *req_stats;     // [4]: n_valid, max|dev|*max|L| (x), max|A21|, reserved
+    float *stat_part;      // [n_stat_blocks][3 NPF + 2]: sum, min, max per foreground parameter, n_valid,
+                           // max|A21|
+    double *beta_bar;      // [NPF] reference point: mean of each foreground parameter (beta_bar, alpha_bar)
+    double *req_stats;     // [4]: n_valid, bound x on |expm1 argument|, max|A21|, reserved
     float *nL32;           // [F] -ln(nu_f/nu0)
     float *nu32;           // [F]
     int *scaleB;           // [F * n_tchunks] power-of-two exponent of each operand tile
@@ -76,8 +82,11 @@ struct ReqDesc {
     float *Bp32;           // [N][F][T] wbar_i A (FP32, SIMT delta form)
     float *dref32;         // [F][T]    reference residual (FP32, SIMT delta form)
     float2 *partials;      // [P][n_part] compensated partial chi^2 (hi, lo)
-    float *pts32;          // [n_tiles][Kp + 4][128] per point: beta - bbar (rows < Kp-2, zero
-                           // beyond N), then A21, nu21, 1/(2 sigma21^2) (rows Kp-2..Kp); tensor path
+    float *pts32;          // [n_tiles][pts_rows][128] per point: beta - bbar of each component's
+                           // spectral index (rows < Kp-2, zero beyond N), then A21, nu21,
+                           // 1/(2 sigma21^2) (rows Kp-2..Kp); with amplitude parameters, rows
+                           // Kp+4.. hold ln(alpha / alpha_bar) of each component, pair-interleaved
+                           // ([Kp/2 pairs][128 points][2]); tensor path
     unsigned *status;      // device status word (shared by a launch)
     unsigned long long *invalid;  // invalid-point counter
 };

@@ -27,40 +27,27 @@ namespace {
 constexpr int PREP_THREADS = 256;
 constexpr int REDUCE_THREADS = 64;
 
-// A point is valid when all its parameters are finite, sigma_n > 0 and
-// sigma21 != 0.  Tested on the bit patterns (integer instructions; FP64 is a
-// scarce pipe on this part).
-__device__ __forceinline__ bool point_valid(const double *th, int N) {
+// A point is valid when all its parameters are finite, sigma_n > 0,
+// sigma21 != 0 and every amplitude scale factor alpha_i > 0 (a gain).  Tested
+// on the bit patterns (integer instructions; FP64 is a scarce pipe on this
+// part).
+__device__ __forceinline__ bool point_valid(const double *th, const ReqDesc &r) {
+    const int NP = r.NPF;
     bool ok = true;
-    for (int k = 0; k < N + 4; ++k)
+    for (int k = 0; k < NP + 4; ++k)
         ok &= (__double_as_longlong(th[k]) & 0x7FF0000000000000ll) != 0x7FF0000000000000ll;
-    ok &= __double_as_longlong(th[N + 3]) > 0;                                 // > +0 (sign clear)
-    ok &= (__double_as_longlong(th[N + 2]) & 0x7FFFFFFFFFFFFFFFll) != 0;      // != +-0
+    ok &= __double_as_longlong(th[NP + 3]) > 0;                                // > +0 (sign clear)
+    ok &= (__double_as_longlong(th[NP + 2]) & 0x7FFFFFFFFFFFFFFFll) != 0;     // != +-0
+    for (int k = r.Nb; k < NP; ++k) ok &= __double_as_longlong(th[k]) > 0;    // alpha > +0
     return ok;
 }
 
-// Deterministic block reductions (fixed shuffle tree, then warps in order).
-template <typename Op>
-__device__ double block_reduce(double v, Op op, double *sh) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
-    __syncthreads();
-    if (lane == 0) sh[warp] = v;
-    __syncthreads();
-    double r = sh[0];
-    for (int w = 1; w < nw; ++w) r = op(r, sh[w]);
-    __syncthreads();
-    return r;
-}
-
-struct OpSum { __device__ double operator()(double a, double b) const { return a + b; } };
-struct OpMin { __device__ double operator()(double a, double b) const { return fmin(a, b); } };
-struct OpMax { __device__ double operator()(double a, double b) const { return fmax(a, b); } };
 
 // a1, pass 1: per block of STAT_BLOCK points (one thread each), the sum / min
-// / max of each region's beta over valid points (FP32: the reference point
-// only has to be a deterministic value near the points; the rearranged
-// likelihood is exact for any reference), the valid count and max |A21|.
+// / max of each foreground parameter (each region's beta, then each amplitude
+// alpha) over valid points (FP32: the reference point only has to be a
+// deterministic value near the points; the rearranged likelihood is exact for
+// any reference), the valid count and max |A21|.
 // Warps reduce by shuffles in a fixed tree and are combined in warp order.
 // Largest s with 2^s * maxabs <= 2^15 (half the FP16 range), clamped to
 // [-40, 40]; exact, from the exponent and mantissa bits (no FP64 log).
@@ -96,10 +83,26 @@ __device__ __forceinline__ float2 unpack_pair(uint32_t u) {
     }
 }
 
+// 8-byte asynchronous copy global -> shared (no register staging; the copies
+// of a thread stay in flight until cp_async_wait_all).
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Parameter rows staged in shared memory are padded to an odd number of
+// doubles so that a warp reading one value of 32 consecutive rows spreads over
+// the banks.
+__host__ __device__ __forceinline__ int padded_row(int R) { return R | 1; }
+
 // a1, pass 2, run by every block of the second prep kernel: the reference
-// point bbar_i = mean of the valid points' beta_i, the largest weight argument
-// x = max_i |beta - bbar_i| * max_f |L_f| (which sets the weight series and the
-// power-of-two scale sW of the weight operand), the valid count and max |A21|.
+// point (bbar_i = mean of the valid points' beta_i, and abar_i = mean alpha_i
+// with amplitude regions), a bound x on the weights' expm1 argument,
+// max_i |beta - bbar_i| * max_f |L_f| + max_i |ln(alpha / abar_i)| (it sets the
+// weight series and the power-of-two scale sW of the weight operand), the
+// valid count and max |A21|.
 // Thread j combines field j of every stat block in block order (one round of
 // independent loads per 16 blocks), so every block computes the same values
 // bit for bit; bbar goes to shared memory (`bbar_sh`), and block 0 of the
@@ -108,8 +111,8 @@ struct Fin {
     float nv, ma, x;
     int sW;
 };
-__device__ Fin prep_finalize(const ReqDesc &r, float *sh /* [3N + 2 + nwarps] */, double *bbar_sh, bool publish) {
-    const int N = r.N, nb = r.n_stat_blocks, W = 3 * N + 2;
+__device__ Fin prep_finalize(const ReqDesc &r, float *sh /* [3 NPF + 2 + 2 nwarps] */, double *bbar_sh, bool publish) {
+    const int N = r.NPF, Nb = r.Nb, nb = r.n_stat_blocks, W = 3 * N + 2;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int j = threadIdx.x; j < W; j += blockDim.x) {
         const int kind = j < 3 * N ? j % 3 : (j == 3 * N ? 0 : 2);   // 0 sum, 1 min, 2 max
@@ -128,22 +131,34 @@ __device__ Fin prep_finalize(const ReqDesc &r, float *sh /* [3N + 2 + nwarps] */
     }
     __syncthreads();
     const float nv = sh[3 * N], ma = sh[3 * N + 1];
-    float dev = 0.0f;
+    float dev = 0.0f, gdev = 0.0f;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         const float bb = nv > 0.0f ? sh[3 * i] / nv : 0.0f;
         bbar_sh[i] = (double)bb;
         if (publish) r.beta_bar[i] = (double)bb;
-        if (nv > 0.0f) dev = fmaxf(dev, fmaxf(sh[3 * i + 2] - bb, bb - sh[3 * i + 1]));
+        if (nv > 0.0f) {
+            if (i < Nb) dev = fmaxf(dev, fmaxf(sh[3 * i + 2] - bb, bb - sh[3 * i + 1]));
+            else gdev = fmaxf(gdev, fmaxf(logf(sh[3 * i + 2] / bb), logf(bb / sh[3 * i + 1])));   // alpha > 0
+        }
     }
-    for (int o = 16; o > 0; o >>= 1) dev = fmaxf(dev, __shfl_xor_sync(0xffffffffu, dev, o));
+    for (int o = 16; o > 0; o >>= 1) {
+        dev = fmaxf(dev, __shfl_xor_sync(0xffffffffu, dev, o));
+        gdev = fmaxf(gdev, __shfl_xor_sync(0xffffffffu, gdev, o));
+    }
     float *wred = sh + W;
-    if (lane == 0) wred[warp] = dev;
+    if (lane == 0) {
+        wred[warp] = dev;
+        wred[nw + warp] = gdev;
+    }
     __syncthreads();
-    float dmax = 0.0f;
-    for (int w = 0; w < nw; ++w) dmax = fmaxf(dmax, wred[w]);
+    float dmax = 0.0f, gmax = 0.0f;
+    for (int w = 0; w < nw; ++w) {
+        dmax = fmaxf(dmax, wred[w]);
+        gmax = fmaxf(gmax, wred[nw + w]);
+    }
     Fin f;
     // a small margin on x covers the FP32 statistics
-    f.x = dmax * (float)r.Lmax * 1.0001f;
+    f.x = (dmax * (float)r.Lmax + gmax) * 1.0001f;
     f.nv = nv;
     f.ma = ma;
     f.sW = pow2_exponent_for(fmaxf(fmaxf(expm1f(f.x), ma), 1.0f));
@@ -157,15 +172,34 @@ __device__ Fin prep_finalize(const ReqDesc &r, float *sh /* [3N + 2 + nwarps] */
     return f;
 }
 
-__global__ void __launch_bounds__(STAT_BLOCK) prep_stats_kernel(const ReqDesc *__restrict__ reqs) {
-    extern __shared__ float sh_stats[];        // [STAT_BLOCK / 32][3N + 2]
+__global__ void __launch_bounds__(STAT_BLOCK) prep_stats_kernel(const ReqDesc *__restrict__ reqs, int staged) {
+    // shared: [STAT_BLOCK / 32][3 NPF + 2] FP32 warp partials, then (staged) the
+    // block's parameter rows [STAT_BLOCK][padded_row(NPF + 4)] FP64
+    extern __shared__ double sh_stats_d[];
     const ReqDesc &r = reqs[blockIdx.y];
     if ((int)blockIdx.x >= r.n_stat_blocks) return;
-    const int N = r.N, W = 3 * N + 2, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int N = r.NPF, W = 3 * N + 2, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
-    const int64_t p = (int64_t)blockIdx.x * STAT_BLOCK + threadIdx.x;
-    const double *th = r.params + (p < r.P ? p : 0) * (N + 4);
-    const bool valid = p < r.P && point_valid(th, N);
+    float *sh_stats = reinterpret_cast<float *>(sh_stats_d);
+    const int64_t p0 = (int64_t)blockIdx.x * STAT_BLOCK, p = p0 + threadIdx.x;
+    const int np = (int)min((int64_t)STAT_BLOCK, r.P - p0);
+    const double *th;
+    if (staged) {
+        // coalesced copies of the block's rows, all in flight at once
+        const int R = N + 4, Rp = padded_row(R);
+        double *slab = sh_stats_d + (nw * W + 1) / 2;
+        const double *src = r.params + p0 * R;
+        for (int k = threadIdx.x; k < np * R; k += blockDim.x) {
+            const int row = k / R;
+            cp_async8(slab + (size_t)row * Rp + (k - row * R), src + k);
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        th = slab + (size_t)(p < r.P ? threadIdx.x : 0) * Rp;
+    } else {
+        th = r.params + (p < r.P ? p : 0) * (N + 4);
+    }
+    const bool valid = p < r.P && point_valid(th, r);
     float *mine = sh_stats + warp * W;
     for (int i = 0; i < N; ++i) {
         const float b = valid ? (float)th[i] : 0.0f;
@@ -204,10 +238,13 @@ __global__ void __launch_bounds__(STAT_BLOCK) prep_stats_kernel(const ReqDesc *_
 }
 
 // a1, pass 3: one block per (channel, t-chunk) builds that channel's
-// reference: wbar_i = (nu_f/nu0)^-bbar_i, wbar_i A[i,f,t] and
-// dref = D - sum_i wbar_i A_i - T_CMB B (FP64), then writes either the FP32
+// reference: wbar_c = (nu_f/nu0)^-bbar_j (times abar_i with amplitude regions)
+// for each component c = (i, j), wbar_c A[c,f,t] and
+// dref = D - sum_c wbar_c A_c - T_CMB B (FP64), then writes either the FP32
 // arrays of the SIMT delta form or the split-precision operand tile of the
-// tensor-core form.
+// tensor-core form.  With amplitude regions the weights of a point are
+// expm1(-(beta_j - bbar_j) L_f + ln(alpha_i / abar_i)), the same exact
+// rearrangement with alpha_i (nu/nu0)^-beta_j = abar_i wbar_j exp(that argument).
 //
 // Operand tile layout (one per channel and t-chunk, 2 x Kp x Tc_pad 16-bit
 // values): [split s in {hi, mid}][k-chunk kc = k/8][t][8 values k%8], i.e. the
@@ -218,124 +255,237 @@ __global__ void __launch_bounds__(STAT_BLOCK) prep_stats_kernel(const ReqDesc *_
 //
 // Blocks beyond the tiles (tensor path only) write the per-point operands of
 // the weight generators, one block per 128-point tile, point-minor so that a
-// thread per point reads them coalesced: rows k < Kp-2 hold beta_{p,k} - bbar_k
-// in FP32 (zero for k >= N), then A21, nu21 and 1/(2 sigma21^2).
-template <int MODE>
-__device__ __forceinline__ void prep_points(const ReqDesc &r, int tile, const double *bbar) {
+// thread per point reads them coalesced: rows k < Kp-2 hold beta_{p,j} - bbar_j
+// of component k's spectral index j in FP32 (zero for k >= N), then A21, nu21
+// and 1/(2 sigma21^2); with amplitude regions, rows Kp+4.. hold
+// ln(alpha_{p,i} / abar_i) of each component's amplitude i, two components per
+// 8-byte pair ([Kp/2][128][2]) so a generator thread loads a pair at once.
+// `th` is this thread's parameter row (staged in shared memory).
+__device__ __forceinline__ void prep_points(const ReqDesc &r, int tile, const double *bbar, const double *th) {
     const int64_t p = (int64_t)tile * TILE_M + threadIdx.x;
     if (threadIdx.x >= TILE_M) return;
-    const int N = r.N, R = r.Kp + 4;
-    float *out = r.pts32 + (size_t)tile * R * TILE_M + threadIdx.x;
+    const int N = r.N, Nb = r.Nb, NP = r.NPF, Kp = r.Kp;
+    float *out = r.pts32 + (size_t)tile * r.pts_rows * TILE_M + threadIdx.x;
     const bool in = p < r.P;
-    const double *th = r.params + (in ? p : 0) * (N + 4);
-    for (int k = 0; k < r.Kp - 2; ++k)
-        out[(size_t)k * TILE_M] = (in && k < N) ? (float)(th[k] - bbar[k]) : 0.0f;
-    out[(size_t)(r.Kp - 2) * TILE_M] = in ? (float)th[N] : 0.0f;
-    out[(size_t)(r.Kp - 1) * TILE_M] = in ? (float)th[N + 1] : 0.0f;
-    const float s21 = in ? (float)th[N + 2] : 1.0f;
-    out[(size_t)r.Kp * TILE_M] = 1.0f / (2.0f * s21 * s21);
+    for (int k = 0; k < Kp - 2; ++k)
+        out[(size_t)k * TILE_M] = (in && k < N) ? (float)(th[k % Nb] - bbar[k % Nb]) : 0.0f;
+    out[(size_t)(Kp - 2) * TILE_M] = in ? (float)th[NP] : 0.0f;
+    out[(size_t)(Kp - 1) * TILE_M] = in ? (float)th[NP + 1] : 0.0f;
+    const float s21 = in ? (float)th[NP + 2] : 1.0f;
+    out[(size_t)Kp * TILE_M] = 1.0f / (2.0f * s21 * s21);
+    if (r.Na) {
+        float2 *g2 = reinterpret_cast<float2 *>(out - threadIdx.x + (size_t)(Kp + 4) * TILE_M) + threadIdx.x;
+        int icur = -1;
+        float gcur = 0.0f;
+        for (int q = 0; q < Kp / 2; ++q) {
+            float gv[2];
+            for (int e = 0; e < 2; ++e) {
+                const int c = 2 * q + e;
+                float v = 0.0f;
+                if (in && c < N) {
+                    const int ia = c / Nb;
+                    if (ia != icur) {
+                        icur = ia;
+                        const double ab = bbar[Nb + ia];
+                        gcur = log1pf((float)(th[Nb + ia] - ab) / (float)ab);   // ln(alpha / abar)
+                    }
+                    v = gcur;
+                }
+                gv[e] = v;
+            }
+            g2[(size_t)q * TILE_M] = make_float2(gv[0], gv[1]);
+        }
+    }
 }
 
-template <int MODE>  // 0 = tensor FP16, 1 = tensor BF16, 2 = SIMT delta, 3 = SIMT direct
+// a1 for the SIMT forms, pass 3: one block per (channel, t-chunk) builds that
+// channel's reference -- wbar_c (FP64), dref[t] = D - sum_c wbar_c A_c - T_CMB B
+// summed in ascending c (FP64: the foreground cancels here) -- and writes the
+// FP32 arrays of the delta form (wbar_c A_c and dref); the direct form only
+// needs the per-channel tables.
+template <int MODE>  // 2 = SIMT delta, 3 = SIMT direct
 __global__ void __launch_bounds__(PREP_THREADS) prep_tiles_kernel(const ReqDesc *__restrict__ reqs) {
     extern __shared__ double smem_d[];
-    __shared__ double sh[32];
-    __shared__ int s_scaleB;
     const ReqDesc &r = reqs[blockIdx.y];
     const int nfc = r.F * r.n_tchunks;
-    const int N = r.N, T = r.T;
-    if ((int)blockIdx.x >= nfc + (MODE <= 1 ? r.n_tiles : 0)) return;
-    // shared memory: bbar [N] FP64, finalise scratch [3N + 2 + 8] FP32 (rounded to
-    // doubles), wbar [N] FP64, dref [Tc_pad] FP64, wbar32 [N] FP32
+    const int N = r.N, NP = r.NPF, Nb = r.Nb, T = r.T;
+    if ((int)blockIdx.x >= nfc) return;
+    // shared memory: bbar [NPF] FP64, finalise scratch [3 NPF + 2 + 16] FP32 (rounded
+    // to doubles), wbar [N] FP64
     double *bbar = smem_d;
-    float *fin_sh = reinterpret_cast<float *>(bbar + N);
-    double *wbar = bbar + N + (3 * N + 2 + 8 + 1) / 2;
-    double *dref = wbar + N;
-    float *wbar32 = reinterpret_cast<float *>(dref + r.Tc_pad);
+    float *fin_sh = reinterpret_cast<float *>(bbar + NP);
+    double *wbar = bbar + NP + (3 * NP + 2 + 16 + 1) / 2;
     prep_finalize(r, fin_sh, bbar, blockIdx.x == 0);
-    if (MODE <= 1 && (int)blockIdx.x >= nfc) {
-        prep_points<MODE>(r, blockIdx.x - nfc, bbar);
-        return;
-    }
     const int fc = blockIdx.x;
     const int f = fc / r.n_tchunks, c = fc % r.n_tchunks;
     const int t0 = c * r.Tc, tn = min(r.Tc, T - t0);
     const double L = r.L[f];
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        wbar[i] = exp(-bbar[i] * L);
-        wbar32[i] = (float)wbar[i];
+        double w = exp(-bbar[i % Nb] * L);
+        if (r.Na) w *= bbar[Nb + i / Nb];
+        wbar[i] = w;
     }
     if (c == 0 && threadIdx.x == 0) {
         r.nL32[f] = (float)(-L);
         r.nu32[f] = (float)r.nu[f];
     }
     __syncthreads();
-    // --- reference residual dref[t] = D - sum_i wbar_i A_i - T_CMB B (FP64: the
-    // foreground cancels here) ---
-    float vmax = 1.0f;
+    if (MODE != 2) return;
     const size_t istride = (size_t)r.F * T;
     for (int t = threadIdx.x; t < tn; t += blockDim.x) {
         const size_t ft = (size_t)f * T + t0 + t;
         double s = 0.0;
         for (int i0 = 0; i0 < N; i0 += 8) {
             double a[8];
-            float a32[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                a[j] = i0 + j < N ? r.A[(size_t)(i0 + j) * istride + ft] : 0.0;
-                a32[j] = i0 + j < N ? r.A32[(size_t)(i0 + j) * istride + ft] : 0.0f;
-            }
+            for (int j = 0; j < 8; ++j) a[j] = i0 + j < N ? r.A[(size_t)(i0 + j) * istride + ft] : 0.0;
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 if (i0 + j < N) {
                     const double bw = wbar[i0 + j] * a[j];
                     s += bw;
-                    // the scale only needs the magnitude: FP32 product (FP64 is a scarce pipe)
-                    vmax = fmaxf(vmax, fabsf(wbar32[i0 + j] * a32[j]));
-                    if (MODE == 2) r.Bp32[(size_t)(i0 + j) * istride + ft] = (float)bw;
+                    r.Bp32[(size_t)(i0 + j) * istride + ft] = (float)bw;
                 }
             }
         }
-        const double d = r.data[ft] - s - r.t_cmb * r.B[ft];
+        r.dref32[ft] = (float)(r.data[ft] - s - r.t_cmb * r.B[ft]);
+    }
+}
+
+// a1 on the tensor path, pass 3 (one launch): blocks [0, F * n_tchunks) build
+// the operand tile of one (channel, t-chunk), the blocks after them the
+// per-point operands of one 128-point tile.  Each block first issues
+// asynchronous copies of everything it reads (the channel's A slab, D and B;
+// or the tile's parameter rows) into shared memory and finalises the request
+// statistics while they land, so the DRAM latency of its inputs hides behind
+// the statistics.  Then, for a channel block: wbar_c (FP64), the products
+// wbar_c A[c,f,t] in place (FP64), dref[t] = D - sum_c wbar_c A_c - T_CMB B
+// summed in ascending c (FP64: the foreground cancels here), the tile scale
+// 2^sB, and the split-precision tile from the products rounded once to FP32.
+//
+// Operand tile layout (one per channel and t-chunk, 2 x Kp x Tc_pad 16-bit
+// values): [split s in {hi, mid}][k-chunk kc = k/8][t][8 values k%8], i.e. the
+// K-major core-matrix layout (8 rows of 16 bytes) the tensor cores read; row k
+// < N holds wbar_k A[k,f,t] 2^sB, row Kp-2 holds 2^sB (multiplies the trough
+// column of the weights), row Kp-1 holds dref 2^sB (multiplies -1), other rows
+// and columns t >= Tc are zero.
+//
+// Shared memory: bbar [NPF], finalise scratch, then the block's slab --
+// channel: wbar A [N][Tc_pad] FP64, D, B, dref [Tc_pad] FP64, wbar [N] FP64,
+// (wbar A) in FP32 [N][Tc_pad]; points: parameter rows [128][padded_row(NPF+4)].
+template <bool BF16>
+__global__ void __launch_bounds__(PREP_THREADS) prep_tc_kernel(const ReqDesc *__restrict__ reqs) {
+    extern __shared__ double smem_d[];
+    __shared__ float sh_red[PREP_THREADS / 32];
+    __shared__ int s_scaleB;
+    const ReqDesc &r = reqs[blockIdx.y];
+    const int nfc = r.F * r.n_tchunks;
+    if ((int)blockIdx.x >= nfc + r.n_tiles) return;
+    const int N = r.N, NP = r.NPF, Nb = r.Nb, T = r.T;
+    double *bbar = smem_d;
+    float *fin_sh = reinterpret_cast<float *>(bbar + NP);
+    double *slab = bbar + NP + (3 * NP + 2 + 16 + 1) / 2;
+    if ((int)blockIdx.x >= nfc) {
+        // ---- per-point operands of one 128-point tile
+        const int tile = blockIdx.x - nfc;
+        const int64_t p0 = (int64_t)tile * TILE_M;
+        const int np = (int)min((int64_t)TILE_M, r.P - p0);
+        const int R = NP + 4, Rp = padded_row(R);
+        const double *src = r.params + p0 * R;
+        for (int k = threadIdx.x; k < np * R; k += blockDim.x) {
+            const int row = k / R;
+            cp_async8(slab + (size_t)row * Rp + (k - row * R), src + k);
+        }
+        prep_finalize(r, fin_sh, bbar, false);
+        cp_async_wait_all();
+        __syncthreads();
+        prep_points(r, tile, bbar, slab + (size_t)((int)threadIdx.x < np ? threadIdx.x : 0) * Rp);
+        return;
+    }
+    // ---- operand tile of one (channel, t-chunk)
+    const int fc = blockIdx.x;
+    const int f = fc / r.n_tchunks, c = fc % r.n_tchunks;
+    const int t0 = c * r.Tc, tn = min(r.Tc, T - t0), Tcp = r.Tc_pad;
+    double *bw = slab;                         // [N][Tcp]
+    double *dd = bw + (size_t)N * Tcp;         // [Tcp] D
+    double *bb = dd + Tcp;                     // [Tcp] B
+    double *dref = bb + Tcp;                   // [Tcp]
+    double *wbar = dref + Tcp;                 // [N]
+    float *bwf = reinterpret_cast<float *>(wbar + N);   // [N][Tcp]
+    const size_t istride = (size_t)r.F * T, ft0 = (size_t)f * T + t0;
+    for (int k = threadIdx.x; k < N * tn; k += blockDim.x) {
+        const int i = k / tn, t = k - i * tn;
+        cp_async8(bw + (size_t)i * Tcp + t, r.A + i * istride + ft0 + t);
+    }
+    for (int t = threadIdx.x; t < tn; t += blockDim.x) {
+        cp_async8(dd + t, r.data + ft0 + t);
+        cp_async8(bb + t, r.B + ft0 + t);
+    }
+    prep_finalize(r, fin_sh, bbar, fc == 0);
+    const double L = r.L[f];
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        double w = exp(-bbar[i % Nb] * L);
+        if (r.Na) w *= bbar[Nb + i / Nb];
+        wbar[i] = w;
+    }
+    if (c == 0 && threadIdx.x == 0) {
+        r.nL32[f] = (float)(-L);
+        r.nu32[f] = (float)r.nu[f];
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    float vmax = 1.0f;
+    for (int k = threadIdx.x; k < N * tn; k += blockDim.x) {
+        const int i = k / tn, t = k - i * tn;
+        const double v = wbar[i] * bw[(size_t)i * Tcp + t];
+        bw[(size_t)i * Tcp + t] = v;
+        const float v32 = (float)v;
+        bwf[(size_t)i * Tcp + t] = v32;
+        vmax = fmaxf(vmax, fabsf(v32));
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < tn; t += blockDim.x) {
+        double sum = 0.0;
+        for (int i = 0; i < N; ++i) sum += bw[(size_t)i * Tcp + t];
+        const double d = dd[t] - sum - r.t_cmb * bb[t];
         dref[t] = d;
         vmax = fmaxf(vmax, fabsf((float)d));
-        if (MODE == 2) r.dref32[ft] = (float)d;
     }
-    if (MODE >= 2) return;
     for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = vmax;
+    if ((threadIdx.x & 31) == 0) sh_red[threadIdx.x >> 5] = vmax;
     __syncthreads();
     if (threadIdx.x == 0) {
-        float v = sh[0];
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = fmaxf(v, (float)sh[w]);
+        float v = sh_red[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = fmaxf(v, sh_red[w]);
         s_scaleB = pow2_exponent_for(v);
         r.scaleB[fc] = s_scaleB;
     }
     __syncthreads();
     const float sB = ldexpf(1.0f, s_scaleB);
-    // --- operand tile: one 16-byte chunk (8 values of k) per (split, kc, t).
-    // Region rows in FP32 (wbar_k A[k,f,t] to 24 bits, finer than the 22-bit
-    // split), the dref row from its FP64 value. ---
-    const int Kp = r.Kp, Tcp = r.Tc_pad, nkc = Kp / 8;
+    // one 16-byte chunk (8 values of k) per (split, kc, t); sB is a power of
+    // two, so (float)(wbar A) * sB is the FP64 product rounded once
+    const int Kp = r.Kp, nkc = Kp / 8;
     uint4 *tile = reinterpret_cast<uint4 *>(r.tiles + (size_t)fc * r.tile_rows * 128);
     for (int j = threadIdx.x; j < nkc * Tcp; j += blockDim.x) {
         const int kc = j / Tcp, t = j % Tcp;
         float v[8];
+#pragma unroll
         for (int e = 0; e < 8; ++e) {
             const int k = kc * 8 + e;
             float x = 0.0f;
             if (t < tn) {
-                if (k < N) x = wbar32[k] * r.A32[(size_t)k * r.F * T + (size_t)f * T + t0 + t] * sB;
+                if (k < N) x = bwf[(size_t)k * Tcp + t] * sB;
                 else if (k == Kp - 2) x = sB;
                 else if (k == Kp - 1) x = (float)(dref[t] * (double)sB);
             }
             v[e] = x;
         }
         uint32_t H[4], M[4];
+#pragma unroll
         for (int e = 0; e < 8; e += 2) {
-            H[e / 2] = pack_pair<MODE == 1>(v[e], v[e + 1]);
-            const float2 h = unpack_pair<MODE == 1>(H[e / 2]);
-            M[e / 2] = pack_pair<MODE == 1>(v[e] - h.x, v[e + 1] - h.y);
+            H[e / 2] = pack_pair<BF16>(v[e], v[e + 1]);
+            const float2 h = unpack_pair<BF16>(H[e / 2]);
+            M[e / 2] = pack_pair<BF16>(v[e] - h.x, v[e + 1] - h.y);
         }
         tile[(size_t)kc * Tcp + t] = make_uint4(H[0], H[1], H[2], H[3]);                 // split 0 (hi)
         tile[(size_t)(nkc + kc) * Tcp + t] = make_uint4(M[0], M[1], M[2], M[3]);         // split 1 (mid)
@@ -412,16 +562,21 @@ __global__ void __launch_bounds__(SIMT_THREADS) simt_kernel(const ReqDesc *__res
     const ReqDesc &r = reqs[find_req_by_item(reqs, n_reqs, item)];
     const int64_t lid = item - r.item_begin;
     const int tile = (int)(lid / r.G), g = (int)(lid % r.G);
-    const int N = r.N, F = r.F, T = r.T;
+    const int N = r.N, Nb = r.Nb, Na = r.Na, NP = r.NPF, F = r.F, T = r.T;
     const int f0 = g * r.ch_per_group, f1 = min(F, f0 + r.ch_per_group);
     float *wcol_all = smem_f;                          // [N][128]
     float *As = smem_f + N * SIMT_THREADS;             // [N][64]
     float *ds = As + N * SIMT_TCH;                     // [64]
+    float *acol = ds + SIMT_TCH + threadIdx.x;         // [Na][128]: alpha (direct) or ln(alpha/abar)
     const int64_t p = (int64_t)tile * TILE_M + threadIdx.x;
     const bool inb = p < r.P;
-    const double *th = r.params + (inb ? p : 0) * (N + 4);
-    const float a21 = (float)th[N], nu21 = (float)th[N + 1];
-    const float inv2s2 = (float)(1.0 / (2.0 * th[N + 2] * th[N + 2]));
+    const double *th = r.params + (inb ? p : 0) * (NP + 4);
+    const float a21 = (float)th[NP], nu21 = (float)th[NP + 1];
+    const float inv2s2 = (float)(1.0 / (2.0 * th[NP + 2] * th[NP + 2]));
+    for (int i = 0; i < Na; ++i) {
+        const double ab = r.beta_bar[Nb + i];
+        acol[i * SIMT_THREADS] = DIRECT ? (float)th[Nb + i] : log1pf((float)(th[Nb + i] - ab) / (float)ab);
+    }
     float qs = 0.0f, qc = 0.0f;
     float *wcol = wcol_all + threadIdx.x;
     for (int f = f0; f < f1; ++f) {
@@ -430,11 +585,18 @@ __global__ void __launch_bounds__(SIMT_THREADS) simt_kernel(const ReqDesc *__res
         const float s21 = a21 * expf(-dnu * dnu * inv2s2);
         if (DIRECT) {
             const float l2 = (float)(r.L[f] * 1.4426950408889634);   // log2(nu/nu0)
-            for (int i = 0; i < N; ++i) wcol[i * SIMT_THREADS] = exp2f(-(float)th[i] * l2);
+            for (int i = 0; i < N; ++i) {
+                const float w = exp2f(-(float)th[i % Nb] * l2);
+                wcol[i * SIMT_THREADS] = Na ? acol[(i / Nb) * SIMT_THREADS] * w : w;
+            }
         } else {
             const float nL = (float)(-r.L[f]);
-            for (int i = 0; i < N; ++i)
-                wcol[i * SIMT_THREADS] = expm1f((float)(th[i] - r.beta_bar[i]) * nL);
+            for (int i = 0; i < N; ++i) {
+                const int j = i % Nb;
+                float y = (float)(th[j] - r.beta_bar[j]) * nL;
+                if (Na) y += acol[(i / Nb) * SIMT_THREADS];
+                wcol[i * SIMT_THREADS] = expm1f(y);
+            }
         }
         float qf = 0.0f;
         for (int tb = 0; tb < T; tb += SIMT_TCH) {
@@ -486,9 +648,9 @@ __global__ void __launch_bounds__(REDUCE_THREADS) reduce_kernel(const ReqDesc *_
     const ReqDesc &r = reqs[find_req_by_point(reqs, n_reqs, gid)];
     const int64_t p = gid - r.pt_begin;
     if (p < 0 || p >= r.P) return;
-    const int N = r.N;
+    const int N = r.NPF;
     const double *th = r.params + p * (N + 4);
-    if (!point_valid(th, N)) {
+    if (!point_valid(th, r)) {
         r.logL[p] = -INFINITY;
         atomicAdd(r.invalid, 1ull);
         return;
@@ -515,21 +677,32 @@ __global__ void model_eval_simt_kernel(const ReqDesc *__restrict__ req, double *
     if (gid >= total) return;
     const int64_t p = gid / ((int64_t)r.F * r.T);
     const int f = (int)((gid / r.T) % r.F), t = (int)(gid % r.T);
-    const int N = r.N;
-    const double *th = r.params + p * (N + 4);
+    const int N = r.N, Nb = r.Nb, Na = r.Na, NP = r.NPF;
+    const double *th = r.params + p * (NP + 4);
     const size_t ft = (size_t)f * r.T + t;
-    const float nuf = (float)r.nu[f], dnu = nuf - (float)th[N + 1];
-    const float s21 = (float)th[N] * expf(-dnu * dnu * (float)(1.0 / (2.0 * th[N + 2] * th[N + 2])));
+    const float nuf = (float)r.nu[f], dnu = nuf - (float)th[NP + 1];
+    const float s21 = (float)th[NP] * expf(-dnu * dnu * (float)(1.0 / (2.0 * th[NP + 2] * th[NP + 2])));
     if (DIRECT) {
         const float l2 = (float)(r.L[f] * 1.4426950408889634);
         float acc = 0.0f;
-        for (int i = 0; i < N; ++i) acc = fmaf(r.A32[(size_t)i * r.F * r.T + ft], exp2f(-(float)th[i] * l2), acc);
+        for (int i = 0; i < N; ++i) {
+            float w = exp2f(-(float)th[i % Nb] * l2);
+            if (Na) w *= (float)th[Nb + i / Nb];
+            acc = fmaf(r.A32[(size_t)i * r.F * r.T + ft], w, acc);
+        }
         out[gid] = (double)(acc + (float)r.t_cmb * r.B32[ft] + s21);
     } else {
         const float nL = (float)(-r.L[f]);
         float acc = 0.0f;
-        for (int i = 0; i < N; ++i)
-            acc = fmaf(r.Bp32[(size_t)i * r.F * r.T + ft], expm1f((float)(th[i] - r.beta_bar[i]) * nL), acc);
+        for (int i = 0; i < N; ++i) {
+            const int j = i % Nb;
+            float y = (float)(th[j] - r.beta_bar[j]) * nL;
+            if (Na) {
+                const double ab = r.beta_bar[Nb + i / Nb];
+                y += log1pf((float)(th[Nb + i / Nb] - ab) / (float)ab);
+            }
+            acc = fmaf(r.Bp32[(size_t)i * r.F * r.T + ft], expm1f(y), acc);
+        }
         const float rr = (r.dref32[ft] - s21) - acc;
         out[gid] = r.data[ft] - (double)rr;
     }
@@ -547,27 +720,57 @@ __global__ void resid_to_model_kernel(const ReqDesc *__restrict__ req, const flo
 
 }  // namespace
 
+// Raise a kernel's dynamic shared-memory limit to `need` bytes when a launch
+// asks for more than the default 48 KB (or the last limit set); the largest
+// size a block may hold is checked by the runtime at the launch.
+template <typename K>
+cudaError_t opt_in_smem(K kernel, size_t need, size_t &current) {
+    if (need <= current) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+    if (e == cudaSuccess) current = need;
+    return e;
+}
+
 cudaError_t launch_prep(const ReqDesc *h_reqs, const ReqDesc *d_reqs, int n_reqs, int precision,
                         int max_stat_blocks, int max_F_chunks, int max_tiles, cudaStream_t stream) {
-    int maxN0 = 0;
-    for (int k = 0; k < n_reqs; ++k) maxN0 = maxN0 > h_reqs[k].N ? maxN0 : h_reqs[k].N;
+    int maxNP = 0;
+    for (int k = 0; k < n_reqs; ++k) maxNP = maxNP > h_reqs[k].NPF ? maxNP : h_reqs[k].NPF;
     dim3 g1(max_stat_blocks, n_reqs);
-    const size_t sm1 = sizeof(float) * (STAT_BLOCK / 32) * (3 * (size_t)maxN0 + 2);
-    prep_stats_kernel<<<g1, STAT_BLOCK, sm1, stream>>>(d_reqs);
-    cudaError_t e = cudaGetLastError();
+    // warp partials, then the staged parameter rows when they fit comfortably
+    const size_t part = sizeof(double) * (((size_t)(STAT_BLOCK / 32) * (3 * maxNP + 2) + 1) / 2);
+    const size_t slab1 = sizeof(double) * (size_t)STAT_BLOCK * padded_row(maxNP + 4);
+    const int staged = slab1 <= 96 * 1024;
+    const size_t sm1 = part + (staged ? slab1 : 0);
+    static size_t stats_opt_in = 48 * 1024;
+    cudaError_t e = opt_in_smem(prep_stats_kernel, sm1, stats_opt_in);
     if (e != cudaSuccess) return e;
-    int maxN = 0, maxTcp = 0;
-    for (int k = 0; k < n_reqs; ++k) {
-        maxN = maxN > h_reqs[k].N ? maxN : h_reqs[k].N;
-        maxTcp = maxTcp > h_reqs[k].Tc_pad ? maxTcp : h_reqs[k].Tc_pad;
-    }
-    const size_t sm = sizeof(double) * (2 * (size_t)maxN + (3 * (size_t)maxN + 2 + 8 + 1) / 2 + maxTcp) +
-                      sizeof(float) * (size_t)maxN;
+    prep_stats_kernel<<<g1, STAT_BLOCK, sm1, stream>>>(d_reqs, staged);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     const bool tc = precision == FG21_PREC_FP16X3 || precision == FG21_PREC_BF16X3;
+    size_t sm = 0;
+    for (int k = 0; k < n_reqs; ++k) {
+        const ReqDesc &r = h_reqs[k];
+        const size_t head = sizeof(double) * ((size_t)r.NPF + (3 * (size_t)r.NPF + 2 + 16 + 1) / 2);
+        size_t need;
+        if (tc) {
+            const size_t chan = sizeof(double) * ((size_t)r.N * r.Tc_pad + 3 * (size_t)r.Tc_pad + r.N) +
+                                sizeof(float) * (size_t)r.N * r.Tc_pad;
+            const size_t pts = sizeof(double) * (size_t)TILE_M * padded_row(r.NPF + 4);
+            need = head + (chan > pts ? chan : pts);
+        } else {
+            need = head + sizeof(double) * (size_t)r.N;
+        }
+        sm = sm > need ? sm : need;
+    }
     dim3 g2(max_F_chunks + (tc ? max_tiles : 0), n_reqs);
+    static size_t tc_opt_in[2] = {48 * 1024, 48 * 1024};
+    if (precision == FG21_PREC_FP16X3) e = opt_in_smem(prep_tc_kernel<false>, sm, tc_opt_in[0]);
+    if (precision == FG21_PREC_BF16X3) e = opt_in_smem(prep_tc_kernel<true>, sm, tc_opt_in[1]);
+    if (e != cudaSuccess) return e;
     switch (precision) {
-        case FG21_PREC_FP16X3: prep_tiles_kernel<0><<<g2, PREP_THREADS, sm, stream>>>(d_reqs); break;
-        case FG21_PREC_BF16X3: prep_tiles_kernel<1><<<g2, PREP_THREADS, sm, stream>>>(d_reqs); break;
+        case FG21_PREC_FP16X3: prep_tc_kernel<false><<<g2, PREP_THREADS, sm, stream>>>(d_reqs); break;
+        case FG21_PREC_BF16X3: prep_tc_kernel<true><<<g2, PREP_THREADS, sm, stream>>>(d_reqs); break;
         case FG21_PREC_FP32_DELTA: prep_tiles_kernel<2><<<g2, PREP_THREADS, sm, stream>>>(d_reqs); break;
         default: prep_tiles_kernel<3><<<g2, PREP_THREADS, sm, stream>>>(d_reqs); break;
     }
@@ -577,13 +780,14 @@ cudaError_t launch_prep(const ReqDesc *h_reqs, const ReqDesc *d_reqs, int n_reqs
 cudaError_t launch_simt(const ReqDesc *h_reqs, const ReqDesc *d_reqs, int n_reqs, int precision,
                         cudaStream_t stream) {
     int64_t items = 0;
-    int maxN = 0;
+    int maxN = 0, maxNa = 0;
     for (int k = 0; k < n_reqs; ++k) {
         items += (int64_t)h_reqs[k].n_tiles * h_reqs[k].G;
         maxN = maxN > h_reqs[k].N ? maxN : h_reqs[k].N;
+        maxNa = maxNa > h_reqs[k].Na ? maxNa : h_reqs[k].Na;
     }
     if (items == 0) return cudaSuccess;
-    const size_t sm = sizeof(float) * ((size_t)maxN * (SIMT_THREADS + SIMT_TCH) + SIMT_TCH);
+    const size_t sm = sizeof(float) * ((size_t)maxN * (SIMT_THREADS + SIMT_TCH) + SIMT_TCH + (size_t)maxNa * SIMT_THREADS);
     static bool attr_done[2] = {false, false};
     const bool direct = precision == FG21_PREC_FP32_DIRECT;
     if (!attr_done[direct]) {

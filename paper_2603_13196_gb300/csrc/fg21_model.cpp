@@ -161,6 +161,7 @@ static int choose_channels_per_group(int64_t total_tiles, int F, int num_sms) {
 
 void plan_request(ReqDesc &r, int precision, int num_sms, int64_t total_tiles) {
     r.Kp = round16(r.N + 2);
+    r.pts_rows = r.Kp + 4 + (r.Na ? r.Kp : 0);
     // t-chunks of at most TC_MAX columns: the same cap for every K keeps the
     // plan of a request independent of what it is batched with
     r.n_tchunks = (r.T + TC_MAX - 1) / TC_MAX;
@@ -179,8 +180,8 @@ void plan_request(ReqDesc &r, int precision, int num_sms, int64_t total_tiles) {
 ReqLayout request_layout(const ReqDesc &r, int precision) {
     ReqLayout L{};
     const bool tc = precision == FG21_PREC_FP16X3 || precision == FG21_PREC_BF16X3;
-    L.stat_part = align256(sizeof(float) * (size_t)r.n_stat_blocks * (3 * r.N + 2));
-    L.beta_bar = align256(sizeof(double) * r.N);
+    L.stat_part = align256(sizeof(float) * (size_t)r.n_stat_blocks * (3 * r.NPF + 2));
+    L.beta_bar = align256(sizeof(double) * r.NPF);
     L.req_stats = align256(sizeof(double) * 4);
     L.nL32 = align256(sizeof(float) * r.F);
     L.nu32 = align256(sizeof(float) * r.F);
@@ -190,7 +191,7 @@ ReqLayout request_layout(const ReqDesc &r, int precision) {
     L.Bp32 = delta ? align256(sizeof(float) * (size_t)r.N * r.F * r.T) : 0;
     L.dref32 = delta ? align256(sizeof(float) * (size_t)r.F * r.T) : 0;
     L.partials = align256(sizeof(float2) * (size_t)r.P * r.n_part);
-    L.pts32 = tc ? align256(sizeof(float) * (size_t)r.n_tiles * (r.Kp + 4) * TILE_M) : 0;
+    L.pts32 = tc ? align256(sizeof(float) * (size_t)r.n_tiles * r.pts_rows * TILE_M) : 0;
     L.tiles = tc ? (size_t)r.F * r.n_tchunks * r.tile_rows * 128 : 0;
     return L;
 }
@@ -371,6 +372,9 @@ ReqDesc model_request(fg21_model *m, const double *d_params, int64_t P, double *
     r.Lmax = m->Lmax;
     r.P = P;
     r.N = m->N;
+    r.Nb = m->n_beta;
+    r.Na = m->n_alpha;
+    r.NPF = m->n_beta + m->n_alpha;
     r.F = m->F;
     r.T = m->T;
     return r;
@@ -395,7 +399,7 @@ static int device_guard(const fg21_model *m) {
 // buffers, evaluated on the device, and logL copied back.
 static int run_host(fg21_model *m, const double *params, int64_t P, double *logL, int precision,
                     cudaStream_t stream) {
-    const size_t pbytes = sizeof(double) * (size_t)P * (m->N + 4), lbytes = sizeof(double) * (size_t)P;
+    const size_t pbytes = sizeof(double) * (size_t)P * m->n_params(), lbytes = sizeof(double) * (size_t)P;
     const size_t need = align256(pbytes) + align256(lbytes) + 64;
     if (m->io_cap < need) {
         if (m->ws.done) FG21_CUDA_TRY(cudaEventSynchronize(m->ws.done));
@@ -483,6 +487,14 @@ int fg21_model_info(const fg21_model *m, int32_t *N, int32_t *F, int32_t *T, int
     if (T) *T = m->T;
     if (n_empty) *n_empty = m->n_empty;
     if (device_bytes) *device_bytes = m->resident_bytes;
+    return FG21_OK;
+}
+
+int fg21_model_shape(const fg21_model *m, int32_t *n_beta, int32_t *n_alpha, int32_t *n_params) {
+    if (!m) return set_error(FG21_E_ARG, "NULL model");
+    if (n_beta) *n_beta = m->n_beta;
+    if (n_alpha) *n_alpha = m->n_alpha;
+    if (n_params) *n_params = m->n_params();
     return FG21_OK;
 }
 
@@ -641,7 +653,7 @@ int fg21_model_eval(fg21_model *m, const double *params, int64_t P, double *T_mo
     rc = device_guard(m);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t pbytes = sizeof(double) * (size_t)P * (m->N + 4);
+    const size_t pbytes = sizeof(double) * (size_t)P * m->n_params();
     const size_t obytes = sizeof(double) * (size_t)P * m->F * m->T;
     double *d_params = nullptr, *d_out = nullptr, *d_logL = nullptr;
     if (cudaMalloc((void **)&d_params, pbytes) != cudaSuccess || cudaMalloc((void **)&d_out, obytes) != cudaSuccess ||
@@ -702,7 +714,7 @@ int fg21_loglike_multi(fg21_model *const *models, const double *const *params, c
     size_t total = 0;
     for (int k = 0; k < n_models; ++k) {
         poff[k] = total;
-        total += align256(sizeof(double) * (size_t)P[k] * (models[k]->N + 4));
+        total += align256(sizeof(double) * (size_t)P[k] * models[k]->n_params());
         loff[k] = total;
         total += align256(sizeof(double) * (size_t)P[k]);
     }
@@ -724,7 +736,7 @@ int fg21_loglike_multi(fg21_model *const *models, const double *const *params, c
     std::vector<int> map;
     for (int k = 0; k < n_models; ++k) {
         if (P[k] == 0) continue;
-        const size_t pb = sizeof(double) * (size_t)P[k] * (models[k]->N + 4);
+        const size_t pb = sizeof(double) * (size_t)P[k] * models[k]->n_params();
         std::memcpy(h_io + poff[k], params[k], pb);
         reqs.push_back(model_request(models[k], (const double *)((char *)d_io + poff[k]), P[k],
                                      (double *)((char *)d_io + loff[k]), precision));

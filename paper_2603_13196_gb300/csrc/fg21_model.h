@@ -67,11 +67,14 @@ int num_sms_of(int device);
 }  // namespace fg21
 
 struct fg21_model {
-    int N = 0, F = 0, T = 0;
+    int N = 0, F = 0, T = 0;        // N: components (rows of A) = max(n_alpha, 1) * n_beta
+    int n_beta = 0;                 // spectral-index regions
+    int n_alpha = 0;                // amplitude regions with a free scale factor (0: none, alpha = 1)
+    int n_params() const { return n_beta + n_alpha + 4; }   // values per parameter row
     int64_t npix = 0;
     int n_empty = 0;
     double nu0 = 0, t_cmb = 0, Lmax = 0;
-    std::vector<double> nu, edges, A, B;
+    std::vector<double> nu, edges, edges_alpha, A, B;
     int device = 0;
     double *d_A = nullptr, *d_B = nullptr, *d_data = nullptr, *d_L = nullptr, *d_nu = nullptr;
     float *d_A32 = nullptr, *d_B32 = nullptr, *d_data32 = nullptr;

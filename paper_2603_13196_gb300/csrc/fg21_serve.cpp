@@ -430,7 +430,7 @@ int fg21_serve_submit(fg21_server *s, int32_t run_id, const double *params, int6
     t->id = s->next_ticket++;
     t->run = run_id;
     t->P = P;
-    t->params.assign(params, params + (size_t)P * (it->second.m->N + 4));
+    t->params.assign(params, params + (size_t)P * it->second.m->n_params());
     t->out = logL_out;
     t->t_submit = Clock::now();
     s->tickets[t->id] = t;

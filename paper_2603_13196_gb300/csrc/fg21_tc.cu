@@ -339,10 +339,13 @@ __device__ __forceinline__ SeriesPlan series_plan(double xmax) {
 // (trough, -1) instead (columns Kr-2, Kr-1).  A chunk whose pairs all lie
 // beyond N (pair index >= nz) is stored as zeros without evaluation.  The
 // Horner chains of a chunk of CH pairs advance together.
-template <int NPHMAX, bool BF16, bool FULL>
+// ALPHA (amplitude regions): the series runs on y = d nL + g with g =
+// ln(alpha / abar) of each component (pairs at gp[i * 128]) and the channel's
+// nL in nL2; e2 then holds the constant coefficients 2^(-s j) / j!.
+template <int NPHMAX, bool BF16, bool FULL, bool ALPHA>
 __device__ __forceinline__ void gen_half(uint32_t t_hi, uint32_t t_mid, const uint64_t *d2, const uint64_t *e2,
                                          SeriesPlan sp, uint64_t sW2, int nph_rt, int nz, bool last, float s21,
-                                         float sW) {
+                                         float sW, const float2 *__restrict__ gp, uint64_t nL2) {
     constexpr int CH = 4;
     const int nph = FULL ? NPHMAX : nph_rt;
 #pragma unroll
@@ -350,9 +353,20 @@ __device__ __forceinline__ void gen_half(uint32_t t_hi, uint32_t t_mid, const ui
         if (!FULL && c0 >= nph) break;
         uint64_t w[CH];
         if (c0 < nz) {
-            if (sp.D == 3) em1_series2<3, CH>(w, d2 + c0, e2);
-            else if (sp.D == 5) em1_series2<5, CH>(w, d2 + c0, e2);
-            else em1_series2<8, CH>(w, d2 + c0, e2);
+            const uint64_t *x2 = d2 + c0;
+            uint64_t y2[CH];
+            if (ALPHA) {
+                // nph is a multiple of CH, so every pair of a chunk below nz is below nph
+#pragma unroll
+                for (int i = 0; i < CH; ++i) {
+                    const float2 g = __ldg(gp + (size_t)(c0 + i) * 128);
+                    y2[i] = fma2(d2[c0 + i], nL2, pk2(g.x, g.y));
+                }
+                x2 = y2;
+            }
+            if (sp.D == 3) em1_series2<3, CH>(w, x2, e2);
+            else if (sp.D == 5) em1_series2<5, CH>(w, x2, e2);
+            else em1_series2<8, CH>(w, x2, e2);
             if (sp.s > 0) {
                 const uint64_t two2 = pk2(2.0f, 2.0f);
                 for (int q = 0; q < sp.s; ++q)
@@ -415,12 +429,13 @@ struct GenItem {
     float a21, nu21, inv2s2, sW;
     int Kr, nz;            // nz: pairs of this half from index nz on carry no region
     SeriesPlan sp;
+    const float2 *gp;      // amplitude regions: this thread's ln(alpha/abar) pairs of its half, else null
 };
 template <int NPHMAX>
 __device__ __forceinline__ void gen_item_load(GenItem<NPHMAX> &g, const ReqDesc &r, const Item &it, int half,
                                               int m) {
     const int Kr = r.Kp, nph = Kr / 4;
-    const float *__restrict__ pts = r.pts32 + (size_t)it.tile * (Kr + 4) * 128 + m;
+    const float *__restrict__ pts = r.pts32 + (size_t)it.tile * r.pts_rows * 128 + m;
     // this half's pairs [half*nph, half*nph + nph): regions 2*pair, 2*pair+1 (zero beyond N)
 #pragma unroll
     for (int i = 0; i < NPHMAX; ++i) {
@@ -436,13 +451,15 @@ __device__ __forceinline__ void gen_item_load(GenItem<NPHMAX> &g, const ReqDesc 
     g.sp = series_plan(r.req_stats[1]);
     g.Kr = Kr;
     g.nz = min(nph, max(0, (r.N + 1) / 2 - half * nph));
+    g.gp = r.Na ? reinterpret_cast<const float2 *>(pts - m + (size_t)(Kr + 4) * 128) + (size_t)half * nph * 128 + m
+                : nullptr;
 }
 
 // The weights of every stage of one item by one generator warp (FULL: the
 // request's Kr equals the kernel's KP).  Per stage: wait until the weight slot
 // is free (the MMAs of stage - ring are done), evaluate and store the weights,
 // then one arrival on full[slot].  Returns false on a wait timeout.
-template <int KP, bool BF16, bool FULL>
+template <int KP, bool BF16, bool FULL, bool ALPHA>
 __device__ __forceinline__ bool gen_item(const Params &prm, Barriers *S, Ring &rg, const ReqDesc &r, const Item &it,
                                          const GenItem<KP / 4> &gi, uint32_t w_lane, int half) {
     constexpr int NPHMAX = KP / 4;
@@ -458,10 +475,10 @@ __device__ __forceinline__ bool gen_item(const Params &prm, Barriers *S, Ring &r
         const int fn = min(f + 1, it.f1 - 1);            // next channel's constants, one ahead
         nL_n = __ldg(nLp + fn);
         nu_n = __ldg(nup + fn);
-        // e_j = (nL / 2^s)^j / j!, times 2^sW when s = 0
+        // e_j = (nL / 2^s)^j / j! (ALPHA: 2^(-s j) / j!, the series being in y), times 2^sW when s = 0
         uint64_t e2[9];
         {
-            const float y1 = nL * ys;
+            const float y1 = ALPHA ? ys : nL * ys;
             float pw = gi.sp.s ? 1.0f : gi.sW, fact = 1.0f;
             e2[0] = 0;
 #pragma unroll
@@ -482,11 +499,11 @@ __device__ __forceinline__ bool gen_item(const Params &prm, Barriers *S, Ring &r
             tc_fence_after();
             const uint32_t wb = w_lane + rg.slot * KP;
             if (FULL)
-                gen_half<NPHMAX, BF16, true>(wb + half * NPHMAX, wb + KP / 2 + half * NPHMAX, gi.d2, e2, gi.sp, sW2,
-                                             NPHMAX, gi.nz, half != 0, s21, gi.sW);
+                gen_half<NPHMAX, BF16, true, ALPHA>(wb + half * NPHMAX, wb + KP / 2 + half * NPHMAX, gi.d2, e2, gi.sp,
+                                                    sW2, NPHMAX, gi.nz, half != 0, s21, gi.sW, gi.gp, pk2(nL, nL));
             else
-                gen_half<NPHMAX, BF16, false>(wb + half * nph, wb + gi.Kr / 2 + half * nph, gi.d2, e2, gi.sp, sW2,
-                                              nph, gi.nz, half != 0, s21, gi.sW);
+                gen_half<NPHMAX, BF16, false, ALPHA>(wb + half * nph, wb + gi.Kr / 2 + half * nph, gi.d2, e2, gi.sp,
+                                                     sW2, nph, gi.nz, half != 0, s21, gi.sW, gi.gp, pk2(nL, nL));
             tmem_st_wait();
             tc_fence_before();
             __syncwarp();
@@ -683,8 +700,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             const ReqDesc &r = reqs[it.req];
             gen_item_load(gi, r, it, half, m);
             // a request's Kr fixes the column count of each half; it must match its operand tiles
-            if (gi.Kr == KP) ok = gen_item<KP, BF16, true>(prm, S, rg, r, it, gi, w_lane, half);
-            else ok = gen_item<KP, BF16, false>(prm, S, rg, r, it, gi, w_lane, half);
+            if (r.Na) ok = gen_item<KP, BF16, false, true>(prm, S, rg, r, it, gi, w_lane, half);
+            else if (gi.Kr == KP) ok = gen_item<KP, BF16, true, false>(prm, S, rg, r, it, gi, w_lane, half);
+            else ok = gen_item<KP, BF16, false, false>(prm, S, rg, r, it, gi, w_lane, half);
         }
     } else if (warp < 16) {
         // ========================================================= epilogue

@@ -52,6 +52,10 @@ class fg21_partition_opts(C.Structure):
     _fields_ = [("n_regions", C.c_int32), ("scheme", C.c_int32), ("weighting", C.c_int32)]
 
 
+class fg21_amplitude_opts(C.Structure):
+    _fields_ = [("n_regions", C.c_int32), ("scheme", C.c_int32), ("weighting", C.c_int32), ("field", C.c_void_p)]
+
+
 class fg21_serve_opts(C.Structure):
     _fields_ = [("mem_budget_bytes", C.c_size_t), ("max_batch_points", C.c_int64), ("max_wait_us", C.c_int32),
                 ("max_inflight", C.c_int32), ("precision", C.c_int32), ("device", C.c_int32)]
@@ -73,6 +77,9 @@ _SIGS = {
     "fg21_device_count": (C.c_int, []),
     "fg21_build_regions": (C.c_int, [_P, _P, _P, _P, _P, _P]),
     "fg21_build_regions_host": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    "fg21_build_regions_ab": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "fg21_build_regions_ab_host": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "fg21_model_shape": (C.c_int, [_P, _P, _P, _P]),
     "fg21_model_destroy": (C.c_int, [_P]),
     "fg21_model_set_data": (C.c_int, [_P, _P]),
     "fg21_model_get_arrays": (C.c_int, [_P, _P, _P]),
@@ -92,6 +99,8 @@ _SIGS = {
     "fg21_graph_launch": (C.c_int, [_P, _P]),
     "fg21_graph_sync_status": (C.c_int, [_P, _P, _P]),
     "fg21_graph_destroy": (C.c_int, [_P]),
+    "fg21_noise_loglike": (C.c_int, [C.c_int64, C.c_double, C.c_double, C.c_int64, C.c_uint64, _P, _P]),
+    "fg21_noise_q": (C.c_int, [_P, C.c_int64, _P, C.c_int64, _P, _P]),
     "fg21_serve_create": (C.c_int, [_P, _P]),
     "fg21_serve_destroy": (C.c_int, [_P]),
     "fg21_serve_register_run": (C.c_int, [_P, _P, _P]),
@@ -194,12 +203,20 @@ def fg21_simulate_data(sky, obs, t21: Sequence[float], sigma_noise: float = 0.0,
 
 
 class Model:
-    """Owner of an fg21_model handle (fg21_model_destroy on close / GC)."""
+    """Owner of an fg21_model handle (fg21_model_destroy on close / GC).  N is
+    the number of components (rows of A); parameter rows have n_params values
+    ([beta_1..beta_Nb, alpha_1..alpha_Na, A21, nu21, sigma21, sigma_n], Na = 0
+    for spectral-index-only models)."""
 
-    def __init__(self, handle: int, N: int, F: int, T: int, labels, edges):
+    def __init__(self, handle: int, N: int, F: int, T: int, labels, edges, Nb: Optional[int] = None,
+                 Na: int = 0, labels_alpha=None, edges_alpha=None):
         self.handle = C.c_void_p(handle)
         self.N, self.F, self.T = N, F, T
+        self.Nb = N if Nb is None else Nb
+        self.Na = Na
+        self.n_params = self.Nb + self.Na + 4
         self.labels, self.edges = labels, edges
+        self.labels_alpha, self.edges_alpha = labels_alpha, edges_alpha
 
     def close(self):
         if self.handle:
@@ -222,6 +239,55 @@ def fg21_build_regions(sky, obs, n_regions: int, scheme="recursive", weighting="
     _check(lib().fg21_build_regions(C.byref(k.sky), C.byref(k.obs), C.byref(opt), C.byref(out), _ptr(lab),
                                     _ptr(edges)), "fg21_build_regions")
     return Model(out.value, n_regions, k.obs.F, k.obs.T, lab, edges)
+
+
+def _amp_opts(n_alpha, scheme_a, weighting_a, field):
+    f = _f64(field)
+    return fg21_amplitude_opts(int(n_alpha), SCHEMES[scheme_a], WEIGHTINGS[weighting_a], _ptr(f)), f
+
+
+def fg21_build_regions_ab(sky, obs, n_beta: int, scheme, weighting, n_alpha: int, field, scheme_a="hierarchical",
+                          weighting_a="beam") -> Model:
+    """Joint amplitude / spectral-index model: spectral-index regions by
+    (scheme, weighting), amplitude regions partitioning `field` [npix] by
+    (scheme_a, weighting_a); components i * n_beta + j."""
+    k = _Keep(sky, obs)
+    opt = fg21_partition_opts(n_beta, SCHEMES[scheme], WEIGHTINGS[weighting])
+    aopt, keep = _amp_opts(n_alpha, scheme_a, weighting_a, field)
+    assert keep.shape == (k.sky.npix,)
+    out = C.c_void_p()
+    lab = np.empty(k.sky.npix, dtype=np.int32)
+    edges = np.empty(n_beta + 1)
+    lab_a = np.empty(k.sky.npix, dtype=np.int32)
+    edges_a = np.empty(n_alpha + 1)
+    _check(lib().fg21_build_regions_ab(C.byref(k.sky), C.byref(k.obs), C.byref(opt), C.byref(aopt), C.byref(out),
+                                       _ptr(lab), _ptr(edges), _ptr(lab_a), _ptr(edges_a)), "fg21_build_regions_ab")
+    return Model(out.value, n_alpha * n_beta, k.obs.F, k.obs.T, lab, edges, Nb=n_beta, Na=n_alpha,
+                 labels_alpha=lab_a, edges_alpha=edges_a)
+
+
+def fg21_build_regions_ab_host(sky, obs, n_beta: int, scheme, weighting, n_alpha: int, field,
+                               scheme_a="hierarchical", weighting_a="beam"):
+    """-> (labels_beta, edges_beta, labels_alpha, edges_alpha, K[Na,Nb,F,T], B[F,T])"""
+    k = _Keep(sky, obs)
+    opt = fg21_partition_opts(n_beta, SCHEMES[scheme], WEIGHTINGS[weighting])
+    aopt, keep = _amp_opts(n_alpha, scheme_a, weighting_a, field)
+    lab = np.empty(k.sky.npix, dtype=np.int32)
+    edges = np.empty(n_beta + 1)
+    lab_a = np.empty(k.sky.npix, dtype=np.int32)
+    edges_a = np.empty(n_alpha + 1)
+    K = np.empty((n_alpha, n_beta, k.obs.F, k.obs.T))
+    B = np.empty((k.obs.F, k.obs.T))
+    _check(lib().fg21_build_regions_ab_host(C.byref(k.sky), C.byref(k.obs), C.byref(opt), C.byref(aopt), _ptr(lab),
+                                            _ptr(edges), _ptr(lab_a), _ptr(edges_a), _ptr(K), _ptr(B)),
+           "fg21_build_regions_ab_host")
+    return lab, edges, lab_a, edges_a, K, B
+
+
+def fg21_model_shape(m: Model) -> dict:
+    nb, na, npar = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(lib().fg21_model_shape(m.handle, C.byref(nb), C.byref(na), C.byref(npar)), "fg21_model_shape")
+    return dict(n_beta=nb.value, n_alpha=na.value, n_params=npar.value)
 
 
 def fg21_model_set_data(m: Model, data: np.ndarray):
@@ -247,7 +313,7 @@ def fg21_model_info(m: Model) -> dict:
 
 def fg21_loglike_batch(m: Model, params: np.ndarray, precision="fp16x3", stream: int = 0) -> np.ndarray:
     p = _f64(params)
-    assert p.ndim == 2 and p.shape[1] == m.N + 4, p.shape
+    assert p.ndim == 2 and p.shape[1] == m.n_params, p.shape
     out = np.empty(p.shape[0])
     _check(lib().fg21_loglike_batch(m.handle, _ptr(p), p.shape[0], _ptr(out), _prec(precision), stream or None),
            "fg21_loglike_batch")
@@ -379,6 +445,21 @@ def fg21_graph_destroy(g: Graph):
 
 
 # ------------------------------------------------------------------ serving
+def fg21_noise_loglike(n_cells: int, sigma_noise: float, sigma_n: float, K: int, seed: int, d_L_noise: int,
+                       stream: int = 0):
+    """L_noise of the accuracy criterion into the DEVICE buffer d_L_noise [K] (asynchronous)."""
+    _check(lib().fg21_noise_loglike(int(n_cells), float(sigma_noise), float(sigma_n), int(K), int(seed), d_L_noise,
+                                    stream or None), "fg21_noise_loglike")
+
+
+def fg21_noise_q(d_L_noise: int, K: int, L_bar, stream: int = 0) -> np.ndarray:
+    """q_i = P(L_noise <= L_bar_i) for each L_bar_i (waits for the stream)."""
+    b = _f64(np.atleast_1d(L_bar))
+    q = np.empty(b.shape[0])
+    _check(lib().fg21_noise_q(d_L_noise, int(K), _ptr(b), b.shape[0], _ptr(q), stream or None), "fg21_noise_q")
+    return q
+
+
 class Server:
     """Owner of an fg21_server handle."""
 

@@ -137,3 +137,67 @@ def fmt_err(name, got, want, tol):
 
 def sigma_floor():
     return math.log(2 * math.pi * I.NOISE_K ** 2)
+
+
+# ------------------------------------------------ amplitude / spectral-index
+# Models with amplitude regions (oracle.OracleModelAB): K[Na, Nb, F, T],
+# params [P, Nb+Na+4].  The kernels' reference point is the mean of every
+# foreground parameter (beta_j and alpha_i) over the request's valid points.
+
+def small_case_ab(npix=2048, Nb=4, Na=3, F=21, T=5, window=4.0, seed=91, scheme="recursive",
+                  scheme_a="hierarchical"):
+    sky = I.make_sky(npix, seed)
+    obs = I.make_obs(F, T, window, 3.0)
+    m = O.build_model_ab(sky, obs, Nb, scheme, "beam", Na, I.amplitude_field(sky), scheme_a, "beam")
+    data = O.simulate_data(sky, obs, np.array(I.FIDUCIAL_T21), I.NOISE_K, I.noise_draws(F, T, seed))
+    return sky, obs, m, data
+
+
+def expected_ab(m, obs, data, params):
+    L = O.loglike_ab(m.K, m.B, data, obs, params)
+    c2 = O.chi2_ab(m.K, m.B, data, obs, params)
+    sig = params[:, -1]
+    return L, c2 / (2.0 * sig * sig)
+
+
+def valid_ab(params, Nb, Na):
+    NP = Nb + Na
+    return (np.all(np.isfinite(params), axis=1) & (params[:, NP + 3] > 0) & (params[:, NP + 2] != 0)
+            & np.all(params[:, Nb:NP] > 0, axis=1))
+
+
+def logl_tolerance_ab(prec: str, m, obs, data, params) -> np.ndarray:
+    """logl_tolerance for the joint model: S = sum_ij |K_ij| |alpha_i w_j(beta_p)
+    - abar_i w_j(bbar)| for the reference-subtracted forms (the departure from
+    the reference point), the whole foreground for the plain form."""
+    Na, Nb = m.K.shape[:2]
+    NP = Nb + Na
+    M = O.fast_model_ab(m.K, m.B, obs, params)
+    r = np.abs(data[None] - M)
+    L = np.log(obs.nu / obs.nu0)
+    w = params[:, Nb:NP, None, None] * np.exp(-params[:, None, :Nb, None] * L)      # [P,Na,Nb,F]
+    if prec == "fp32_direct":
+        S = np.einsum("pijf,ijft->pft", np.abs(w), np.abs(m.K))
+        C = 4.0 * (Na * Nb + 4)
+    else:
+        ok = valid_ab(params, Nb, Na)
+        ref = params[ok, :NP].mean(axis=0)
+        w0 = ref[Nb:NP, None, None] * np.exp(-ref[None, :Nb, None] * L)           # [Na,Nb,F]
+        S = np.einsum("pijf,ijft->pft", np.abs(w - w0[None]), np.abs(m.K))
+        C = C_TOL
+    return 1e-2 + C * U[prec] * np.sum(r * (S + r), axis=(1, 2)) / params[:, NP + 3] ** 2
+
+
+def near_posterior_ab(m, obs, dbeta: float, dalpha: float, P: int, seed: int = 6, sigma=I.NOISE_K):
+    """Data = the joint model at a truth (beta in [2.5, 2.7], alpha in
+    [0.95, 1.05]) plus 25 mK noise; P points moved by U(+-dbeta) in beta and
+    by relative U(+-dalpha) in alpha."""
+    Na, Nb = m.K.shape[:2]
+    rng = I.rng(seed, I.SUB_PARAMS, 78)
+    truth = np.concatenate([rng.uniform(2.5, 2.7, Nb), rng.uniform(0.95, 1.05, Na), [0.155, 85.0, 15.0, sigma]])
+    data = O.fast_model_ab(m.K, m.B, obs, truth)[0] + sigma * I.noise_draws(obs.F, obs.T, seed, 4)
+    g = I.rng(seed, I.SUB_PARAMS, 79)
+    pts = np.repeat(truth[None], P, axis=0)
+    pts[:, :Nb] += g.uniform(-dbeta, dbeta, size=(P, Nb))
+    pts[:, Nb:Nb + Na] *= 1.0 + g.uniform(-dalpha, dalpha, size=(P, Na))
+    return truth, data, pts

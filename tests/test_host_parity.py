@@ -75,3 +75,44 @@ def test_empty_regions_are_allowed():
     assert (counts == 0).any()
     assert np.all(A[counts == 0] == 0.0)
     _compare(sky, obs, 8, "recursive", "beam")
+
+
+# ------------------------------------------------ amplitude / spectral-index
+def _compare_ab(sky, obs, Nb, scheme, weighting, Na, field, scheme_a, weighting_a):
+    lab, edges, lab_a, edges_a, K, B = fg21.fg21_build_regions_ab_host(sky, obs, Nb, scheme, weighting, Na, field,
+                                                                       scheme_a, weighting_a)
+    m = O.build_model_ab(sky, obs, Nb, scheme, weighting, Na, field, scheme_a, weighting_a)
+    assert m.margin > 1e-12, "degenerate seed: a deciding comparison is a near-tie"
+    assert np.array_equal(lab, m.labels_b) and np.array_equal(edges, m.edges_b)
+    assert np.array_equal(lab_a, m.labels_a) and np.array_equal(edges_a, m.edges_a)
+    np.testing.assert_allclose(K, m.K, rtol=1e-12, atol=1e-13 * np.abs(m.K).max())
+    np.testing.assert_allclose(B, m.B, rtol=1e-12)
+
+
+@pytest.mark.parametrize("scheme,scheme_a", [("recursive", "hierarchical"), ("hierarchical", "recursive"),
+                                             ("percentile", "linear")])
+@pytest.mark.parametrize("weighting_a", ["beam", "sky"])
+def test_amplitude_regions(scheme, scheme_a, weighting_a):
+    """Spectral-index and amplitude labels bit-exact, K over the intersections
+    to summation-order rounding (the library builds K as one set of
+    combined-label sums, the oracle from the two masks)."""
+    sky = I.make_sky(1536, 31)
+    obs = I.make_obs(13, 3, 4.0, lst0_h=5.0)
+    field = I.amplitude_field(sky)
+    for Nb, Na in ((3, 2), (5, 4), (1, 3), (6, 1)):
+        _compare_ab(sky, obs, Nb, scheme, "beam", Na, field, scheme_a, weighting_a)
+
+
+def test_amplitude_regions_errors():
+    sky = I.make_sky(256, 2)
+    obs = I.make_obs(5, 2, 1.0)
+    field = I.amplitude_field(sky)
+    with pytest.raises(fg21.Fg21Error) as e:
+        fg21.fg21_build_regions_ab_host(sky, obs, 3, "recursive", "beam", 0, field)
+    assert e.value.code == fg21.FG21_E_ARG
+    with pytest.raises(fg21.Fg21Error):
+        fg21.fg21_build_regions_ab_host(sky, obs, 12, "recursive", "beam", 11, field)     # 132 components
+    bad = field.copy()
+    bad[7] = np.inf
+    with pytest.raises(fg21.Fg21Error):
+        fg21.fg21_build_regions_ab_host(sky, obs, 3, "recursive", "beam", 2, bad)
