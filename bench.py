@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--precision", default="fp16x3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-alpha", action="store_true", help="skip the amplitude-mask model line")
+    ap.add_argument("--no-noise", action="store_true", help="skip the accuracy-criterion (L_noise) line")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample budget")
     return ap.parse_args()
 
@@ -326,6 +328,82 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def alpha_phase(fg21, I, sky, obs, precision, flush, stream, K, Nb=12, Na=2, P=16384):
+    """The joint amplitude / spectral-index model (N_alpha > 1) on the same sky and
+    observation: Nb x Na = 24 components (the K of the headline), P prior draws,
+    timed as graph replays like the headline, plus per-kernel times of direct calls."""
+    import numpy as np
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    t0 = time.time()
+    m = fg21.fg21_build_regions_ab(sky, obs, Nb, "recursive", "beam", Na, I.amplitude_field(sky), "hierarchical",
+                                   "beam")
+    build_s = time.time() - t0
+    data = fg21.fg21_simulate_data(sky, obs, I.FIDUCIAL_T21, I.NOISE_K, I.noise_draws(obs.F, obs.T, 7))
+    fg21.fg21_model_set_data(m, data)
+    params = I.prior_draws_ab(P, Nb, Na, seed=I.BASE_SEED + 3, extra=50)
+    d_p = torch.from_numpy(params).to(dev)
+    d_l = torch.empty(P, dtype=torch.float64, device=dev)
+    sptr = stream.cuda_stream
+    cpg, _ = fg21.fg21_autotune(m, d_p.data_ptr(), P, d_l.data_ptr(), precision, sptr)
+    g = fg21.fg21_graph_create(m, d_p.data_ptr(), P, d_l.data_ptr(), precision)
+    for _ in range(3):
+        flush.zero_()
+        g.launch(sptr)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    torch.cuda.synchronize()
+    for k in range(K):
+        flush.zero_()
+        evs[k][0].record(stream)
+        g.launch(sptr)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    inv = g.sync_status(sptr)
+    g.close()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / K
+    fg21.fg21_model_timing(m, True)
+    for _ in range(max(3, K // 4)):
+        flush.zero_()
+        fg21.fg21_loglike_batch_device(m, d_p.data_ptr(), P, d_l.data_ptr(), precision, sptr)
+    calls, prep_ms, main_ms, red_ms = fg21.fg21_model_timing_totals(m)
+    fg21.fg21_model_timing(m, False)
+    assert np.all(np.isfinite(d_l.cpu().numpy())) and inv == 0
+    m.close()
+    return {"workload": f"npix{sky.npix}_Nb{Nb}_Na{Na}_F{obs.F}_T{obs.T}_P{P}", "components": Nb * Na,
+            "value": P / (ms * 1e-3), "unit": "logL evals/s", "ms_per_step": ms, "steps": K,
+            "channels_per_item": cpg, "build_regions_s": round(build_s, 3),
+            "kernels_ms": {"prep": prep_ms / calls, "tc_loglike": main_ms / calls, "reduce": red_ms / calls},
+            "path": "fg21_graph_launch of fg21_build_regions_ab's model (amplitude masks, ln T230 field)"}
+
+
+def noise_phase(fg21, stream, reps, n_cells, K=65536, sigma=0.025):
+    """The accuracy criterion of Sec. 5.2.2: K noise-only likelihoods over the
+    benchmark's F*T cells (fg21_noise_loglike), then q for a few fitted
+    likelihoods (fg21_noise_q)."""
+    import numpy as np
+    import torch
+    d = torch.empty(K, dtype=torch.float64, device="cuda")
+    sptr = stream.cuda_stream
+    for r in range(3):
+        fg21.fg21_noise_loglike(n_cells, sigma, sigma, K, 1000 + r, d.data_ptr(), sptr)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    torch.cuda.synchronize()
+    for r in range(reps):
+        evs[r][0].record(stream)
+        fg21.fg21_noise_loglike(n_cells, sigma, sigma, K, 2000 + r, d.data_ptr(), sptr)
+        evs[r][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / reps
+    L = d.cpu().numpy()
+    t0 = time.perf_counter()
+    q = fg21.fg21_noise_q(d.data_ptr(), K, np.quantile(L, [0.005, 0.01, 0.5]), sptr)
+    q_ms = (time.perf_counter() - t0) * 1e3
+    return {"workload": f"n_cells{n_cells}_K{K}", "value": K / (ms * 1e-3), "unit": "noise realisations/s",
+            "ms_per_step": ms, "steps": reps, "draws_per_s": K * n_cells / (ms * 1e-3),
+            "q_call_ms": q_ms, "q_at_quantiles_0.005_0.01_0.5": [float(x) for x in q],
+            "path": "fg21_noise_loglike (Philox4x32-10 + Box-Muller radius, one block per realisation)"}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -509,6 +587,10 @@ def main():
         "clocks": clk,
         "macs_per_s": N * F * T * P * ws / (step_ms * 1e-3),
     }
+    if rank == 0 and not args.no_alpha:
+        line["alpha_model"] = alpha_phase(fg21, I, sky, obs, args.precision, flush, stream, max(3, args.steps // 4))
+    if rank == 0 and not args.no_noise:
+        line["noise_q"] = noise_phase(fg21, stream, max(3, args.steps // 20), F * T)
     if rank == 0 and not args.no_serve:
         sv = serve_phase(fg21, I)
         line["serve"] = sv
