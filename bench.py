@@ -577,7 +577,7 @@ def main():
                                 "upload and four launches per call)"},
         "e2e": {"value": P * ws / e2e_s, "unit": "logL evals/s", "h2d_bytes_per_step": int(params.nbytes),
                 "d2h_bytes_per_step": int(P * 8)},
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": 4 * args.steps,     # prep_stats, prep_tc, tc_loglike, reduce
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": f"{pk_kind} dense bf16 burst (fp16 same nominal rate)",

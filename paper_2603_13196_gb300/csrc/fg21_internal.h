@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "fg21.h"
 
 namespace fg21 {
@@ -34,6 +36,7 @@ constexpr int TC_MAX = 192;         // max t-columns per MMA (tcgen05 N): two st
                                     // fit the 512 tensor-memory columns of an SM
 constexpr int STAT_BLOCK = 256;     // points (threads) per statistics block of the per-request prep
 constexpr int KP_MAX = 64;          // max padded K on the tensor path
+static_assert(STAT_BLOCK % TILE_M == 0, "a statistics block covers whole 128-point tiles");
 
 // Per-request descriptor, laid out identically on host and device.
 struct ReqDesc {
@@ -82,6 +85,7 @@ struct ReqDesc {
     float *Bp32;           // [N][F][T] wbar_i A (FP32, SIMT delta form)
     float *dref32;         // [F][T]    reference residual (FP32, SIMT delta form)
     float2 *partials;      // [P][n_part] compensated partial chi^2 (hi, lo)
+    unsigned char *pvalid; // [P] 1 if the point is valid (written by the statistics pass)
     float *pts32;          // [n_tiles][pts_rows][128] per point: beta - bbar of each component's
                            // spectral index (rows < Kp-2, zero beyond N), then A21, nu21,
                            // 1/(2 sigma21^2) (rows Kp-2..Kp); with amplitude parameters, rows
@@ -93,10 +97,10 @@ struct ReqDesc {
 
 // Sizes of one request's workspace pieces (bytes, each 256-aligned).
 struct ReqLayout {
-    size_t stat_part, beta_bar, req_stats, nL32, nu32, scaleB, scaleW, Bp32, dref32, partials, pts32, tiles;
+    size_t stat_part, beta_bar, req_stats, nL32, nu32, scaleB, scaleW, Bp32, dref32, partials, pvalid, pts32, tiles;
     size_t total() const {
         return stat_part + beta_bar + req_stats + nL32 + nu32 + scaleB + scaleW + Bp32 + dref32 +
-               partials + pts32 + tiles;
+               partials + pvalid + pts32 + tiles;
     }
 };
 
@@ -136,5 +140,15 @@ cudaError_t launch_tc(const TcLaunch &L, int num_sms, cudaStream_t stream);
 // Largest multiple of 8 (<= 256 rows of 128 bytes) dividing every tile height.
 int tc_box_rows(const int64_t *tile_rows, int n);
 int tc_map_init();  // resolves cuTensorMapEncodeTiled; FG21_OK or error
+
+// Region building on the current device (fg21_build.cu): the importance
+// weights w[npix] of `weighting` (Sec. 4.2) and, optionally, B[F][T]; the
+// response functions A[N][F][T] of the components `lab` (Sec. 2.2 eq.
+// chromatic_function) and B.  Same FP64 arithmetic as the host code, other
+// summation order.  FG21_OK or an error code (message set).
+int device_importance(const fg21_sky *s, const fg21_obs *o, int weighting, std::vector<double> &w,
+                      std::vector<double> *B);
+int device_precompute(const fg21_sky *s, const fg21_obs *o, const std::vector<int32_t> &lab, int N,
+                      std::vector<double> &A, std::vector<double> &B);
 
 }  // namespace fg21

@@ -83,6 +83,21 @@ __device__ __forceinline__ float2 unpack_pair(uint32_t u) {
     }
 }
 
+// double -> float rounded to nearest (ties away from zero) with integer
+// instructions: conversions run on the FP64 pipe, which is scarce on this
+// part.  Below the normal float range the result is a signed zero, above it
+// (and for NaN) a signed infinity.
+__device__ __forceinline__ float f32_of_f64(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const unsigned sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
+    if (e <= 0) return __uint_as_float(sign);
+    if (e >= 255) return __uint_as_float(sign | 0x7F800000u);
+    const unsigned m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);       // mantissa bits 51..29
+    return __uint_as_float((sign | ((unsigned)e << 23) | m) + ((lo >> 28) & 1u));   // a carry rounds up the exponent
+}
+
 // 8-byte asynchronous copy global -> shared (no register staging; the copies
 // of a thread stay in flight until cp_async_wait_all).
 __device__ __forceinline__ void cp_async8(void *dst, const void *src) {
@@ -118,7 +133,7 @@ __device__ Fin prep_finalize(const ReqDesc &r, float *sh /* [3 NPF + 2 + 2 nwarp
         const int kind = j < 3 * N ? j % 3 : (j == 3 * N ? 0 : 2);   // 0 sum, 1 min, 2 max
         const float *q = r.stat_part + j;
         float v = kind == 0 ? 0.0f : kind == 1 ? INFINITY : -INFINITY;
-        // 16 independent loads in flight per round, combined in block order
+        // 32 independent loads in flight per round, combined in block order
         for (int b0 = 0; b0 < nb; b0 += 16) {
             float x[16];
 #pragma unroll
@@ -200,9 +215,10 @@ __global__ void __launch_bounds__(STAT_BLOCK) prep_stats_kernel(const ReqDesc *_
         th = r.params + (p < r.P ? p : 0) * (N + 4);
     }
     const bool valid = p < r.P && point_valid(th, r);
+    if (p < r.P) r.pvalid[p] = valid;
     float *mine = sh_stats + warp * W;
     for (int i = 0; i < N; ++i) {
-        const float b = valid ? (float)th[i] : 0.0f;
+        const float b = valid ? f32_of_f64(th[i]) : 0.0f;
         float s = b, mn = valid ? b : INFINITY, mx = valid ? b : -INFINITY;
         for (int o = 16; o > 0; o >>= 1) {
             s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -215,7 +231,7 @@ __global__ void __launch_bounds__(STAT_BLOCK) prep_stats_kernel(const ReqDesc *_
             mine[3 * i + 2] = mx;
         }
     }
-    float nv = valid ? 1.0f : 0.0f, ma = valid ? fabsf((float)th[N]) : 0.0f;
+    float nv = valid ? 1.0f : 0.0f, ma = valid ? fabsf(f32_of_f64(th[N])) : 0.0f;
     for (int o = 16; o > 0; o >>= 1) {
         nv += __shfl_xor_sync(0xffffffffu, nv, o);
         ma = fmaxf(ma, __shfl_xor_sync(0xffffffffu, ma, o));
@@ -268,10 +284,10 @@ __device__ __forceinline__ void prep_points(const ReqDesc &r, int tile, const do
     float *out = r.pts32 + (size_t)tile * r.pts_rows * TILE_M + threadIdx.x;
     const bool in = p < r.P;
     for (int k = 0; k < Kp - 2; ++k)
-        out[(size_t)k * TILE_M] = (in && k < N) ? (float)(th[k % Nb] - bbar[k % Nb]) : 0.0f;
-    out[(size_t)(Kp - 2) * TILE_M] = in ? (float)th[NP] : 0.0f;
-    out[(size_t)(Kp - 1) * TILE_M] = in ? (float)th[NP + 1] : 0.0f;
-    const float s21 = in ? (float)th[NP + 2] : 1.0f;
+        out[(size_t)k * TILE_M] = (in && k < N) ? f32_of_f64(th[k % Nb] - bbar[k % Nb]) : 0.0f;
+    out[(size_t)(Kp - 2) * TILE_M] = in ? f32_of_f64(th[NP]) : 0.0f;
+    out[(size_t)(Kp - 1) * TILE_M] = in ? f32_of_f64(th[NP + 1]) : 0.0f;
+    const float s21 = in ? f32_of_f64(th[NP + 2]) : 1.0f;
     out[(size_t)Kp * TILE_M] = 1.0f / (2.0f * s21 * s21);
     if (r.Na) {
         float2 *g2 = reinterpret_cast<float2 *>(out - threadIdx.x + (size_t)(Kp + 4) * TILE_M) + threadIdx.x;
@@ -287,7 +303,7 @@ __device__ __forceinline__ void prep_points(const ReqDesc &r, int tile, const do
                     if (ia != icur) {
                         icur = ia;
                         const double ab = bbar[Nb + ia];
-                        gcur = log1pf((float)(th[Nb + ia] - ab) / (float)ab);   // ln(alpha / abar)
+                        gcur = log1pf(f32_of_f64(th[Nb + ia] - ab) / f32_of_f64(ab));   // ln(alpha / abar)
                     }
                     v = gcur;
                 }
@@ -439,7 +455,7 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_tc_kernel(const ReqDesc *__
         const int i = k / tn, t = k - i * tn;
         const double v = wbar[i] * bw[(size_t)i * Tcp + t];
         bw[(size_t)i * Tcp + t] = v;
-        const float v32 = (float)v;
+        const float v32 = f32_of_f64(v);
         bwf[(size_t)i * Tcp + t] = v32;
         vmax = fmaxf(vmax, fabsf(v32));
     }
@@ -449,7 +465,7 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_tc_kernel(const ReqDesc *__
         for (int i = 0; i < N; ++i) sum += bw[(size_t)i * Tcp + t];
         const double d = dd[t] - sum - r.t_cmb * bb[t];
         dref[t] = d;
-        vmax = fmaxf(vmax, fabsf((float)d));
+        vmax = fmaxf(vmax, fabsf(f32_of_f64(d)));
     }
     for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
     if ((threadIdx.x & 31) == 0) sh_red[threadIdx.x >> 5] = vmax;
@@ -476,7 +492,7 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_tc_kernel(const ReqDesc *__
             if (t < tn) {
                 if (k < N) x = bwf[(size_t)k * Tcp + t] * sB;
                 else if (k == Kp - 2) x = sB;
-                else if (k == Kp - 1) x = (float)(dref[t] * (double)sB);
+                else if (k == Kp - 1) x = f32_of_f64(dref[t]) * sB;       // sB = 2^s: exact
             }
             v[e] = x;
         }
@@ -648,22 +664,21 @@ __global__ void __launch_bounds__(REDUCE_THREADS) reduce_kernel(const ReqDesc *_
     const ReqDesc &r = reqs[find_req_by_point(reqs, n_reqs, gid)];
     const int64_t p = gid - r.pt_begin;
     if (p < 0 || p >= r.P) return;
-    const int N = r.NPF;
-    const double *th = r.params + p * (N + 4);
-    if (!point_valid(th, r)) {
+    if (!r.pvalid[p]) {      // the statistics pass tested the point (point_valid)
         r.logL[p] = -INFINITY;
         atomicAdd(r.invalid, 1ull);
         return;
     }
+    const double sig = r.params[p * (r.NPF + 4) + r.NPF + 3];
     float sh = 0.0f, sl = 0.0f;
     const float2 *__restrict__ part = r.partials + (size_t)p * r.n_part;
+#pragma unroll 4
     for (int g = 0; g < r.n_part; ++g) {
         const float2 v = part[g];
         two_sum_acc(sh, sl, v.x);
         two_sum_acc(sh, sl, v.y);
     }
     const double chi2 = (double)sh + (double)sl;
-    const double sig = th[N + 3];
     const double n = (double)r.F * (double)r.T;
     r.logL[p] = -0.5 * (n * log(2.0 * 3.141592653589793 * sig * sig) + chi2 / (sig * sig));
 }

@@ -191,6 +191,7 @@ ReqLayout request_layout(const ReqDesc &r, int precision) {
     L.Bp32 = delta ? align256(sizeof(float) * (size_t)r.N * r.F * r.T) : 0;
     L.dref32 = delta ? align256(sizeof(float) * (size_t)r.F * r.T) : 0;
     L.partials = align256(sizeof(float2) * (size_t)r.P * r.n_part);
+    L.pvalid = align256((size_t)r.P);
     L.pts32 = tc ? align256(sizeof(float) * (size_t)r.n_tiles * r.pts_rows * TILE_M) : 0;
     L.tiles = tc ? (size_t)r.F * r.n_tchunks * r.tile_rows * 128 : 0;
     return L;
@@ -235,6 +236,7 @@ int prepare_requests(Workspace &ws, std::vector<ReqDesc> &reqs, int precision, P
         r.Bp32 = L.Bp32 ? (float *)p : nullptr; p += L.Bp32;
         r.dref32 = L.dref32 ? (float *)p : nullptr; p += L.dref32;
         r.partials = (float2 *)p; p += L.partials;
+        r.pvalid = (unsigned char *)p; p += L.pvalid;
         r.pts32 = L.pts32 ? (float *)p : nullptr; p += L.pts32;
         r.item_begin = item;
         item += (int64_t)r.n_tiles * r.G;

@@ -700,7 +700,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             const ReqDesc &r = reqs[it.req];
             gen_item_load(gi, r, it, half, m);
             // a request's Kr fixes the column count of each half; it must match its operand tiles
-            if (r.Na) ok = gen_item<KP, BF16, false, true>(prm, S, rg, r, it, gi, w_lane, half);
+            if (r.Na) ok = gi.Kr == KP ? gen_item<KP, BF16, true, true>(prm, S, rg, r, it, gi, w_lane, half)
+                                       : gen_item<KP, BF16, false, true>(prm, S, rg, r, it, gi, w_lane, half);
             else if (gi.Kr == KP) ok = gen_item<KP, BF16, true, false>(prm, S, rg, r, it, gi, w_lane, half);
             else ok = gen_item<KP, BF16, false, false>(prm, S, rg, r, it, gi, w_lane, half);
         }
