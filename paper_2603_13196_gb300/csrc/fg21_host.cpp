@@ -355,9 +355,11 @@ void partition_field(int64_t npix, const double *field, const std::vector<double
 }
 
 // Spectral-index regions (opt), optionally amplitude regions (aopt), and the
-// response functions of their intersections: component i * Nb + j.
+// response functions of their intersections: component i * Nb + j.  With
+// `device` the O(Npix F T) sums (importance weights, response functions) run
+// on the current GPU (fg21_build.cu); the partition is the same host code.
 int build_host(const fg21_sky *sky, const fg21_obs *obs, const fg21_partition_opts *opt,
-               const fg21_amplitude_opts *aopt, Built &out) {
+               const fg21_amplitude_opts *aopt, Built &out, bool device) {
     if (!opt) return set_error(FG21_E_ARG, "NULL opt");
     int rc = check_inputs(sky, obs);
     if (rc) return rc;
@@ -379,19 +381,28 @@ int build_host(const fg21_sky *sky, const fg21_obs *obs, const fg21_partition_op
     const int N = std::max(Na, 1) * Nb;
     try {
         Geometry g;
-        build_geometry(sky, obs, g);
+        if (!device) build_geometry(sky, obs, g);
+        auto weights = [&](int weighting, std::vector<double> &w) -> int {
+            if (device) return device_importance(sky, obs, weighting, w, nullptr);
+            importance(sky, obs, g, weighting, w);
+            return FG21_OK;
+        };
         std::vector<double> w;
-        importance(sky, obs, g, opt->weighting, w);
+        if ((rc = weights(opt->weighting, w))) return rc;
         partition_field(sky->npix, sky->beta, w, Nb, opt->scheme, out.edges, out.lab);
         std::vector<int32_t> comp = out.lab;
         if (Na) {
             std::vector<double> wa;
-            if (aopt->weighting != opt->weighting) importance(sky, obs, g, aopt->weighting, wa);
+            if (aopt->weighting != opt->weighting && (rc = weights(aopt->weighting, wa))) return rc;
             partition_field(sky->npix, aopt->field, aopt->weighting != opt->weighting ? wa : w, Na, aopt->scheme,
                             out.edges_a, out.lab_a);
             for (int64_t q = 0; q < sky->npix; ++q) comp[q] = out.lab_a[q] * Nb + out.lab[q];
         }
-        precompute(sky, obs, g, comp, N, out.A, out.B);
+        if (device) {
+            if ((rc = device_precompute(sky, obs, comp, N, out.A, out.B))) return rc;
+        } else {
+            precompute(sky, obs, g, comp, N, out.A, out.B);
+        }
         std::vector<int64_t> count(N, 0);
         for (int64_t q = 0; q < sky->npix; ++q) count[comp[q]]++;
         out.n_empty = 0;
@@ -443,7 +454,7 @@ int fg21_build_regions_host(const fg21_sky *sky, const fg21_obs *obs, const fg21
                             int32_t *labels_out, double *edges_out, double *A_out, double *B_out) {
     clear_error();
     Built b;
-    int rc = build_host(sky, obs, opt, nullptr, b);
+    int rc = build_host(sky, obs, opt, nullptr, b, false);
     if (rc) return rc;
     if (labels_out) std::memcpy(labels_out, b.lab.data(), sizeof(int32_t) * b.lab.size());
     if (edges_out) std::memcpy(edges_out, b.edges.data(), sizeof(double) * b.edges.size());
@@ -458,7 +469,7 @@ int fg21_build_regions(const fg21_sky *sky, const fg21_obs *obs, const fg21_part
     if (!out) return set_error(FG21_E_ARG, "NULL out");
     *out = nullptr;
     Built b;
-    int rc = build_host(sky, obs, opt, nullptr, b);
+    int rc = build_host(sky, obs, opt, nullptr, b, true);
     if (rc) return rc;
     if (labels_out) std::memcpy(labels_out, b.lab.data(), sizeof(int32_t) * sky->npix);
     if (edges_out) std::memcpy(edges_out, b.edges.data(), sizeof(double) * b.edges.size());
@@ -471,7 +482,7 @@ int fg21_build_regions_ab_host(const fg21_sky *sky, const fg21_obs *obs, const f
     clear_error();
     if (!alpha_opt) return set_error(FG21_E_ARG, "NULL alpha_opt");
     Built b;
-    int rc = build_host(sky, obs, beta_opt, alpha_opt, b);
+    int rc = build_host(sky, obs, beta_opt, alpha_opt, b, false);
     if (rc) return rc;
     if (beta_labels) std::memcpy(beta_labels, b.lab.data(), sizeof(int32_t) * b.lab.size());
     if (beta_edges) std::memcpy(beta_edges, b.edges.data(), sizeof(double) * b.edges.size());
@@ -490,7 +501,7 @@ int fg21_build_regions_ab(const fg21_sky *sky, const fg21_obs *obs, const fg21_p
     *out = nullptr;
     if (!alpha_opt) return set_error(FG21_E_ARG, "NULL alpha_opt");
     Built b;
-    int rc = build_host(sky, obs, beta_opt, alpha_opt, b);
+    int rc = build_host(sky, obs, beta_opt, alpha_opt, b, true);
     if (rc) return rc;
     if (beta_labels) std::memcpy(beta_labels, b.lab.data(), sizeof(int32_t) * b.lab.size());
     if (beta_edges) std::memcpy(beta_edges, b.edges.data(), sizeof(double) * b.edges.size());
