@@ -49,6 +49,9 @@ struct ReqDesc {
     const float *A32;      // [N][F][T]   (direct FP32 form)
     const float *B32;      // [F][T]
     const float *data32;   // [F][T]
+    const float *A_lo;     // [N][F][T]   A - (float)A: with A32 a double-float copy of A (tensor-path prep)
+    const float *E_hi;     // [F][T]      E = D - T_CMB B as a double-float pair (hi, lo)
+    const float *E_lo;     // [F][T]
     // request I/O (device)
     const double *params;  // [P][NPF+4]
     double *logL;          // [P]

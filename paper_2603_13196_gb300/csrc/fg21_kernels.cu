@@ -107,6 +107,22 @@ __device__ __forceinline__ void cp_async8(void *dst, const void *src) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+
+// (sh, sl) += (xh, xl) in double-float arithmetic: Knuth's two-sum of the high
+// parts, the low parts added to its error, then renormalised.
+__device__ __forceinline__ void df_add(float &sh, float &sl, float xh, float xl) {
+    const float s = sh + xh;
+    const float bb = s - sh;
+    const float err = ((sh - (s - bb)) + (xh - bb)) + (sl + xl);
+    sh = s + err;
+    sl = err - (sh - s);
+}
+
 // Parameter rows staged in shared memory are padded to an odd number of
 // doubles so that a warp reading one value of 32 consecutive rows spreads over
 // the banks.
@@ -374,10 +390,11 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_tiles_kernel(const ReqDesc 
 // asynchronous copies of everything it reads (the channel's A slab, D and B;
 // or the tile's parameter rows) into shared memory and finalises the request
 // statistics while they land, so the DRAM latency of its inputs hides behind
-// the statistics.  Then, for a channel block: wbar_c (FP64), the products
-// wbar_c A[c,f,t] in place (FP64), dref[t] = D - sum_c wbar_c A_c - T_CMB B
-// summed in ascending c (FP64: the foreground cancels here), the tile scale
-// 2^sB, and the split-precision tile from the products rounded once to FP32.
+// the statistics.  Then, for a channel block: wbar_c (FP64, split into an FP32
+// pair), the products wbar_c A[c,f,t] in place and dref[t] = D - T_CMB B -
+// sum_c wbar_c A_c summed in ascending c, both in double-float arithmetic (the
+// foreground cancels in dref), the tile scale 2^sB, and the split-precision
+// tile from the products rounded to FP32.
 //
 // Operand tile layout (one per channel and t-chunk, 2 x Kp x Tc_pad 16-bit
 // values): [split s in {hi, mid}][k-chunk kc = k/8][t][8 values k%8], i.e. the
@@ -387,8 +404,9 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_tiles_kernel(const ReqDesc 
 // and columns t >= Tc are zero.
 //
 // Shared memory: bbar [NPF], finalise scratch, then the block's slab --
-// channel: wbar A [N][Tc_pad] FP64, D, B, dref [Tc_pad] FP64, wbar [N] FP64,
-// (wbar A) in FP32 [N][Tc_pad]; points: parameter rows [128][padded_row(NPF+4)].
+// channel: the products' hi and lo parts [N][Tc_pad] each, E hi / lo and dref
+// [Tc_pad], wbar hi / lo [N] (FP32); points: parameter rows
+// [128][padded_row(NPF+4)] FP64.
 template <bool BF16>
 __global__ void __launch_bounds__(PREP_THREADS) prep_tc_kernel(const ReqDesc *__restrict__ reqs) {
     extern __shared__ double smem_d[];
@@ -418,31 +436,39 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_tc_kernel(const ReqDesc *__
         prep_points(r, tile, bbar, slab + (size_t)((int)threadIdx.x < np ? threadIdx.x : 0) * Rp);
         return;
     }
-    // ---- operand tile of one (channel, t-chunk)
+    // ---- operand tile of one (channel, t-chunk), in double-float arithmetic
+    // (FP32 pairs; the FP64 pipe of this part is scarce): A = A32 + A_lo and
+    // E = D - T_CMB B = E_hi + E_lo come from the model; p_c = wbar_c A_c by an
+    // FMA two-product, dref = E - sum_c p_c by two-sums in ascending c (about
+    // 2^-47 relative to the foreground, 1e-9 K at 1e4 K).
     const int fc = blockIdx.x;
     const int f = fc / r.n_tchunks, c = fc % r.n_tchunks;
     const int t0 = c * r.Tc, tn = min(r.Tc, T - t0), Tcp = r.Tc_pad;
-    double *bw = slab;                         // [N][Tcp]
-    double *dd = bw + (size_t)N * Tcp;         // [Tcp] D
-    double *bb = dd + Tcp;                     // [Tcp] B
-    double *dref = bb + Tcp;                   // [Tcp]
-    double *wbar = dref + Tcp;                 // [N]
-    float *bwf = reinterpret_cast<float *>(wbar + N);   // [N][Tcp]
+    float *ph = reinterpret_cast<float *>(slab);   // [N][Tcp] A hi, then the products' hi parts
+    float *pl = ph + (size_t)N * Tcp;              // [N][Tcp] A lo, then the products' lo parts
+    float *eh = pl + (size_t)N * Tcp;              // [Tcp]
+    float *el = eh + Tcp;                          // [Tcp]
+    float *dref = el + Tcp;                        // [Tcp] dref rounded to FP32
+    float *whi = dref + Tcp;                       // [N]
+    float *wlo = whi + N;                          // [N]
     const size_t istride = (size_t)r.F * T, ft0 = (size_t)f * T + t0;
     for (int k = threadIdx.x; k < N * tn; k += blockDim.x) {
         const int i = k / tn, t = k - i * tn;
-        cp_async8(bw + (size_t)i * Tcp + t, r.A + i * istride + ft0 + t);
+        cp_async4(ph + (size_t)i * Tcp + t, r.A32 + i * istride + ft0 + t);
+        cp_async4(pl + (size_t)i * Tcp + t, r.A_lo + i * istride + ft0 + t);
     }
     for (int t = threadIdx.x; t < tn; t += blockDim.x) {
-        cp_async8(dd + t, r.data + ft0 + t);
-        cp_async8(bb + t, r.B + ft0 + t);
+        cp_async4(eh + t, r.E_hi + ft0 + t);
+        cp_async4(el + t, r.E_lo + ft0 + t);
     }
     prep_finalize(r, fin_sh, bbar, fc == 0);
     const double L = r.L[f];
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         double w = exp(-bbar[i % Nb] * L);
         if (r.Na) w *= bbar[Nb + i / Nb];
-        wbar[i] = w;
+        const float h = f32_of_f64(w);
+        whi[i] = h;
+        wlo[i] = f32_of_f64(w - (double)h);
     }
     if (c == 0 && threadIdx.x == 0) {
         r.nL32[f] = (float)(-L);
@@ -453,19 +479,25 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_tc_kernel(const ReqDesc *__
     float vmax = 1.0f;
     for (int k = threadIdx.x; k < N * tn; k += blockDim.x) {
         const int i = k / tn, t = k - i * tn;
-        const double v = wbar[i] * bw[(size_t)i * Tcp + t];
-        bw[(size_t)i * Tcp + t] = v;
-        const float v32 = f32_of_f64(v);
-        bwf[(size_t)i * Tcp + t] = v32;
-        vmax = fmaxf(vmax, fabsf(v32));
+        const size_t o = (size_t)i * Tcp + t;
+        const float ah = ph[o], al = pl[o], wh = whi[i], wl = wlo[i];
+        const float hi = wh * ah;
+        const float lo = fmaf(wh, al, fmaf(wl, ah, fmaf(wh, ah, -hi)));   // two-product + cross terms
+        const float sh = hi + lo;
+        ph[o] = sh;                                 // normalised pair: sh is the product rounded to FP32
+        pl[o] = lo - (sh - hi);
+        vmax = fmaxf(vmax, fabsf(sh));
     }
     __syncthreads();
     for (int t = threadIdx.x; t < tn; t += blockDim.x) {
-        double sum = 0.0;
-        for (int i = 0; i < N; ++i) sum += bw[(size_t)i * Tcp + t];
-        const double d = dd[t] - sum - r.t_cmb * bb[t];
-        dref[t] = d;
-        vmax = fmaxf(vmax, fabsf(f32_of_f64(d)));
+        float sh = 0.0f, sl = 0.0f;
+        for (int i = 0; i < N; ++i) {
+            const size_t o = (size_t)i * Tcp + t;
+            df_add(sh, sl, ph[o], pl[o]);
+        }
+        df_add(sh, sl, -eh[t], -el[t]);              // sum_c p_c - E = -dref
+        dref[t] = -sh;
+        vmax = fmaxf(vmax, fabsf(sh));
     }
     for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
     if ((threadIdx.x & 31) == 0) sh_red[threadIdx.x >> 5] = vmax;
@@ -490,9 +522,9 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_tc_kernel(const ReqDesc *__
             const int k = kc * 8 + e;
             float x = 0.0f;
             if (t < tn) {
-                if (k < N) x = bwf[(size_t)k * Tcp + t] * sB;
+                if (k < N) x = ph[(size_t)k * Tcp + t] * sB;              // sB = 2^s: exact
                 else if (k == Kp - 2) x = sB;
-                else if (k == Kp - 1) x = f32_of_f64(dref[t]) * sB;       // sB = 2^s: exact
+                else if (k == Kp - 1) x = dref[t] * sB;
             }
             v[e] = x;
         }
@@ -769,8 +801,7 @@ cudaError_t launch_prep(const ReqDesc *h_reqs, const ReqDesc *d_reqs, int n_reqs
         const size_t head = sizeof(double) * ((size_t)r.NPF + (3 * (size_t)r.NPF + 2 + 16 + 1) / 2);
         size_t need;
         if (tc) {
-            const size_t chan = sizeof(double) * ((size_t)r.N * r.Tc_pad + 3 * (size_t)r.Tc_pad + r.N) +
-                                sizeof(float) * (size_t)r.N * r.Tc_pad;
+            const size_t chan = sizeof(float) * (2 * (size_t)r.N * r.Tc_pad + 3 * (size_t)r.Tc_pad + 2 * (size_t)r.N);
             const size_t pts = sizeof(double) * (size_t)TILE_M * padded_row(r.NPF + 4);
             need = head + (chan > pts ? chan : pts);
         } else {

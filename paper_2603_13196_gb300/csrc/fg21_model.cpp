@@ -311,6 +311,19 @@ int enqueue_requests(Workspace &ws, std::vector<ReqDesc> &reqs, int precision, c
 }
 
 // ------------------------------------------------------------------ model
+// E = D - T_CMB B (FP64) as a double-float pair: hi = (float)E, lo = (float)(E - hi).
+// data may be NULL (a zero data vector).
+void split_data_term(const fg21_model *m, const double *data, std::vector<float> &hi, std::vector<float> &lo) {
+    const size_t FT = (size_t)m->F * m->T;
+    hi.resize(FT);
+    lo.resize(FT);
+    for (size_t k = 0; k < FT; ++k) {
+        const double e = (data ? data[k] : 0.0) - m->t_cmb * m->B[k];
+        hi[k] = (float)e;
+        lo[k] = (float)(e - (double)hi[k]);
+    }
+}
+
 int model_upload(fg21_model *m) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -325,9 +338,13 @@ int model_upload(fg21_model *m) {
         L[f] = std::log(m->nu[f] / m->nu0);
         m->Lmax = std::max(m->Lmax, std::fabs(L[f]));
     }
-    std::vector<float> A32(NFT), B32(FT), zero32(FT, 0.0f);
-    for (size_t k = 0; k < NFT; ++k) A32[k] = (float)m->A[k];
+    std::vector<float> A32(NFT), Alo(NFT), B32(FT), zero32(FT, 0.0f), Ehi(FT), Elo(FT);
+    for (size_t k = 0; k < NFT; ++k) {
+        A32[k] = (float)m->A[k];
+        Alo[k] = (float)(m->A[k] - (double)A32[k]);
+    }
     for (size_t k = 0; k < FT; ++k) B32[k] = (float)m->B[k];
+    split_data_term(m, nullptr, Ehi, Elo);
     struct Item { void **dst; const void *src; size_t bytes; };
     std::vector<double> zero(FT, 0.0);
     Item items[] = {
@@ -339,6 +356,9 @@ int model_upload(fg21_model *m) {
         {(void **)&m->d_A32, A32.data(), sizeof(float) * NFT},
         {(void **)&m->d_B32, B32.data(), sizeof(float) * FT},
         {(void **)&m->d_data32, zero32.data(), sizeof(float) * FT},
+        {(void **)&m->d_Alo, Alo.data(), sizeof(float) * NFT},
+        {(void **)&m->d_Ehi, Ehi.data(), sizeof(float) * FT},
+        {(void **)&m->d_Elo, Elo.data(), sizeof(float) * FT},
     };
     m->resident_bytes = 0;
     for (auto &it : items) {
@@ -368,6 +388,9 @@ ReqDesc model_request(fg21_model *m, const double *d_params, int64_t P, double *
     r.A32 = m->d_A32;
     r.B32 = m->d_B32;
     r.data32 = m->d_data32;
+    r.A_lo = m->d_Alo;
+    r.E_hi = m->d_Ehi;
+    r.E_lo = m->d_Elo;
     r.params = d_params;
     r.logL = d_logL;
     r.t_cmb = m->t_cmb;
@@ -448,7 +471,8 @@ int fg21_model_destroy(fg21_model *m) {
     {
         std::lock_guard<std::mutex> lk(m->mu);
         m->ws.release();
-        void *ptrs[] = {m->d_A, m->d_B, m->d_data, m->d_L, m->d_nu, m->d_A32, m->d_B32, m->d_data32, m->io_d};
+        void *ptrs[] = {m->d_A, m->d_B, m->d_data, m->d_L, m->d_nu, m->d_A32, m->d_B32, m->d_data32, m->d_Alo,
+                        m->d_Ehi, m->d_Elo, m->io_d};
         for (void *p : ptrs)
             if (p) cudaFree(p);
         if (m->io_h) cudaFreeHost(m->io_h);
@@ -468,9 +492,13 @@ int fg21_model_set_data(fg21_model *m, const double *data) {
         if (!std::isfinite(data[k])) return set_error(FG21_E_ARG, "non-finite data[%zu]", k);
         d32[k] = (float)data[k];
     }
+    std::vector<float> ehi, elo;
+    split_data_term(m, data, ehi, elo);
     if (m->ws.done) FG21_CUDA_TRY(cudaEventSynchronize(m->ws.done));
     FG21_CUDA_TRY(cudaMemcpy(m->d_data, data, sizeof(double) * FT, cudaMemcpyHostToDevice));
     FG21_CUDA_TRY(cudaMemcpy(m->d_data32, d32.data(), sizeof(float) * FT, cudaMemcpyHostToDevice));
+    FG21_CUDA_TRY(cudaMemcpy(m->d_Ehi, ehi.data(), sizeof(float) * FT, cudaMemcpyHostToDevice));
+    FG21_CUDA_TRY(cudaMemcpy(m->d_Elo, elo.data(), sizeof(float) * FT, cudaMemcpyHostToDevice));
     return FG21_OK;
 }
 

@@ -78,6 +78,7 @@ struct fg21_model {
     int device = 0;
     double *d_A = nullptr, *d_B = nullptr, *d_data = nullptr, *d_L = nullptr, *d_nu = nullptr;
     float *d_A32 = nullptr, *d_B32 = nullptr, *d_data32 = nullptr;
+    float *d_Alo = nullptr, *d_Ehi = nullptr, *d_Elo = nullptr;   // double-float parts of A and D - T_CMB B
     size_t resident_bytes = 0;      // A, B, data, tables (not the workspace)
     char *io_d = nullptr, *io_h = nullptr;   // params/logL staging of the host-buffer calls
     size_t io_cap = 0;
