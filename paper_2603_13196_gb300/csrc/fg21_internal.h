@@ -38,6 +38,23 @@ constexpr int STAT_BLOCK = 256;     // points (threads) per statistics block of 
 constexpr int KP_MAX = 64;          // max padded K on the tensor path
 static_assert(STAT_BLOCK % TILE_M == 0, "a statistics block covers whole 128-point tiles");
 
+// Series parameters of the weights' expm1 (tensor path) for |argument| <= xmax:
+// s halvings of the argument (undone by squarings) until it is at most 0.55,
+// then the Taylor degree D: 3 for |y| <= 0.01, 5 for |y| <= 0.1, else 8.  Prep
+// (the per-channel coefficients) and the generators derive it from the same x.
+struct SeriesPlan {
+    int D, s;
+};
+__host__ __device__ inline SeriesPlan series_plan(double xmax) {
+    SeriesPlan sp{8, 0};
+    while (xmax > 0.55 && sp.s < 12) {
+        xmax *= 0.5;
+        ++sp.s;
+    }
+    sp.D = xmax <= 0.01 ? 3 : xmax <= 0.1 ? 5 : 8;
+    return sp;
+}
+
 // Per-request descriptor, laid out identically on host and device.
 struct ReqDesc {
     // model arrays (device)
@@ -82,6 +99,8 @@ struct ReqDesc {
     double *beta_bar;      // [NPF] reference point: mean of each foreground parameter (beta_bar, alpha_bar)
     double *req_stats;     // [4]: n_valid, bound x on |expm1 argument|, max|A21|, reserved
     float *nL32;           // [F] -ln(nu_f/nu0)
+    unsigned long long *coef2;   // [F][8] the weight series' coefficients e_j = (nL_f 2^-s)^j / j! (times
+                                 // 2^sW when s = 0), j = 1..8, each as a packed FP32 pair (tensor path)
     float *nu32;           // [F]
     int *scaleB;           // [F * n_tchunks] power-of-two exponent of each operand tile
     int *scaleW;           // [1] power-of-two exponent of the weight operand
@@ -100,9 +119,10 @@ struct ReqDesc {
 
 // Sizes of one request's workspace pieces (bytes, each 256-aligned).
 struct ReqLayout {
-    size_t stat_part, beta_bar, req_stats, nL32, nu32, scaleB, scaleW, Bp32, dref32, partials, pvalid, pts32, tiles;
+    size_t stat_part, beta_bar, req_stats, nL32, nu32, coef2, scaleB, scaleW, Bp32, dref32, partials, pvalid, pts32,
+        tiles;
     size_t total() const {
-        return stat_part + beta_bar + req_stats + nL32 + nu32 + scaleB + scaleW + Bp32 + dref32 +
+        return stat_part + beta_bar + req_stats + nL32 + nu32 + coef2 + scaleB + scaleW + Bp32 + dref32 +
                partials + pvalid + pts32 + tiles;
     }
 };

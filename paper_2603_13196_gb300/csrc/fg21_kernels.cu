@@ -461,8 +461,24 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_tc_kernel(const ReqDesc *__
         cp_async4(eh + t, r.E_hi + ft0 + t);
         cp_async4(el + t, r.E_lo + ft0 + t);
     }
-    prep_finalize(r, fin_sh, bbar, fc == 0);
+    const Fin fin = prep_finalize(r, fin_sh, bbar, fc == 0);
     const double L = r.L[f];
+    if (c == 0 && threadIdx.x == 32) {
+        // the generators' series coefficients for this channel (the same FP32
+        // operations, in the same order, as a generator would do them)
+        const SeriesPlan sp = series_plan((double)fin.x);
+        const float ys = ldexpf(1.0f, -sp.s), sW = ldexpf(1.0f, fin.sW);
+        const float y1 = (float)(-L) * ys;
+        float pw = sp.s ? 1.0f : sW, fact = 1.0f;
+#pragma unroll
+        for (int j = 1; j < 9; ++j) {
+            pw *= y1;
+            fact *= (float)j;
+            const float e = pw * (1.0f / fact);
+            r.coef2[(size_t)f * 8 + j - 1] =
+                ((unsigned long long)__float_as_uint(e) << 32) | (unsigned long long)__float_as_uint(e);
+        }
+    }
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         double w = exp(-bbar[i % Nb] * L);
         if (r.Na) w *= bbar[Nb + i / Nb];

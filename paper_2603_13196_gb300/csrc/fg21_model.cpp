@@ -185,6 +185,7 @@ ReqLayout request_layout(const ReqDesc &r, int precision) {
     L.req_stats = align256(sizeof(double) * 4);
     L.nL32 = align256(sizeof(float) * r.F);
     L.nu32 = align256(sizeof(float) * r.F);
+    L.coef2 = tc ? align256(sizeof(unsigned long long) * 8 * (size_t)r.F) : 0;
     L.scaleB = align256(sizeof(int) * (size_t)r.F * r.n_tchunks);
     L.scaleW = align256(sizeof(int));
     const bool delta = precision == FG21_PREC_FP32_DELTA;
@@ -231,6 +232,7 @@ int prepare_requests(Workspace &ws, std::vector<ReqDesc> &reqs, int precision, P
         r.req_stats = (double *)p; p += L.req_stats;
         r.nL32 = (float *)p; p += L.nL32;
         r.nu32 = (float *)p; p += L.nu32;
+        r.coef2 = L.coef2 ? (unsigned long long *)p : nullptr; p += L.coef2;
         r.scaleB = (int *)p; p += L.scaleB;
         r.scaleW = (int *)p; p += L.scaleW;
         r.Bp32 = L.Bp32 ? (float *)p : nullptr; p += L.Bp32;

@@ -93,6 +93,7 @@ extern "C" int fg21_loglike_batch_device_noalloc(fg21_model *m, const double *d_
     r.req_stats = (double *)p; p += L.req_stats;
     r.nL32 = (float *)p; p += L.nL32;
     r.nu32 = (float *)p; p += L.nu32;
+    r.coef2 = (unsigned long long *)p; p += L.coef2;
     r.scaleB = (int *)p; p += L.scaleB;
     r.scaleW = (int *)p; p += L.scaleW;
     r.Bp32 = nullptr; p += L.Bp32;

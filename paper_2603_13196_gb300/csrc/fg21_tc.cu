@@ -317,20 +317,6 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t 
     mid = pack2<BF16>(ra, rb);
 }
 
-// Series parameters of a request: squarings s and degree D for |x| <= xmax.
-struct SeriesPlan {
-    int D, s;
-};
-__device__ __forceinline__ SeriesPlan series_plan(double xmax) {
-    SeriesPlan sp{8, 0};
-    while (xmax > 0.55 && sp.s < 12) {
-        xmax *= 0.5;
-        ++sp.s;
-    }
-    sp.D = xmax <= 0.01 ? 3 : xmax <= 0.1 ? 5 : 8;
-    return sp;
-}
-
 // One channel's weights of this thread's point for its half of the request's
 // Kr columns (nph = Kr/4 pairs, at most NPHMAX; FULL: nph = NPHMAX), written
 // to tensor memory: hi at columns t_hi.., mid at t_mid.. (one 32-bit column
@@ -477,16 +463,25 @@ __device__ __forceinline__ bool gen_item(const Params &prm, Barriers *S, Ring &r
         nu_n = __ldg(nup + fn);
         // e_j = (nL / 2^s)^j / j! (ALPHA: 2^(-s j) / j!, the series being in y), times 2^sW when s = 0
         uint64_t e2[9];
-        {
-            const float y1 = ALPHA ? ys : nL * ys;
+        e2[0] = 0;
+        if (ALPHA) {
+            // constant coefficients 2^(-s j) / j! (the series runs in y)
             float pw = gi.sp.s ? 1.0f : gi.sW, fact = 1.0f;
-            e2[0] = 0;
 #pragma unroll
             for (int j = 1; j < 9; ++j) {
-                pw *= y1;
+                pw *= ys;
                 fact *= (float)j;
                 const float e = pw * (1.0f / fact);
                 e2[j] = pk2(e, e);
+            }
+        } else {
+            // the channel's coefficients, written by prep as packed pairs
+            const ulonglong2 *cf = reinterpret_cast<const ulonglong2 *>(r.coef2 + (size_t)f * 8);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const ulonglong2 v = __ldg(cf + j);
+                e2[2 * j + 1] = v.x;
+                e2[2 * j + 2] = v.y;
             }
         }
         float s21 = 0.0f;
@@ -523,17 +518,27 @@ __device__ __forceinline__ void acc_issue(uint32_t taddr, int b0, int nb, float 
     for (int i = 1; i < NB; ++i)
         if (nb > i) tmem_ld16(taddr + (b0 + i) * 16, v[i]);
 }
+// Sum of squares of NB 16-column blocks with packed FP32x2 FMAs: accumulator
+// pair k sums columns 2k, 2k+8 (low half) and 2k+1, 2k+9 (high half) of every
+// block, i.e. eight independent scalar chains in a fixed order, combined by a
+// fixed tree (half the instructions of scalar FMAs).
 template <int NB>
 __device__ __forceinline__ float acc_sumsq(const float (&v)[NB][16], int nb) {
-    float q[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // independent accumulators
+    uint64_t q[4] = {0, 0, 0, 0};
 #pragma unroll
     for (int bb = 0; bb < NB; ++bb) {
         if (bb < nb) {
 #pragma unroll
-            for (int jj = 0; jj < 16; ++jj) q[jj & 7] = fmaf(v[bb][jj], v[bb][jj], q[jj & 7]);
+            for (int jj = 0; jj < 16; jj += 2) {
+                const uint64_t x = pk2(v[bb][jj], v[bb][jj + 1]);
+                q[(jj >> 1) & 3] = fma2(x, x, q[(jj >> 1) & 3]);
+            }
         }
     }
-    return ((q[0] + q[1]) + (q[2] + q[3])) + ((q[4] + q[5]) + (q[6] + q[7]));
+    float a[8];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) upk2(q[k], a[2 * k], a[2 * k + 1]);
+    return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
 }
 
 // The epilogue of every stage of one item by one epilogue warp: per stage wait
