@@ -108,6 +108,8 @@ struct ReqDesc {
     float *dref32;         // [F][T]    reference residual (FP32, SIMT delta form)
     float2 *partials;      // [P][n_part] compensated partial chi^2 (hi, lo)
     unsigned char *pvalid; // [P] 1 if the point is valid (written by the statistics pass)
+    double2 *pnorm;        // [P] (F T ln(2 pi sigma_n^2), 1 / sigma_n^2) of each valid point (tensor path: written
+                           // by prep's point blocks; null on the SIMT paths, whose reduction forms them itself)
     float *pts32;          // [n_tiles][pts_rows][128] per point: beta - bbar of each component's
                            // spectral index (rows < Kp-2, zero beyond N), then A21, nu21,
                            // 1/(2 sigma21^2) (rows Kp-2..Kp); with amplitude parameters, rows
@@ -119,11 +121,11 @@ struct ReqDesc {
 
 // Sizes of one request's workspace pieces (bytes, each 256-aligned).
 struct ReqLayout {
-    size_t stat_part, beta_bar, req_stats, nL32, nu32, coef2, scaleB, scaleW, Bp32, dref32, partials, pvalid, pts32,
-        tiles;
+    size_t stat_part, beta_bar, req_stats, nL32, nu32, coef2, scaleB, scaleW, Bp32, dref32, partials, pvalid, pnorm,
+        pts32, tiles;
     size_t total() const {
         return stat_part + beta_bar + req_stats + nL32 + nu32 + coef2 + scaleB + scaleW + Bp32 + dref32 +
-               partials + pvalid + pts32 + tiles;
+               partials + pvalid + pnorm + pts32 + tiles;
     }
 };
 

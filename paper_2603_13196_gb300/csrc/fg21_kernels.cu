@@ -305,6 +305,12 @@ __device__ __forceinline__ void prep_points(const ReqDesc &r, int tile, const do
     out[(size_t)(Kp - 1) * TILE_M] = in ? f32_of_f64(th[NP + 1]) : 0.0f;
     const float s21 = in ? f32_of_f64(th[NP + 2]) : 1.0f;
     out[(size_t)Kp * TILE_M] = 1.0f / (2.0f * s21 * s21);
+    // the sigma_n terms of eq. likelihood for the reduction (FP64, once per point)
+    if (in && r.pvalid[p]) {
+        const double sig = th[NP + 3];
+        r.pnorm[p] = make_double2((double)r.F * (double)r.T * log(2.0 * 3.141592653589793 * sig * sig),
+                                  1.0 / (sig * sig));
+    }
     if (r.Na) {
         float2 *g2 = reinterpret_cast<float2 *>(out - threadIdx.x + (size_t)(Kp + 4) * TILE_M) + threadIdx.x;
         int icur = -1;
@@ -717,7 +723,6 @@ __global__ void __launch_bounds__(REDUCE_THREADS) reduce_kernel(const ReqDesc *_
         atomicAdd(r.invalid, 1ull);
         return;
     }
-    const double sig = r.params[p * (r.NPF + 4) + r.NPF + 3];
     float sh = 0.0f, sl = 0.0f;
     const float2 *__restrict__ part = r.partials + (size_t)p * r.n_part;
 #pragma unroll 4
@@ -727,8 +732,14 @@ __global__ void __launch_bounds__(REDUCE_THREADS) reduce_kernel(const ReqDesc *_
         two_sum_acc(sh, sl, v.y);
     }
     const double chi2 = (double)sh + (double)sl;
-    const double n = (double)r.F * (double)r.T;
-    r.logL[p] = -0.5 * (n * log(2.0 * 3.141592653589793 * sig * sig) + chi2 / (sig * sig));
+    if (r.pnorm) {           // sigma_n terms from prep (tensor path)
+        const double2 nm = r.pnorm[p];
+        r.logL[p] = -0.5 * (nm.x + chi2 * nm.y);
+    } else {
+        const double sig = r.params[p * (r.NPF + 4) + r.NPF + 3];
+        const double n = (double)r.F * (double)r.T;
+        r.logL[p] = -0.5 * (n * log(2.0 * 3.141592653589793 * sig * sig) + chi2 / (sig * sig));
+    }
 }
 
 // Validation helper: T_model[p,f,t] with the arithmetic of the SIMT forms.

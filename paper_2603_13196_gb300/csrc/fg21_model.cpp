@@ -193,6 +193,7 @@ ReqLayout request_layout(const ReqDesc &r, int precision) {
     L.dref32 = delta ? align256(sizeof(float) * (size_t)r.F * r.T) : 0;
     L.partials = align256(sizeof(float2) * (size_t)r.P * r.n_part);
     L.pvalid = align256((size_t)r.P);
+    L.pnorm = tc ? align256(sizeof(double2) * (size_t)r.P) : 0;
     L.pts32 = tc ? align256(sizeof(float) * (size_t)r.n_tiles * r.pts_rows * TILE_M) : 0;
     L.tiles = tc ? (size_t)r.F * r.n_tchunks * r.tile_rows * 128 : 0;
     return L;
@@ -239,6 +240,7 @@ int prepare_requests(Workspace &ws, std::vector<ReqDesc> &reqs, int precision, P
         r.dref32 = L.dref32 ? (float *)p : nullptr; p += L.dref32;
         r.partials = (float2 *)p; p += L.partials;
         r.pvalid = (unsigned char *)p; p += L.pvalid;
+        r.pnorm = L.pnorm ? (double2 *)p : nullptr; p += L.pnorm;
         r.pts32 = L.pts32 ? (float *)p : nullptr; p += L.pts32;
         r.item_begin = item;
         item += (int64_t)r.n_tiles * r.G;

@@ -100,6 +100,7 @@ extern "C" int fg21_loglike_batch_device_noalloc(fg21_model *m, const double *d_
     r.dref32 = nullptr; p += L.dref32;
     r.partials = (float2 *)p; p += L.partials;
     r.pvalid = (unsigned char *)p; p += L.pvalid;
+    r.pnorm = (double2 *)p; p += L.pnorm;
     r.pts32 = (float *)p; p += L.pts32;
     char *arena = p;
     r.item_begin = 0;
