@@ -145,3 +145,32 @@ def test_ab_multi_and_graph_mixed_with_beta_only(fg21lib):
         assert fg21lib.fg21_graph_sync_status(g, s) == 0
         assert np.array_equal(la.cpu().numpy(), got[0]) and np.array_equal(lb.cpu().numpy(), got[1])
     g.close()
+
+
+def test_ab_served_and_allocation_free(fg21lib):
+    """The serving loop (bit for bit the direct call's results) and the
+    allocation-free device call (within tolerance of them) run amplitude-mask
+    models."""
+    import ctypes as C
+    torch = pytest.importorskip("torch")
+    sky, obs, m, data = cases.small_case_ab(npix=2048, Nb=5, Na=3, F=31, T=8)
+    model = _model(fg21lib, sky, obs, m)
+    fg21lib.fg21_model_set_data(model, data)
+    params = I.prior_draws_ab(500, 5, 3, seed=21)
+    direct = fg21lib.fg21_loglike_batch(model, params, "fp16x3")
+    srv = fg21lib.Server(mem_budget_bytes=1 << 30, max_batch_points=4096, max_wait_us=100, max_inflight=2)
+    rid, admitted = fg21lib.fg21_serve_register_run(srv, model)
+    assert admitted
+    t, out = fg21lib.fg21_serve_submit(srv, rid, params)
+    assert fg21lib.fg21_serve_wait(srv, t, 60000) == 0
+    srv.close()
+    np.testing.assert_array_equal(out, direct)
+    d_p = torch.from_numpy(params).cuda()
+    d_na = torch.full((500,), float("nan"), dtype=torch.float64, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    rc = fg21lib.lib().fg21_loglike_batch_device_noalloc(model.handle, C.c_void_p(d_p.data_ptr()), 500,
+                                                          C.c_void_p(d_na.data_ptr()), 0, C.c_void_p(s))
+    assert rc == 0, fg21lib.lib().fg21_last_error()
+    torch.cuda.synchronize()
+    tol = cases.logl_tolerance_ab("fp16x3", m, obs, data, params)
+    assert np.all(np.abs(d_na.cpu().numpy() - direct) <= tol)
