@@ -94,9 +94,9 @@ struct ReqDesc {
     int64_t pt_begin;            // first global point index of this request (reduction)
     char *tiles;                 // this request's operand tiles (arena + tile_row0 * 128)
     // workspace (device)
-    float *stat_part;      // [n_stat_blocks][3 NPF + 2]: sum, min, max per foreground parameter, n_valid,
+    float *stat_part;      // [n_stat_blocks][2 NPF + 2]: min, max per foreground parameter, n_valid,
                            // max|A21|
-    double *beta_bar;      // [NPF] reference point: mean of each foreground parameter (beta_bar, alpha_bar)
+    double *beta_bar;      // [NPF] reference point: midrange of each foreground parameter (beta_bar, alpha_bar)
     double *req_stats;     // [4]: n_valid, bound x on |expm1 argument|, max|A21|, reserved
     float *nL32;           // [F] -ln(nu_f/nu0)
     unsigned long long *coef2;   // [F][8] the weight series' coefficients e_j = (nL_f 2^-s)^j / j! (times

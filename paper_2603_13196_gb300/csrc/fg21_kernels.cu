@@ -3,8 +3,8 @@
 //
 // The likelihood of eq. likelihood (Sec. 2.3.1) over the fast forward model of
 // eq. fast_forward_model (Sec. 2.2) is evaluated in a reference-subtracted form:
-// with a per-request reference spectral index bbar_i (mean over the request's
-// valid points) and wbar_{i,f} = (nu_f/nu0)^-bbar_i,
+// with a per-request reference spectral index bbar_i (the midrange of the
+// request's valid points) and wbar_{i,f} = (nu_f/nu0)^-bbar_i,
 //
 //   D - M = dref[f,t] - sum_i (wbar_{i,f} A[i,f,t]) expm1(-(beta_{p,i} - bbar_i) L_f) - T21(nu_f)
 //   dref[f,t] = D[f,t] - sum_i wbar_{i,f} A[i,f,t] - T_CMB B[f,t]          (FP64, once per request)
@@ -43,11 +43,22 @@ __device__ __forceinline__ bool point_valid(const double *th, const ReqDesc &r) 
 }
 
 
-// a1, pass 1: per block of STAT_BLOCK points (one thread each), the sum / min
-// / max of each foreground parameter (each region's beta, then each amplitude
-// alpha) over valid points (FP32: the reference point only has to be a
-// deterministic value near the points; the rearranged likelihood is exact for
-// any reference), the valid count and max |A21|.
+// a1, pass 1: per block of STAT_BLOCK points (one thread each), the min and
+// max of each foreground parameter (each region's beta, then each amplitude
+// alpha) over valid points, the valid count and max |A21|.  The reference
+// point is the midrange (min + max) / 2: the rearranged likelihood is exact for
+// any reference, and the midrange minimises max |theta - reference|, the bound
+// that sets the weight series.  FP32, warp reductions by redux.sync.
+__device__ __forceinline__ float warp_min(float v) {
+    float r;
+    asm("redux.sync.min.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ float warp_max(float v) {
+    float r;
+    asm("redux.sync.max.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+    return r;
+}
 // Warps reduce by shuffles in a fixed tree and are combined in warp order.
 // Largest s with 2^s * maxabs <= 2^15 (half the FP16 range), clamped to
 // [-40, 40]; exact, from the exponent and mantissa bits (no FP64 log).
@@ -129,8 +140,8 @@ __device__ __forceinline__ void df_add(float &sh, float &sl, float xh, float xl)
 __host__ __device__ __forceinline__ int padded_row(int R) { return R | 1; }
 
 // a1, pass 2, run by every block of the second prep kernel: the reference
-// point (bbar_i = mean of the valid points' beta_i, and abar_i = mean alpha_i
-// with amplitude regions), a bound x on the weights' expm1 argument,
+// point (bbar_i = midrange of the valid points' beta_i, and abar_i = midrange
+// of alpha_i with amplitude regions), a bound x on the weights' expm1 argument,
 // max_i |beta - bbar_i| * max_f |L_f| + max_i |ln(alpha / abar_i)| (it sets the
 // weight series and the power-of-two scale sW of the weight operand), the
 // valid count and max |A21|.
@@ -142,11 +153,11 @@ struct Fin {
     float nv, ma, x;
     int sW;
 };
-__device__ Fin prep_finalize(const ReqDesc &r, float *sh /* [3 NPF + 2 + 2 nwarps] */, double *bbar_sh, bool publish) {
-    const int N = r.NPF, Nb = r.Nb, nb = r.n_stat_blocks, W = 3 * N + 2;
+__device__ Fin prep_finalize(const ReqDesc &r, float *sh /* [2 NPF + 2 + 2 nwarps] */, double *bbar_sh, bool publish) {
+    const int N = r.NPF, Nb = r.Nb, nb = r.n_stat_blocks, W = 2 * N + 2;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int j = threadIdx.x; j < W; j += blockDim.x) {
-        const int kind = j < 3 * N ? j % 3 : (j == 3 * N ? 0 : 2);   // 0 sum, 1 min, 2 max
+        const int kind = j < 2 * N ? 1 + (j & 1) : (j == 2 * N ? 0 : 2);   // 0 sum, 1 min, 2 max
         const float *q = r.stat_part + j;
         float v = kind == 0 ? 0.0f : kind == 1 ? INFINITY : -INFINITY;
         // 32 independent loads in flight per round, combined in block order
@@ -161,15 +172,16 @@ __device__ Fin prep_finalize(const ReqDesc &r, float *sh /* [3 NPF + 2 + 2 nwarp
         sh[j] = v;
     }
     __syncthreads();
-    const float nv = sh[3 * N], ma = sh[3 * N + 1];
+    const float nv = sh[2 * N], ma = sh[2 * N + 1];
     float dev = 0.0f, gdev = 0.0f;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        const float bb = nv > 0.0f ? sh[3 * i] / nv : 0.0f;
+        const float mn = sh[2 * i], mx = sh[2 * i + 1];
+        const float bb = nv > 0.0f ? 0.5f * (mn + mx) : 0.0f;
         bbar_sh[i] = (double)bb;
         if (publish) r.beta_bar[i] = (double)bb;
         if (nv > 0.0f) {
-            if (i < Nb) dev = fmaxf(dev, fmaxf(sh[3 * i + 2] - bb, bb - sh[3 * i + 1]));
-            else gdev = fmaxf(gdev, fmaxf(logf(sh[3 * i + 2] / bb), logf(bb / sh[3 * i + 1])));   // alpha > 0
+            if (i < Nb) dev = fmaxf(dev, fmaxf(mx - bb, bb - mn));
+            else gdev = fmaxf(gdev, fmaxf(logf(mx / bb), logf(bb / mn)));   // alpha > 0
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -204,12 +216,12 @@ __device__ Fin prep_finalize(const ReqDesc &r, float *sh /* [3 NPF + 2 + 2 nwarp
 }
 
 __global__ void __launch_bounds__(STAT_BLOCK) prep_stats_kernel(const ReqDesc *__restrict__ reqs, int staged) {
-    // shared: [STAT_BLOCK / 32][3 NPF + 2] FP32 warp partials, then (staged) the
+    // shared: [STAT_BLOCK / 32][2 NPF + 2] FP32 warp partials, then (staged) the
     // block's parameter rows [STAT_BLOCK][padded_row(NPF + 4)] FP64
-    extern __shared__ double sh_stats_d[];
+    extern __shared__ double sh_stats_d[];     // [STAT_BLOCK / 32][2 NPF + 2] partials, then the rows
     const ReqDesc &r = reqs[blockIdx.y];
     if ((int)blockIdx.x >= r.n_stat_blocks) return;
-    const int N = r.NPF, W = 3 * N + 2, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int N = r.NPF, W = 2 * N + 2, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
     float *sh_stats = reinterpret_cast<float *>(sh_stats_d);
     const int64_t p0 = (int64_t)blockIdx.x * STAT_BLOCK, p = p0 + threadIdx.x;
@@ -235,31 +247,22 @@ __global__ void __launch_bounds__(STAT_BLOCK) prep_stats_kernel(const ReqDesc *_
     float *mine = sh_stats + warp * W;
     for (int i = 0; i < N; ++i) {
         const float b = valid ? f32_of_f64(th[i]) : 0.0f;
-        float s = b, mn = valid ? b : INFINITY, mx = valid ? b : -INFINITY;
-        for (int o = 16; o > 0; o >>= 1) {
-            s += __shfl_xor_sync(0xffffffffu, s, o);
-            mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        }
+        const float mn = warp_min(valid ? b : INFINITY), mx = warp_max(valid ? b : -INFINITY);
         if (lane == 0) {
-            mine[3 * i] = s;
-            mine[3 * i + 1] = mn;
-            mine[3 * i + 2] = mx;
+            mine[2 * i] = mn;
+            mine[2 * i + 1] = mx;
         }
     }
-    float nv = valid ? 1.0f : 0.0f, ma = valid ? fabsf(f32_of_f64(th[N])) : 0.0f;
-    for (int o = 16; o > 0; o >>= 1) {
-        nv += __shfl_xor_sync(0xffffffffu, nv, o);
-        ma = fmaxf(ma, __shfl_xor_sync(0xffffffffu, ma, o));
-    }
+    const float nv = (float)__popc(__ballot_sync(0xffffffffu, valid));
+    const float ma = warp_max(valid ? fabsf(f32_of_f64(th[N])) : 0.0f);
     if (lane == 0) {
-        mine[3 * N] = nv;
-        mine[3 * N + 1] = ma;
+        mine[2 * N] = nv;
+        mine[2 * N + 1] = ma;
     }
     __syncthreads();
     float *out = r.stat_part + (size_t)blockIdx.x * W;
     for (int j = threadIdx.x; j < W; j += blockDim.x) {
-        const int kind = j < 3 * N ? j % 3 : (j == 3 * N ? 0 : 2);   // 0 sum, 1 min, 2 max
+        const int kind = j < 2 * N ? 1 + (j & 1) : (j == 2 * N ? 0 : 2);   // 0 sum, 1 min, 2 max
         float v = sh_stats[j];
         for (int w = 1; w < nw; ++w) {
             const float x = sh_stats[w * W + j];
@@ -348,11 +351,11 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_tiles_kernel(const ReqDesc 
     const int nfc = r.F * r.n_tchunks;
     const int N = r.N, NP = r.NPF, Nb = r.Nb, T = r.T;
     if ((int)blockIdx.x >= nfc) return;
-    // shared memory: bbar [NPF] FP64, finalise scratch [3 NPF + 2 + 16] FP32 (rounded
+    // shared memory: bbar [NPF] FP64, finalise scratch [2 NPF + 2 + 16] FP32 (rounded
     // to doubles), wbar [N] FP64
     double *bbar = smem_d;
     float *fin_sh = reinterpret_cast<float *>(bbar + NP);
-    double *wbar = bbar + NP + (3 * NP + 2 + 16 + 1) / 2;
+    double *wbar = bbar + NP + (2 * NP + 2 + 16 + 1) / 2;
     prep_finalize(r, fin_sh, bbar, blockIdx.x == 0);
     const int fc = blockIdx.x;
     const int f = fc / r.n_tchunks, c = fc % r.n_tchunks;
@@ -424,7 +427,7 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_tc_kernel(const ReqDesc *__
     const int N = r.N, NP = r.NPF, Nb = r.Nb, T = r.T;
     double *bbar = smem_d;
     float *fin_sh = reinterpret_cast<float *>(bbar + NP);
-    double *slab = bbar + NP + (3 * NP + 2 + 16 + 1) / 2;
+    double *slab = bbar + NP + (2 * NP + 2 + 16 + 1) / 2;
     if ((int)blockIdx.x >= nfc) {
         // ---- per-point operands of one 128-point tile
         const int tile = blockIdx.x - nfc;
@@ -811,7 +814,7 @@ cudaError_t launch_prep(const ReqDesc *h_reqs, const ReqDesc *d_reqs, int n_reqs
     for (int k = 0; k < n_reqs; ++k) maxNP = maxNP > h_reqs[k].NPF ? maxNP : h_reqs[k].NPF;
     dim3 g1(max_stat_blocks, n_reqs);
     // warp partials, then the staged parameter rows when they fit comfortably
-    const size_t part = sizeof(double) * (((size_t)(STAT_BLOCK / 32) * (3 * maxNP + 2) + 1) / 2);
+    const size_t part = sizeof(double) * (((size_t)(STAT_BLOCK / 32) * (2 * maxNP + 2) + 1) / 2);
     const size_t slab1 = sizeof(double) * (size_t)STAT_BLOCK * padded_row(maxNP + 4);
     const int staged = slab1 <= 96 * 1024;
     const size_t sm1 = part + (staged ? slab1 : 0);
@@ -825,7 +828,7 @@ cudaError_t launch_prep(const ReqDesc *h_reqs, const ReqDesc *d_reqs, int n_reqs
     size_t sm = 0;
     for (int k = 0; k < n_reqs; ++k) {
         const ReqDesc &r = h_reqs[k];
-        const size_t head = sizeof(double) * ((size_t)r.NPF + (3 * (size_t)r.NPF + 2 + 16 + 1) / 2);
+        const size_t head = sizeof(double) * ((size_t)r.NPF + (2 * (size_t)r.NPF + 2 + 16 + 1) / 2);
         size_t need;
         if (tc) {
             const size_t chan = sizeof(float) * (2 * (size_t)r.N * r.Tc_pad + 3 * (size_t)r.Tc_pad + 2 * (size_t)r.N);

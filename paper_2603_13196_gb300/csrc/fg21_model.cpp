@@ -180,7 +180,7 @@ void plan_request(ReqDesc &r, int precision, int num_sms, int64_t total_tiles) {
 ReqLayout request_layout(const ReqDesc &r, int precision) {
     ReqLayout L{};
     const bool tc = precision == FG21_PREC_FP16X3 || precision == FG21_PREC_BF16X3;
-    L.stat_part = align256(sizeof(float) * (size_t)r.n_stat_blocks * (3 * r.NPF + 2));
+    L.stat_part = align256(sizeof(float) * (size_t)r.n_stat_blocks * (2 * r.NPF + 2));
     L.beta_bar = align256(sizeof(double) * r.NPF);
     L.req_stats = align256(sizeof(double) * 4);
     L.nL32 = align256(sizeof(float) * r.F);

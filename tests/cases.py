@@ -82,9 +82,13 @@ def expected(m, obs, data, params):
 
 
 def reference_beta(params, N):
-    """The kernels' reference point: mean beta_i over the request's valid points."""
+    """The kernels' reference point: the midrange of beta_i over the request's
+    valid points."""
     ok = np.all(np.isfinite(params), axis=1) & (params[:, N + 3] > 0) & (params[:, N + 2] != 0)
-    return params[ok, :N].mean(axis=0) if ok.any() else np.zeros(N)
+    if not ok.any():
+        return np.zeros(N)
+    v = params[ok, :N]
+    return 0.5 * (v.min(axis=0) + v.max(axis=0))
 
 
 def logl_tolerance(prec: str, m, obs, data, params) -> np.ndarray:
@@ -141,7 +145,7 @@ def sigma_floor():
 
 # ------------------------------------------------ amplitude / spectral-index
 # Models with amplitude regions (oracle.OracleModelAB): K[Na, Nb, F, T],
-# params [P, Nb+Na+4].  The kernels' reference point is the mean of every
+# params [P, Nb+Na+4].  The kernels' reference point is the midrange of every
 # foreground parameter (beta_j and alpha_i) over the request's valid points.
 
 def small_case_ab(npix=2048, Nb=4, Na=3, F=21, T=5, window=4.0, seed=91, scheme="recursive",
@@ -181,7 +185,8 @@ def logl_tolerance_ab(prec: str, m, obs, data, params) -> np.ndarray:
         C = 4.0 * (Na * Nb + 4)
     else:
         ok = valid_ab(params, Nb, Na)
-        ref = params[ok, :NP].mean(axis=0)
+        v = params[ok, :NP]
+        ref = 0.5 * (v.min(axis=0) + v.max(axis=0))
         w0 = ref[Nb:NP, None, None] * np.exp(-ref[None, :Nb, None] * L)           # [Na,Nb,F]
         S = np.einsum("pijf,ijft->pft", np.abs(w - w0[None]), np.abs(m.K))
         C = C_TOL
