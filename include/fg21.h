@@ -260,7 +260,7 @@ int fg21_loglike_batch_device(fg21_model *m, const double *d_params, int64_t P, 
  * one static device array of FG21_NOALLOC_SCRATCH_BYTES (32 MiB) that every GPU
  * which loads the library keeps until the process exits.  The model itself
  * must already exist (fg21_build_regions allocates it).  A request whose
- * scratch would not fit returns FG21_E_RANGE (the limit is about 140,000
+ * scratch would not fit returns FG21_E_RANGE (the limit is about 105,000
  * points at N = 24, F = 301, T = 100; split larger batches).  The first
  * call on a device looks up the array's device address (cudaGetSymbolAddress)
  * with that device current, so make that first call before any stream capture.

@@ -157,3 +157,38 @@ def test_workload2_full(fg21lib):
         report(f"w2_{prec}", max_abs=np.max(np.abs(got - want)),
                max_rel_dterm=np.max(np.abs(got - want) / np.abs(dterm)))
         assert np.all(np.abs(got - want) <= tol), cases.fmt_err(prec, got, want, tol)
+
+
+def test_workload3_benchmark_configuration_sampled(fg21lib):
+    """The benchmark's own workload and launch configuration (49152-pixel sky,
+    N = 24, F = 301, T = 100, 16384 prior draws; the work split fg21_autotune
+    picks; the step replayed from a CUDA graph): labels equal the oracle's, and
+    every 64th logL (256 points the oracle evaluates one by one) is within the
+    derived tolerance."""
+    torch = pytest.importorskip("torch")
+    wl = cases.I.workload(3)
+    sky, obs = wl.sky(), wl.obs()
+    m = O.build_model(sky, obs, wl.N, wl.scheme, wl.weighting)
+    data = O.simulate_data(sky, obs, np.array(cases.I.FIDUCIAL_T21), cases.I.NOISE_K, wl.noise())
+    model = fg21lib.fg21_build_regions(sky, obs, wl.N, wl.scheme, wl.weighting)
+    assert np.array_equal(model.labels, m.labels)
+    fg21lib.fg21_model_set_data(model, data)
+    params = wl.params()
+    P = params.shape[0]
+    d_p = torch.from_numpy(params).cuda()
+    d_l = torch.empty(P, dtype=torch.float64, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    fg21lib.fg21_autotune(model, d_p.data_ptr(), P, d_l.data_ptr(), "fp16x3", s)
+    g = fg21lib.fg21_graph_create(model, d_p.data_ptr(), P, d_l.data_ptr(), "fp16x3")
+    g.launch(s)
+    assert g.sync_status(s) == 0
+    got = d_l.cpu().numpy()
+    g.close()
+    idx = np.arange(0, P, 64)
+    want, dterm = cases.expected(m, obs, data, params[idx])
+    tol = cases.logl_tolerance("fp16x3", m, obs, data, params[idx])
+    err = np.abs(got[idx] - want)
+    report("w3_graph_sampled", max_abs=err.max(), max_rel_dterm=np.max(err / np.abs(dterm)),
+           max_err_over_tol=np.max(err / tol))
+    assert np.all(err <= tol), cases.fmt_err("w3", got[idx], want, tol)
+    assert np.all(np.isfinite(got))
