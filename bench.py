@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-alpha", action="store_true", help="skip the amplitude-mask model line")
     ap.add_argument("--no-noise", action="store_true", help="skip the accuracy-criterion (L_noise) line")
+    ap.add_argument("--no-occam", action="store_true", help="skip the log L_max(N) line")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample budget")
     return ap.parse_args()
 
@@ -66,6 +67,24 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def max_over_ranks(values, device=None):
+    """Element-wise maximum of per-rank timings (a no-op on one process): each
+    replica times its own batch, the job is as slow as its slowest rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def replica_throughput(points_per_rank, world_size, step_ms):
+    """Whole-job units per second: every rank evaluates its own batch of
+    points_per_rank in step_ms (the max over ranks)."""
+    return points_per_rank * world_size / (step_ms * 1e-3)
 
 
 def peaks():
@@ -318,10 +337,11 @@ def run_reference(args):
         times.append(time.perf_counter() - t)
     step = sum(times) / len(times)
     v = n / step
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "logL evals/s", "n_gpus": 0,
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "logL evals/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": step * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample_points_per_step": n},
+            "config": {"workload": WORKLOAD, "sample_points_per_step": n,
+                       "where": "the FP64 oracle on rank 0's host cores (the other ranks exit without work)"},
             "cpu_baseline": {"value": v, "unit": "logL evals/s", "cores": os.cpu_count(), "kind": "oracle",
                              "sample": f"{n} points of the {wl.P}-point batch per step"},
             "e2e": {"value": v, "unit": "logL evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -402,6 +422,30 @@ def noise_phase(fg21, stream, reps, n_cells, K=65536, sigma=0.025):
             "ms_per_step": ms, "steps": reps, "draws_per_s": K * n_cells / (ms * 1e-3),
             "q_call_ms": q_ms, "q_at_quantiles_0.005_0.01_0.5": [float(x) for x in q],
             "path": "fg21_noise_loglike (Philox4x32-10 + Box-Muller radius, one block per realisation)"}
+
+
+def occam_phase(fg21, I):
+    """The maximum-likelihood side of the Occam experiment (Sec. 6.1) on workload
+    2's sky and observation: log L_max(N) for N = 1..8 under recursive (nested,
+    warm-started) and linear splits, every candidate evaluated by the library."""
+    import numpy as np
+    from paper_2603_13196_gb300 import occam
+    wl = I.workload(2)
+    sky, obs = wl.sky(), wl.obs()
+    data = fg21.fg21_simulate_data(sky, obs, I.FIDUCIAL_T21, I.NOISE_K, wl.noise())
+    out = {}
+    evals, t0 = 0, time.time()
+    for scheme in ("recursive", "linear"):
+        curve = occam.logl_max_curve(sky, obs, data, scheme, list(range(1, 9)), I.FIDUCIAL_T21, rounds=20,
+                                     batch=4096, seed=3)
+        out[scheme] = [round(c.logL_max, 2) for c in curve]
+        evals += sum(c.n_evals for c in curve)
+    dt = time.time() - t0
+    L = np.array(out["recursive"])
+    return {"workload": f"npix{sky.npix}_F{obs.F}_T{obs.T}_N1-8", "logL_max": out,
+            "nested_monotone": bool(np.all(np.diff(L) >= -1e-2)), "evals": evals, "seconds": round(dt, 3),
+            "evals_per_s": evals / dt,
+            "path": "occam.logl_max_curve: batched cross-entropy search, fg21_loglike_batch_device (fp32_delta)"}
 
 
 def main():
@@ -512,14 +556,9 @@ def main():
     clocks.stop()
 
     # the max over ranks of the per-step device time
-    step_ms, call_ms = gres["ms_per_step"], res["ms_per_step"]
-    if ws > 1:
-        t = torch.tensor([step_ms, call_ms, direct["ms_per_step"]], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        step_ms, call_ms, direct_ms = float(t[0]), float(t[1]), float(t[2])
-    else:
-        direct_ms = direct["ms_per_step"]
-    value = P * ws / (step_ms * 1e-3)
+    step_ms, call_ms, direct_ms = max_over_ranks([gres["ms_per_step"], res["ms_per_step"], direct["ms_per_step"]],
+                                                 dev)
+    value = replica_throughput(P, ws, step_ms)
 
     # end to end through the host-buffer C-ABI call
     e2e_K = max(5, args.steps // 4)
@@ -531,11 +570,7 @@ def main():
     t = time.perf_counter()
     for _ in range(e2e_K):
         out = fg21.fg21_loglike_batch(model, params, args.precision)
-    e2e_s = (time.perf_counter() - t) / e2e_K
-    if ws > 1:
-        tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(tt[0])
+    e2e_s = max_over_ranks([(time.perf_counter() - t) / e2e_K], dev)[0]
     assert np.all(np.isfinite(out))
 
     pk, pk_kind = peaks()
@@ -591,6 +626,8 @@ def main():
         line["alpha_model"] = alpha_phase(fg21, I, sky, obs, args.precision, flush, stream, max(3, args.steps // 4))
     if rank == 0 and not args.no_noise:
         line["noise_q"] = noise_phase(fg21, stream, max(3, args.steps // 20), F * T)
+    if rank == 0 and not args.no_occam:
+        line["occam"] = occam_phase(fg21, I)
     if rank == 0 and not args.no_serve:
         sv = serve_phase(fg21, I)
         line["serve"] = sv
