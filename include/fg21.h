@@ -277,6 +277,23 @@ int fg21_loglike_batch_device_noalloc(fg21_model *m, const double *d_params, int
  * reported an internal failure. */
 int fg21_model_sync_status(fg21_model *m, void *stream, int64_t *invalid_count);
 
+/* The paper has no counterpart to this call: it checks the library's failure
+ * detection without a GPU fault.  Every wait inside the tensor-core
+ * likelihood kernel is bounded (4 s); when a wait runs out the kernel sets a
+ * bit of its device status word, tells its other warps to stop, and returns,
+ * and the next status read reports FG21_E_DEVICE.  This call runs one block of
+ * four warps whose waits use that same primitive on barriers that nothing
+ * ever completes, on `stream`, and waits for it (about 4 s): warp 0 times out
+ * with the kernel's limit, and warps 1-3, whose own limit is twice as long,
+ * must stop through the abort signal.  Outputs: *status_word = the device
+ * status word (bit 0 set when warp 0 timed out); elapsed_s[4] = the seconds
+ * each warp waited, from the GPU's global timer (negative if its barrier
+ * unexpectedly completed).  Returns FG21_E_DEVICE when the status word is
+ * non-zero (the expected outcome, the same code a stalled likelihood launch
+ * gives), FG21_OK when no wait expired, FG21_E_ARG for a NULL output,
+ * FG21_E_CUDA or FG21_E_NOMEM on a CUDA failure.  The CUDA context stays usable. */
+int fg21_selftest_bounded_wait(uint32_t *status_word, double *elapsed_s, void *stream);
+
 /* Measured choice of the work split of requests of P points of model m at
  * `precision` (the number of channels per work item of the batched
  * evaluation of eq. likelihood over eq. fast_forward_model): runs one

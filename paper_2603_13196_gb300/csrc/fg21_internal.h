@@ -162,6 +162,9 @@ struct TcLaunch {
     unsigned *status;
 };
 cudaError_t launch_tc(const TcLaunch &L, int num_sms, cudaStream_t stream);
+// One CTA whose waits expire by design (status + 4 per-warp waiting times).
+cudaError_t launch_wait_selftest(unsigned *status, unsigned long long *elapsed, cudaStream_t stream);
+constexpr int WAIT_SELFTEST_WARPS = 4;
 // Largest multiple of 8 (<= 256 rows of 128 bytes) dividing every tile height.
 int tc_box_rows(const int64_t *tile_rows, int n);
 int tc_map_init();  // resolves cuTensorMapEncodeTiled; FG21_OK or error

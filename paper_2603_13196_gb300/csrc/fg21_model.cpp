@@ -639,6 +639,34 @@ int fg21_model_sync_status(fg21_model *m, void *stream, int64_t *invalid_count) 
     return FG21_OK;
 }
 
+int fg21_selftest_bounded_wait(uint32_t *status_word, double *elapsed_s, void *stream) {
+    if (!status_word || !elapsed_s) return set_error(FG21_E_ARG, "NULL output");
+    cudaStream_t s = (cudaStream_t)stream;
+    void *p = nullptr;
+    if (cudaMalloc(&p, 64) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(FG21_E_NOMEM, "cudaMalloc of 64 bytes failed");
+    }
+    // [0, 4): status word; [32, 64): one waiting time per warp
+    unsigned *d_status = (unsigned *)p;
+    unsigned long long *d_elapsed = (unsigned long long *)((char *)p + 32);
+    unsigned char h[64];
+    cudaError_t e = cudaMemsetAsync(p, 0, 64, s);
+    if (e == cudaSuccess) e = launch_wait_selftest(d_status, d_elapsed, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, p, 64, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(p);
+    if (e != cudaSuccess) return cuda_error(e, "bounded-wait self-test");
+    std::memcpy(status_word, h, sizeof(uint32_t));
+    for (int w = 0; w < WAIT_SELFTEST_WARPS; ++w) {
+        unsigned long long ns;
+        std::memcpy(&ns, h + 32 + 8 * w, sizeof ns);
+        elapsed_s[w] = ns == ~0ull ? -1.0 : 1e-9 * (double)ns;
+    }
+    if (*status_word) return set_error(FG21_E_DEVICE, "self-test kernel reported status 0x%x", *status_word);
+    return FG21_OK;
+}
+
 int fg21_model_timing(fg21_model *m, int enable) {
     if (!m) return set_error(FG21_E_ARG, "NULL model");
     std::lock_guard<std::mutex> lk(m->mu);

@@ -123,13 +123,13 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
 }
 // Bounded wait: true when the phase completed; false on timeout or abort.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, Barriers *S, unsigned *status,
-                                          unsigned code) {
+                                          unsigned code, uint64_t limit_ns = WAIT_LIMIT_NS) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     while (true) {
         if (mbar_try_wait(bar, parity)) return true;
         if (S->abort_flag) return false;
-        if (globaltimer() - t0 > WAIT_LIMIT_NS) {
+        if (globaltimer() - t0 > limit_ns) {
             atomicOr(status, code);
             S->abort_flag = 1;
             return false;
@@ -882,7 +882,35 @@ cudaError_t launch_common(const ReqDesc *d_reqs, int n_reqs, int64_t n_items, in
     return bf16 ? launch_kp<64, true>(map, prm, grid, sm, stream) : launch_kp<64, false>(map, prm, grid, sm, stream);
 }
 
+// Self-test of the bounded waits, on barriers that nothing ever arrives on.
+// Warp 0 waits with the kernel's limit: it gives up first, sets
+// STATUS_TIMEOUT_TMA and raises the abort flag.  Warps 1-3 wait with twice
+// that limit and must come back through the abort flag, as the other roles of
+// a stalled likelihood launch do, without a status bit of their own.
+// elapsed[w] = nanoseconds warp w waited (all ones if its barrier completed).
+__global__ void __launch_bounds__(128) wait_selftest_kernel(unsigned *status, unsigned long long *elapsed) {
+    __shared__ Barriers S;
+    if (threadIdx.x == 0) {
+        mbar_init(&S.full[0], 1);
+        mbar_init(&S.full[1], 1);
+        S.abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5;
+    const uint64_t t0 = globaltimer();
+    const bool ok = warp == 0 ? mbar_wait(&S.full[0], 0, &S, status, STATUS_TIMEOUT_TMA)
+                              : mbar_wait(&S.full[1], 0, &S, status, STATUS_TIMEOUT_GEN, 2 * WAIT_LIMIT_NS);
+    const uint64_t dt = globaltimer() - t0;
+    if ((threadIdx.x & 31) == 0) elapsed[warp] = ok ? ~0ull : dt;
+}
+
 }  // namespace
+
+cudaError_t launch_wait_selftest(unsigned *status, unsigned long long *elapsed, cudaStream_t stream) {
+    wait_selftest_kernel<<<1, 128, 0, stream>>>(status, elapsed);
+    return cudaGetLastError();
+}
 
 int tc_map_init() {
     std::call_once(g_encode_once, [] {

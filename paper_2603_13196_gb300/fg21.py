@@ -89,6 +89,7 @@ _SIGS = {
     "fg21_loglike_batch_device": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int, _P]),
     "fg21_loglike_batch_device_noalloc": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int, _P]),
     "fg21_model_sync_status": (C.c_int, [_P, _P, _P]),
+    "fg21_selftest_bounded_wait": (C.c_int, [_P, _P, _P]),
     "fg21_autotune": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int, _P, _P, _P]),
     "fg21_model_eval": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int, _P]),
     "fg21_model_timing": (C.c_int, [_P, C.c_int]),
@@ -337,6 +338,18 @@ def fg21_model_sync_status(m: Model, stream: int = 0) -> int:
     n = C.c_int64()
     _check(lib().fg21_model_sync_status(m.handle, stream or None, C.byref(n)), "fg21_model_sync_status")
     return n.value
+
+
+def fg21_selftest_bounded_wait(stream: int = 0):
+    """-> (return code, device status word, seconds each of the 4 warps waited).
+    The expected outcome is FG21_E_DEVICE with bit 0 set: the code is returned,
+    not raised."""
+    st = C.c_uint32(0)
+    el = (C.c_double * 4)()
+    rc = lib().fg21_selftest_bounded_wait(C.byref(st), el, stream or None)
+    if rc not in (FG21_OK, FG21_E_DEVICE):
+        _check(rc, "fg21_selftest_bounded_wait")
+    return rc, st.value, list(el)
 
 
 def fg21_model_timing(m: Model, enable: bool = True):
