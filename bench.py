@@ -208,28 +208,19 @@ def serve_phase(fg21, I, seconds=3.0, n_runs=64):
     import queue
     import numpy as np
 
-    g = I.rng(I.BASE_SEED + 5, I.SUB_ARRIVALS)
-    Ns, Ts = [5, 9, 14, 20, 30], [1, 10, 50]
+    mix, reqs = I.serving_mix(n_runs)
     srv = fg21.Server(mem_budget_bytes=60 << 30, max_batch_points=65536, max_wait_us=200, max_inflight=2)
     runs, models = [], []
     t0 = time.time()
-    for k in range(n_runs):
-        N, T = Ns[k % 5], Ts[(k // 5) % 3]
-        window = 0.0 if T == 1 else float(g.choice([2.0, 6.0, 12.0]))
-        sky = I.make_sky(3072, I.BASE_SEED + 500 + k)
-        obs = I.make_obs(151, T, window, lst0_h=float(g.uniform(0, 24)))
-        m = fg21.fg21_build_regions(sky, obs, N, "recursive")
-        fg21.fg21_model_set_data(m, fg21.fg21_simulate_data(sky, obs, I.FIDUCIAL_T21, I.NOISE_K,
-                                                            I.noise_draws(151, T, k)))
+    for run in mix:
+        sky, obs = run.sky(), run.obs()
+        m = fg21.fg21_build_regions(sky, obs, run.N, "recursive")
+        fg21.fg21_model_set_data(m, fg21.fg21_simulate_data(sky, obs, I.FIDUCIAL_T21, I.NOISE_K, run.noise()))
         rid, _ = fg21.fg21_serve_register_run(srv, m)
-        runs.append((rid, N, T))
+        runs.append((rid, run.N, run.T))
         models.append(m)
     build_s = time.time() - t0
-    pool = []
-    for j in range(256):
-        k = int(g.integers(0, n_runs))
-        P = int(g.integers(128, 4097))
-        pool.append((runs[k][0], I.prior_draws(P, runs[k][1], seed=j, extra=k), runs[k][1] * 151 * runs[k][2]))
+    pool = [(runs[k][0], p, runs[k][1] * 151 * runs[k][2]) for k, p in reqs]
 
     def closed(dur):
         stop = time.time() + dur

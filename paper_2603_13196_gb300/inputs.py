@@ -254,3 +254,48 @@ def uneven_batch(n_models: int = 32, seed: int = BASE_SEED + 4, npix: int = 3072
         out.append(Workload(f"m{m}_N{N}_T{T}_P{P}", npix, N, F, T, window, P,
                             seed=seed * 100 + m, lst0_h=lst0))
     return out
+
+
+@dataclasses.dataclass
+class ServingRun:
+    """One nested-sampling run of the serving workload: its own 3072-pixel sky,
+    F = 151 channels, N regions, T LST bins over its own window."""
+    N: int
+    T: int
+    window_h: float
+    lst0_h: float
+    sky_seed: int
+    noise_seed: int
+    npix: int = 3072
+    F: int = 151
+
+    def sky(self) -> Sky:
+        return make_sky(self.npix, self.sky_seed)
+
+    def obs(self) -> Obs:
+        return make_obs(self.F, self.T, self.window_h, lst0_h=self.lst0_h)
+
+    def noise(self) -> np.ndarray:
+        return noise_draws(self.F, self.T, self.noise_seed)
+
+
+def serving_mix(n_runs: int = 64, n_requests: int = 256):
+    """Workload 5: n_runs runs (N cycling through 5, 9, 14, 20, 30; T through 1,
+    10, 50, each with its own window and LST start) and a pool of n_requests
+    requests (run index, prior draws of 128..4096 points) to uniformly chosen
+    runs.  -> (runs, [(run index, params)])."""
+    g = rng(BASE_SEED + 5, SUB_ARRIVALS)
+    Ns, Ts = [5, 9, 14, 20, 30], [1, 10, 50]
+    runs = []
+    for k in range(n_runs):
+        N, T = Ns[k % 5], Ts[(k // 5) % 3]
+        window = 0.0 if T == 1 else float(g.choice([2.0, 6.0, 12.0]))
+        lst0 = float(g.uniform(0, 24))
+        runs.append(ServingRun(N, T, window, lst0, BASE_SEED + 500 + k, k))
+    reqs = []
+    for j in range(n_requests):
+        k = int(g.integers(0, n_runs))
+        P = int(g.integers(128, 4097))
+        reqs.append((k, prior_draws(P, runs[k].N, seed=j, extra=k)))
+    return runs, reqs
+
