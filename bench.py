@@ -194,9 +194,29 @@ def cpu_baseline(sky, obs, N, params, seconds):
     t = time.perf_counter()
     O.loglike(m.A, m.B, data, obs, params[:n])
     dt = time.perf_counter() - t
-    return {"value": n / dt, "unit": "logL evals/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{n} of the {params.shape[0]} points of one batch (same workload), FP64, "
-                      f"OpenMP over points, {dt:.1f} s"}, m, data
+    out = {"value": n / dt, "unit": "logL evals/s", "cores": os.cpu_count(), "kind": "oracle",
+           "sample": f"{n} of the {params.shape[0]} points of one batch (same workload), FP64, "
+                     f"OpenMP over points, {dt:.1f} s"}
+    # the same oracle on one thread (OpenMP's thread count set through its runtime)
+    try:
+        import ctypes
+        gomp = ctypes.CDLL("libgomp.so.1")
+        nthreads = gomp.omp_get_max_threads()
+        gomp.omp_set_num_threads(1)
+        try:
+            t = time.perf_counter()
+            O.loglike(m.A, m.B, data, obs, params[:4])
+            per1 = (time.perf_counter() - t) / 4
+            n1 = int(max(4, min(n, 0.15 * seconds / max(per1, 1e-9))))
+            t = time.perf_counter()
+            O.loglike(m.A, m.B, data, obs, params[:n1])
+            dt1 = time.perf_counter() - t
+        finally:
+            gomp.omp_set_num_threads(nthreads)
+        out["single_thread"] = {"value": n1 / dt1, "cores": 1, "sample": f"{n1} points, {dt1:.1f} s"}
+    except OSError:
+        pass
+    return out, m, data
 
 
 def serve_phase(fg21, I, seconds=3.0, n_runs=64):
