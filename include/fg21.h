@@ -230,6 +230,9 @@ int fg21_simulate_data(const fg21_sky *sky, const fg21_obs *obs, const double *t
  *   logL[p]  = -1/2 sum_{f,t} [ ln(2 pi sigma_n^2) + (D[f,t] - M[p,f,t])^2 / sigma_n^2 ]
  * params [P][N+4] and logL [P] are HOST buffers; the call copies params to the
  * device, evaluates on `stream`, copies logL back and returns when done.
+ * Buffers in page-locked memory (cudaMallocHost, cudaHostAlloc,
+ * cudaHostRegister) are copied by DMA directly; pageable ones pass through a
+ * page-locked staging buffer the model keeps.
  * precision: FG21_PREC_*.  Points with a non-finite parameter, sigma_n <= 0 or
  * sigma21 == 0 get logL = -inf and are counted (fg21_last_invalid_count); the
  * call still succeeds.  Prior bounds are not enforced.  P = 0 is a no-op.

@@ -38,6 +38,8 @@ void graph_free(fg21_graph *g) {
 
 }  // namespace
 
+unsigned *fg21::graph_status(fg21_graph *g) { return g->ws.d_status; }
+
 extern "C" {
 
 int fg21_graph_create_multi(fg21_model *const *models, const double *const *d_params, const int64_t *P,

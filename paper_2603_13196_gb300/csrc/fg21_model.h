@@ -82,6 +82,11 @@ struct fg21_model {
     size_t resident_bytes = 0;      // A, B, data, tables (not the workspace)
     char *io_d = nullptr, *io_h = nullptr;   // params/logL staging of the host-buffer calls
     size_t io_cap = 0;
+    // the host-buffer call's evaluation captured as a CUDA graph on io_d, replayed
+    // while the point count, precision, staging buffers and work split stay the same
+    fg21_graph *host_graph = nullptr;
+    int64_t hg_P = 0;
+    int hg_prec = -1, hg_cpg = -1;
     fg21::Workspace ws;
     std::map<std::pair<int, int>, int> tuned_cpg;   // (precision, 128-point tiles) -> channels per group
     std::mutex tune_mu;                              // guards tuned_cpg
@@ -93,4 +98,6 @@ int model_upload(fg21_model *m);
 // A request descriptor of model m for `precision` (carrying the autotuned work
 // split for its size, if any).
 ReqDesc model_request(fg21_model *m, const double *d_params, int64_t P, double *d_logL, int precision);
+// The device status word (and invalid count) of a graph's workspace.
+unsigned *graph_status(fg21_graph *g);
 }  // namespace fg21

@@ -312,10 +312,16 @@ def fg21_model_info(m: Model) -> dict:
     return dict(N=N.value, F=F.value, T=T.value, n_empty=ne.value, device_bytes=nb.value)
 
 
-def fg21_loglike_batch(m: Model, params: np.ndarray, precision="fp16x3", stream: int = 0) -> np.ndarray:
+def fg21_loglike_batch(m: Model, params: np.ndarray, precision="fp16x3", stream: int = 0,
+                       out: Optional[np.ndarray] = None) -> np.ndarray:
+    """logL of every row of params (host arrays).  `out` (float64 [P], contiguous)
+    receives the result when given; page-locked params / out are copied by DMA
+    directly, without the library's staging copy."""
     p = _f64(params)
     assert p.ndim == 2 and p.shape[1] == m.n_params, p.shape
-    out = np.empty(p.shape[0])
+    if out is None:
+        out = np.empty(p.shape[0])
+    assert out.dtype == np.float64 and out.shape == (p.shape[0],) and out.flags.c_contiguous
     _check(lib().fg21_loglike_batch(m.handle, _ptr(p), p.shape[0], _ptr(out), _prec(precision), stream or None),
            "fg21_loglike_batch")
     return out

@@ -70,3 +70,52 @@ def test_graph_multi_matches_multi_and_oracle(fg21lib):
         want, _ = cases.expected(om, obs, data, p)
         assert np.all(np.abs(got - want) <= cases.logl_tolerance("fp16x3", om, obs, data, p)), wl.name
     g.close()
+
+
+@pytest.mark.parametrize("prec", ["fp16x3", "fp32_delta"])
+def test_host_call_pinned_buffers_and_its_cached_graph(fg21lib, prec):
+    """The host-buffer call replays a graph it keeps per (size, precision, work
+    split): page-locked and pageable buffers give the same logL, which equals the
+    direct device call bit for bit; a new size, a new tuned split and invalid
+    points all go through it correctly."""
+    import torch
+    sky, obs, m, data = cases.small_case(npix=2048, N=7, F=41, T=9, window=4.0)
+    model = fg21lib.fg21_build_regions(sky, obs, 7)
+    fg21lib.fg21_model_set_data(model, data)
+    stream = torch.cuda.current_stream().cuda_stream
+
+    def device_call(params):
+        d_p = torch.from_numpy(params).cuda()
+        d_l = torch.empty(params.shape[0], dtype=torch.float64, device="cuda")
+        fg21lib.fg21_loglike_batch_device(model, d_p.data_ptr(), params.shape[0], d_l.data_ptr(), prec, stream)
+        assert fg21lib.fg21_model_sync_status(model, stream) == 0
+        return d_l.cpu().numpy()
+
+    p1, p2 = I.prior_draws(300, 7, seed=3), I.prior_draws(129, 7, seed=4)
+    a = fg21lib.fg21_loglike_batch(model, p1, prec)              # pageable: staged; captures the graph
+    hp = torch.empty(p1.shape, dtype=torch.float64, pin_memory=True).numpy()
+    hp[:] = p1
+    ho = torch.empty(p1.shape[0], dtype=torch.float64, pin_memory=True).numpy()
+    b = fg21lib.fg21_loglike_batch(model, hp, prec, out=ho)     # page-locked: direct DMA, replay
+    assert b is ho and np.array_equal(a, b)
+    assert np.array_equal(a, device_call(p1))
+    c = fg21lib.fg21_loglike_batch(model, p2, prec)              # another size: a new graph
+    assert np.array_equal(c, device_call(p2))
+    assert np.array_equal(fg21lib.fg21_loglike_batch(model, p1, prec), a)
+    want, _ = cases.expected(m, obs, data, p1)
+    assert np.all(np.abs(a - want) <= cases.logl_tolerance(prec, m, obs, data, p1))
+    # a tuned work split for this size replaces the kept graph
+    d_p = torch.from_numpy(p1).cuda()
+    d_l = torch.empty(300, dtype=torch.float64, device="cuda")
+    fg21lib.fg21_autotune(model, d_p.data_ptr(), 300, d_l.data_ptr(), prec, stream)
+    t = fg21lib.fg21_loglike_batch(model, p1, prec)
+    assert np.array_equal(t, device_call(p1))
+    assert np.all(np.abs(t - want) <= cases.logl_tolerance(prec, m, obs, data, p1))
+    # invalid points: -inf and counted through the replayed graph
+    p3 = p1.copy()
+    p3[5, -1] = -1.0
+    p3[7, 0] = np.nan
+    r = fg21lib.fg21_loglike_batch(model, p3, prec)
+    assert np.isneginf(r[5]) and np.isneginf(r[7]) and np.all(np.isfinite(np.delete(r, [5, 7])))
+    assert fg21lib.fg21_last_invalid_count() == 2
+    model.close()
