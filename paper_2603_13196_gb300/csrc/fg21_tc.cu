@@ -93,6 +93,15 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
+// One arrival for the whole (converged) warp, made by an elected lane under a
+// predicate rather than a branch.
+__device__ __forceinline__ void mbar_arrive_warp(uint64_t *bar) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "elect.sync _|p, 0xffffffff;\n\t"
+        "@p mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];\n\t}" ::"r"(smem_u32(bar))
+        : "memory");
+}
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                  "r"(bytes)
@@ -502,7 +511,7 @@ __device__ __forceinline__ bool gen_item(const Params &prm, Barriers *S, Ring &r
             tmem_st_wait();
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&S->full[rg.slot]);
+            mbar_arrive_warp(&S->full[rg.slot]);
             rg.next(prm.ring);
         }
     }
@@ -588,7 +597,7 @@ __device__ __forceinline__ bool epi_item(const Params &prm, Barriers *S, Ring &r
             }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&S->full[rg.slot]);      // accumulator free for stage + ring
+            mbar_arrive_warp(&S->full[rg.slot]);                 // accumulator free for stage + ring
             rg.next(prm.ring);
             qf += q * unscale * unscale;
         }
