@@ -13,13 +13,17 @@ contraction, trough, residual and square (a2-a5), per-point reduction and logL
                captured once (fg21_graph_launch; CUDA events on the launch
                stream, L2 flushed by a 256 MiB write between timed steps)
   direct_call  the same step through fg21_loglike_batch_device every time
-  e2e          the same through the host-buffer C-ABI call (params H2D and
-               logL D2H inside the timed region)
+  e2e          the same through the host-buffer C-ABI call on page-locked
+               buffers (params H2D and logL D2H inside the timed region)
   fp32_direct  the plain FP32 SIMT kernel on the same device and protocol
   roofline     dominant kernel (tcgen05 likelihood kernel): algorithmic flops
                (2 N F T per point) / its mean launch time, against the measured
                dense 16-bit tensor peak
-  cpu_baseline the FP64 oracle on the host cores, on a bounded sample
+  cpu_baseline the FP64 oracle on the host cores (all of them, and one), on a
+               bounded sample
+  alpha_model, noise_q, occam, small_batch, serve
+               the amplitude-mask model, the noise-only likelihood workload,
+               log L_max(N), the 64-point latency case and the serving mix
 
 `--impl reference` times the oracle alone (the reference arm of this build).
 Multi-GPU: one process per GPU under torchrun, each rank an independent
@@ -58,6 +62,7 @@ def parse():
     ap.add_argument("--no-alpha", action="store_true", help="skip the amplitude-mask model line")
     ap.add_argument("--no-noise", action="store_true", help="skip the accuracy-criterion (L_noise) line")
     ap.add_argument("--no-occam", action="store_true", help="skip the log L_max(N) line")
+    ap.add_argument("--no-small", action="store_true", help="skip the 64-point latency line")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample budget")
     return ap.parse_args()
 
@@ -435,6 +440,58 @@ def noise_phase(fg21, stream, reps, n_cells, K=65536, sigma=0.025):
             "path": "fg21_noise_loglike (Philox4x32-10 + Box-Muller radius, one block per realisation)"}
 
 
+def small_batch_phase(fg21, I, stream, K=200):
+    """The launch-latency-bound end of the workloads: 64 prior draws at N = 3,
+    F = 151, T = 1 (3072-pixel sky, hierarchical regions).  Median time per
+    evaluation of the direct device call (plan, descriptor upload, four launches),
+    of the graph replay, and of the host-buffer call on page-locked buffers."""
+    import numpy as np
+    import torch
+    wl = I.workload(1)
+    sky, obs = wl.sky(), wl.obs()
+    m = fg21.fg21_build_regions(sky, obs, wl.N, wl.scheme, wl.weighting)
+    fg21.fg21_model_set_data(m, fg21.fg21_simulate_data(sky, obs, I.FIDUCIAL_T21, I.NOISE_K, wl.noise()))
+    params = wl.params()
+    P = params.shape[0]
+    d_p = torch.from_numpy(params).cuda()
+    d_l = torch.empty(P, dtype=torch.float64, device="cuda")
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+
+    def device_times(run):
+        for _ in range(10):
+            run()
+        torch.cuda.synchronize()
+        for a, b in evs:
+            a.record()
+            run()
+            b.record()
+        torch.cuda.synchronize()
+        return float(np.median([a.elapsed_time(b) for a, b in evs])) * 1e3
+
+    direct_us = device_times(lambda: fg21.fg21_loglike_batch_device(m, d_p.data_ptr(), P, d_l.data_ptr(), "fp16x3",
+                                                                    stream))
+    g = fg21.fg21_graph_create(m, d_p.data_ptr(), P, d_l.data_ptr(), "fp16x3")
+    graph_us = device_times(lambda: g.launch(stream))
+    assert g.sync_status(stream) == 0
+    g.close()
+    h_p = torch.empty(params.shape, dtype=torch.float64, pin_memory=True).numpy()
+    h_p[:] = params
+    h_o = torch.empty(P, dtype=torch.float64, pin_memory=True).numpy()
+    for _ in range(10):
+        fg21.fg21_loglike_batch(m, h_p, "fp16x3", out=h_o)
+    ts = []
+    for _ in range(K):
+        t = time.perf_counter()
+        fg21.fg21_loglike_batch(m, h_p, "fp16x3", out=h_o)
+        ts.append(time.perf_counter() - t)
+    assert np.all(np.isfinite(h_o))
+    m.close()
+    return {"workload": wl.name, "direct_call_us": direct_us, "graph_replay_us": graph_us,
+            "host_call_us": float(np.median(ts)) * 1e6,
+            "what": "median per evaluation of 64 points: device call, graph replay (CUDA events), and the "
+                    "host-buffer call on page-locked buffers (wall clock, copies and synchronisation included)"}
+
+
 def occam_phase(fg21, I):
     """The maximum-likelihood side of the Occam experiment (Sec. 6.1) on workload
     2's sky and observation: log L_max(N) for N = 1..8 under recursive (nested,
@@ -645,6 +702,8 @@ def main():
         line["noise_q"] = noise_phase(fg21, stream, max(3, args.steps // 20), F * T)
     if rank == 0 and not args.no_occam:
         line["occam"] = occam_phase(fg21, I)
+    if rank == 0 and not args.no_small:
+        line["small_batch"] = small_batch_phase(fg21, I, stream)
     if rank == 0 and not args.no_serve:
         sv = serve_phase(fg21, I)
         line["serve"] = sv
