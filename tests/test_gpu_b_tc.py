@@ -192,3 +192,50 @@ def test_workload3_benchmark_configuration_sampled(fg21lib):
            max_err_over_tol=np.max(err / tol))
     assert np.all(err <= tol), cases.fmt_err("w3", got[idx], want, tol)
     assert np.all(np.isfinite(got))
+
+
+# the largest shapes each path takes: N = 62 fills K = 64 on the tensor path,
+# T = 192 is one full-width t-chunk (the ring drops to its minimum of two stage
+# slots), T = 193 splits into two chunks; N = 126 is the SIMT and build limit
+MAX_SHAPES = [
+    # (npix, N, F, T, P, precisions)
+    (4096, 62, 7, 192, 300, ("fp16x3", "bf16x3")),
+    (4096, 62, 5, 193, 131, ("fp16x3",)),
+    (4096, 126, 5, 3, 200, ("fp32_delta", "fp32_direct")),
+]
+
+
+@pytest.mark.parametrize("shape", MAX_SHAPES, ids=lambda s: "N%d_F%d_T%d_P%d" % s[1:5])
+def test_maximum_shapes(fg21lib, shape):
+    npix, N, F, T, P, precs = shape
+    sky, obs, m, data = cases.small_case(npix=npix, N=N, F=F, T=T, window=12.0)
+    model = fg21lib.fg21_build_regions(sky, obs, N)
+    assert np.array_equal(model.labels, m.labels)
+    fg21lib.fg21_model_set_data(model, data)
+    params = cases.I.prior_draws(P, N, seed=N + T)
+    want, dterm = cases.expected(m, obs, data, params)
+    for prec in precs:
+        got = fg21lib.fg21_loglike_batch(model, params, prec)
+        tol = cases.logl_tolerance(prec, m, obs, data, params)
+        report(f"max_shape_{prec}_N{N}_T{T}", max_err_over_tol=np.max(np.abs(got - want) / tol))
+        assert np.all(np.abs(got - want) <= tol), cases.fmt_err(prec, got, want, tol)
+    model.close()
+
+
+def test_limits_refused(fg21lib):
+    """One past each limit is refused with its documented code, not evaluated."""
+    sky, obs, m, data = cases.small_case(npix=2048, N=63, F=5, T=2)
+    model = fg21lib.fg21_build_regions(sky, obs, 63)
+    fg21lib.fg21_model_set_data(model, data)
+    params = cases.I.prior_draws(10, 63, seed=2)
+    with pytest.raises(fg21lib.Fg21Error) as e:
+        fg21lib.fg21_loglike_batch(model, params, "fp16x3")
+    assert e.value.code == fg21lib.FG21_E_RANGE
+    # the SIMT forms take N = 63
+    got = fg21lib.fg21_loglike_batch(model, params, "fp32_delta")
+    want, _ = cases.expected(m, obs, data, params)
+    assert np.all(np.abs(got - want) <= cases.logl_tolerance("fp32_delta", m, obs, data, params))
+    model.close()
+    with pytest.raises(fg21lib.Fg21Error) as e:
+        fg21lib.fg21_build_regions(sky, obs, 127)
+    assert e.value.code == fg21lib.FG21_E_ARG
