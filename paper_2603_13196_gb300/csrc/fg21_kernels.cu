@@ -26,6 +26,7 @@ namespace {
 
 constexpr int PREP_THREADS = 256;
 constexpr int REDUCE_THREADS = 64;
+constexpr int REDUCE_SERIAL_MAX = 32;       // longest partial row summed by one thread
 
 // A point is valid when all its parameters are finite, sigma_n > 0,
 // sigma21 != 0 and every amplitude scale factor alpha_i > 0 (a gain).  Tested
@@ -716,23 +717,50 @@ __device__ __forceinline__ void two_sum_acc(float &s, float &c, float x) {
     c += (s - (t - z)) + (x - z);
     s = t;
 }
+// Each request's rows are summed in a form fixed by the row length alone, so a
+// request's logL does not depend on what it is batched with:
+//  - rows of at most REDUCE_SERIAL_MAX partials (the usual case): one thread per
+//    point sums its row in ascending order (double-float);
+//  - longer rows (one channel per group at small P): one warp per point, lane l
+//    summing partials l, l+32, ... in ascending order, the lanes' sums combined
+//    in a fixed butterfly.
+// WARP selects the form a launch serves; requests of the other form are skipped.
+template <bool WARP>
 __global__ void __launch_bounds__(REDUCE_THREADS) reduce_kernel(const ReqDesc *__restrict__ reqs, int n_reqs) {
-    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t gid = WARP ? tid >> 5 : tid;
+    const int lane = WARP ? (int)(threadIdx.x & 31) : 0;
     const ReqDesc &r = reqs[find_req_by_point(reqs, n_reqs, gid)];
     const int64_t p = gid - r.pt_begin;
-    if (p < 0 || p >= r.P) return;
+    if (p < 0 || p >= r.P) return;       // uniform over a warp in WARP mode
+    if ((r.n_part > REDUCE_SERIAL_MAX) != WARP) return;
     if (!r.pvalid[p]) {      // the statistics pass tested the point (point_valid)
-        r.logL[p] = -INFINITY;
-        atomicAdd(r.invalid, 1ull);
+        if (lane == 0) {
+            r.logL[p] = -INFINITY;
+            atomicAdd(r.invalid, 1ull);
+        }
         return;
     }
     float sh = 0.0f, sl = 0.0f;
     const float2 *__restrict__ part = r.partials + (size_t)p * r.n_part;
+    if (WARP) {
+        for (int g = lane; g < r.n_part; g += 32) {
+            const float2 v = part[g];
+            two_sum_acc(sh, sl, v.x);
+            two_sum_acc(sh, sl, v.y);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, sh, o), ol = __shfl_xor_sync(0xffffffffu, sl, o);
+            df_add(sh, sl, oh, ol);
+        }
+        if (lane != 0) return;
+    } else {
 #pragma unroll 4
-    for (int g = 0; g < r.n_part; ++g) {
-        const float2 v = part[g];
-        two_sum_acc(sh, sl, v.x);
-        two_sum_acc(sh, sl, v.y);
+        for (int g = 0; g < r.n_part; ++g) {
+            const float2 v = part[g];
+            two_sum_acc(sh, sl, v.x);
+            two_sum_acc(sh, sl, v.y);
+        }
     }
     const double chi2 = (double)sh + (double)sl;
     if (r.pnorm) {           // sigma_n terms from prep (tensor path)
@@ -883,8 +911,15 @@ cudaError_t launch_reduce(const ReqDesc *h_reqs, const ReqDesc *d_reqs, int n_re
     int64_t pts = 0;
     for (int k = 0; k < n_reqs; ++k) pts += h_reqs[k].P;
     if (pts == 0) return cudaSuccess;
+    bool serial = false, warp = false;
+    for (int k = 0; k < n_reqs; ++k) {
+        if (h_reqs[k].P == 0) continue;
+        (h_reqs[k].n_part > REDUCE_SERIAL_MAX ? warp : serial) = true;
+    }
     const int th = REDUCE_THREADS;
-    reduce_kernel<<<(unsigned)((pts + th - 1) / th), th, 0, stream>>>(d_reqs, n_reqs);
+    if (serial) reduce_kernel<false><<<(unsigned)((pts + th - 1) / th), th, 0, stream>>>(d_reqs, n_reqs);
+    const int64_t per_block = th / 32;
+    if (warp) reduce_kernel<true><<<(unsigned)((pts + per_block - 1) / per_block), th, 0, stream>>>(d_reqs, n_reqs);
     return cudaGetLastError();
 }
 
