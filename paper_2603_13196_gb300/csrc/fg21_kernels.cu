@@ -25,6 +25,12 @@ namespace fg21 {
 namespace {
 
 constexpr int PREP_THREADS = 256;
+constexpr int FIN_GROUP_SCRATCH = 512;   // floats of per-group finalise results
+// Head of the prep kernels' shared memory, in doubles: bbar [NPF] FP64, the
+// finalise scratch [2 NPF + 2 + 16] FP32 and the group results [FIN_GROUP_SCRATCH] FP32.
+__host__ __device__ inline int prep_head_doubles(int NP) {
+    return NP + (2 * NP + 2 + 16 + 1) / 2 + FIN_GROUP_SCRATCH / 2;
+}
 constexpr int REDUCE_THREADS = 64;
 constexpr int REDUCE_SERIAL_MAX = 32;       // longest partial row summed by one thread
 
@@ -146,29 +152,43 @@ __host__ __device__ __forceinline__ int padded_row(int R) { return R | 1; }
 // max_i |beta - bbar_i| * max_f |L_f| + max_i |ln(alpha / abar_i)| (it sets the
 // weight series and the power-of-two scale sW of the weight operand), the
 // valid count and max |A21|.
-// Thread j combines field j of every stat block in block order (one round of
-// independent loads per 16 blocks), so every block computes the same values
-// bit for bit; bbar goes to shared memory (`bbar_sh`), and block 0 of the
+// The fields are minima, maxima and an exact integer count, so the order in
+// which the stat blocks combine does not change a bit: G threads share each
+// field (thread (g, j) takes blocks g, g+G, ..., sixteen independent loads per
+// round), then thread j combines the G results.  Every block computes the same
+// values bit for bit; bbar goes to shared memory (`bbar_sh`), and block 0 of the
 // request publishes the results for the later kernels.
 struct Fin {
     float nv, ma, x;
     int sW;
 };
-__device__ Fin prep_finalize(const ReqDesc &r, float *sh /* [2 NPF + 2 + 2 nwarps] */, double *bbar_sh, bool publish) {
+__device__ Fin prep_finalize(const ReqDesc &r, float *sh /* [2 NPF + 2 + 2 nwarps] */,
+                             float *gpart /* [FIN_GROUP_SCRATCH] */, double *bbar_sh, bool publish) {
     const int N = r.NPF, Nb = r.Nb, nb = r.n_stat_blocks, W = 2 * N + 2;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int j = threadIdx.x; j < W; j += blockDim.x) {
-        const int kind = j < 2 * N ? 1 + (j & 1) : (j == 2 * N ? 0 : 2);   // 0 sum, 1 min, 2 max
+    const int G = max(1, min((int)blockDim.x / W, FIN_GROUP_SCRATCH / W));
+    for (int idx = threadIdx.x; idx < G * W; idx += blockDim.x) {
+        const int g = idx / W, j = idx - g * W;
+        const int kind = j < 2 * N ? 1 + (j & 1) : (j == 2 * N ? 0 : 2);   // 0 count, 1 min, 2 max
         const float *q = r.stat_part + j;
         float v = kind == 0 ? 0.0f : kind == 1 ? INFINITY : -INFINITY;
-        // 32 independent loads in flight per round, combined in block order
-        for (int b0 = 0; b0 < nb; b0 += 16) {
+        for (int b0 = g; b0 < nb; b0 += 16 * G) {
             float x[16];
 #pragma unroll
-            for (int u = 0; u < 16; ++u) x[u] = b0 + u < nb ? __ldg(q + (size_t)(b0 + u) * W) : 0.0f;
+            for (int u = 0; u < 16; ++u) x[u] = b0 + u * G < nb ? __ldg(q + (size_t)(b0 + u * G) * W) : 0.0f;
 #pragma unroll
             for (int u = 0; u < 16; ++u)
-                if (b0 + u < nb) v = kind == 0 ? v + x[u] : kind == 1 ? fminf(v, x[u]) : fmaxf(v, x[u]);
+                if (b0 + u * G < nb) v = kind == 0 ? v + x[u] : kind == 1 ? fminf(v, x[u]) : fmaxf(v, x[u]);
+        }
+        gpart[idx] = v;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < W; j += blockDim.x) {
+        const int kind = j < 2 * N ? 1 + (j & 1) : (j == 2 * N ? 0 : 2);
+        float v = gpart[j];
+        for (int g = 1; g < G; ++g) {
+            const float x = gpart[g * W + j];
+            v = kind == 0 ? v + x : kind == 1 ? fminf(v, x) : fmaxf(v, x);
         }
         sh[j] = v;
     }
@@ -296,27 +316,40 @@ __global__ void __launch_bounds__(STAT_BLOCK) prep_stats_kernel(const ReqDesc *_
 // and 1/(2 sigma21^2); with amplitude regions, rows Kp+4.. hold
 // ln(alpha_{p,i} / abar_i) of each component's amplitude i, two components per
 // 8-byte pair ([Kp/2][128][2]) so a generator thread loads a pair at once.
-// `th` is this thread's parameter row (staged in shared memory).
+// Two threads per point (`half` 0 and 1 of the block): the deviation rows
+// alternate between them; half 0 also writes the trough rows and the sigma_n
+// terms, half 1 the amplitude rows.  `th` is the point's parameter row (staged
+// in shared memory).
 __device__ __forceinline__ void prep_points(const ReqDesc &r, int tile, const double *bbar, const double *th) {
-    const int64_t p = (int64_t)tile * TILE_M + threadIdx.x;
-    if (threadIdx.x >= TILE_M) return;
+    const int pidx = threadIdx.x % TILE_M, half = threadIdx.x / TILE_M;
+    if (half > 1) return;
+    const int64_t p = (int64_t)tile * TILE_M + pidx;
     const int N = r.N, Nb = r.Nb, NP = r.NPF, Kp = r.Kp;
-    float *out = r.pts32 + (size_t)tile * r.pts_rows * TILE_M + threadIdx.x;
+    float *out = r.pts32 + (size_t)tile * r.pts_rows * TILE_M + pidx;
     const bool in = p < r.P;
-    for (int k = 0; k < Kp - 2; ++k)
-        out[(size_t)k * TILE_M] = (in && k < N) ? f32_of_f64(th[k % Nb] - bbar[k % Nb]) : 0.0f;
-    out[(size_t)(Kp - 2) * TILE_M] = in ? f32_of_f64(th[NP]) : 0.0f;
-    out[(size_t)(Kp - 1) * TILE_M] = in ? f32_of_f64(th[NP + 1]) : 0.0f;
-    const float s21 = in ? f32_of_f64(th[NP + 2]) : 1.0f;
-    out[(size_t)Kp * TILE_M] = 1.0f / (2.0f * s21 * s21);
-    // the sigma_n terms of eq. likelihood for the reduction (FP64, once per point)
-    if (in && r.pvalid[p]) {
-        const double sig = th[NP + 3];
-        r.pnorm[p] = make_double2((double)r.F * (double)r.T * log(2.0 * 3.141592653589793 * sig * sig),
-                                  1.0 / (sig * sig));
+    for (int k = half; k < Kp - 2; k += 2) {
+        float v = 0.0f;
+        if (in && k < N) {
+            const int j = Nb == N ? k : k % Nb;
+            v = f32_of_f64(th[j] - bbar[j]);
+        }
+        out[(size_t)k * TILE_M] = v;
+    }
+    if (half == 0) {
+        out[(size_t)(Kp - 2) * TILE_M] = in ? f32_of_f64(th[NP]) : 0.0f;
+        out[(size_t)(Kp - 1) * TILE_M] = in ? f32_of_f64(th[NP + 1]) : 0.0f;
+        const float s21 = in ? f32_of_f64(th[NP + 2]) : 1.0f;
+        out[(size_t)Kp * TILE_M] = 1.0f / (2.0f * s21 * s21);
+        // the sigma_n terms of eq. likelihood for the reduction (FP64, once per point)
+        if (in && r.pvalid[p]) {
+            const double sig = th[NP + 3];
+            r.pnorm[p] = make_double2((double)r.F * (double)r.T * log(2.0 * 3.141592653589793 * sig * sig),
+                                      1.0 / (sig * sig));
+        }
+        return;
     }
     if (r.Na) {
-        float2 *g2 = reinterpret_cast<float2 *>(out - threadIdx.x + (size_t)(Kp + 4) * TILE_M) + threadIdx.x;
+        float2 *g2 = reinterpret_cast<float2 *>(out - pidx + (size_t)(Kp + 4) * TILE_M) + pidx;
         int icur = -1;
         float gcur = 0.0f;
         for (int q = 0; q < Kp / 2; ++q) {
@@ -352,12 +385,12 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_tiles_kernel(const ReqDesc 
     const int nfc = r.F * r.n_tchunks;
     const int N = r.N, NP = r.NPF, Nb = r.Nb, T = r.T;
     if ((int)blockIdx.x >= nfc) return;
-    // shared memory: bbar [NPF] FP64, finalise scratch [2 NPF + 2 + 16] FP32 (rounded
-    // to doubles), wbar [N] FP64
+    // shared memory: the head (bbar, finalise scratch and group results), then wbar [N] FP64
     double *bbar = smem_d;
     float *fin_sh = reinterpret_cast<float *>(bbar + NP);
-    double *wbar = bbar + NP + (2 * NP + 2 + 16 + 1) / 2;
-    prep_finalize(r, fin_sh, bbar, blockIdx.x == 0);
+    float *gpart = reinterpret_cast<float *>(bbar + NP + (2 * NP + 2 + 16 + 1) / 2);
+    double *wbar = bbar + prep_head_doubles(NP);
+    prep_finalize(r, fin_sh, gpart, bbar, blockIdx.x == 0);
     const int fc = blockIdx.x;
     const int f = fc / r.n_tchunks, c = fc % r.n_tchunks;
     const int t0 = c * r.Tc, tn = min(r.Tc, T - t0);
@@ -413,7 +446,7 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_tiles_kernel(const ReqDesc 
 // column of the weights), row Kp-1 holds dref 2^sB (multiplies -1), other rows
 // and columns t >= Tc are zero.
 //
-// Shared memory: bbar [NPF], finalise scratch, then the block's slab --
+// Shared memory: bbar [NPF], finalise scratch and group results, then the block's slab --
 // channel: the products' hi and lo parts [N][Tc_pad] each, E hi / lo and dref
 // [Tc_pad], wbar hi / lo [N] (FP32); points: parameter rows
 // [128][padded_row(NPF+4)] FP64.
@@ -428,7 +461,8 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_tc_kernel(const ReqDesc *__
     const int N = r.N, NP = r.NPF, Nb = r.Nb, T = r.T;
     double *bbar = smem_d;
     float *fin_sh = reinterpret_cast<float *>(bbar + NP);
-    double *slab = bbar + NP + (2 * NP + 2 + 16 + 1) / 2;
+    float *gpart = reinterpret_cast<float *>(bbar + NP + (2 * NP + 2 + 16 + 1) / 2);
+    double *slab = bbar + prep_head_doubles(NP);
     if ((int)blockIdx.x >= nfc) {
         // ---- per-point operands of one 128-point tile
         const int tile = blockIdx.x - nfc;
@@ -440,10 +474,11 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_tc_kernel(const ReqDesc *__
             const int row = k / R;
             cp_async8(slab + (size_t)row * Rp + (k - row * R), src + k);
         }
-        prep_finalize(r, fin_sh, bbar, false);
+        prep_finalize(r, fin_sh, gpart, bbar, false);
         cp_async_wait_all();
         __syncthreads();
-        prep_points(r, tile, bbar, slab + (size_t)((int)threadIdx.x < np ? threadIdx.x : 0) * Rp);
+        const int pidx = threadIdx.x % TILE_M;
+        prep_points(r, tile, bbar, slab + (size_t)(pidx < np ? pidx : 0) * Rp);
         return;
     }
     // ---- operand tile of one (channel, t-chunk), in double-float arithmetic
@@ -471,7 +506,7 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_tc_kernel(const ReqDesc *__
         cp_async4(eh + t, r.E_hi + ft0 + t);
         cp_async4(el + t, r.E_lo + ft0 + t);
     }
-    const Fin fin = prep_finalize(r, fin_sh, bbar, fc == 0);
+    const Fin fin = prep_finalize(r, fin_sh, gpart, bbar, fc == 0);
     const double L = r.L[f];
     if (c == 0 && threadIdx.x == 32) {
         // the generators' series coefficients for this channel (the same FP32
@@ -856,7 +891,7 @@ cudaError_t launch_prep(const ReqDesc *h_reqs, const ReqDesc *d_reqs, int n_reqs
     size_t sm = 0;
     for (int k = 0; k < n_reqs; ++k) {
         const ReqDesc &r = h_reqs[k];
-        const size_t head = sizeof(double) * ((size_t)r.NPF + (2 * (size_t)r.NPF + 2 + 16 + 1) / 2);
+        const size_t head = sizeof(double) * (size_t)prep_head_doubles(r.NPF);
         size_t need;
         if (tc) {
             const size_t chan = sizeof(float) * (2 * (size_t)r.N * r.Tc_pad + 3 * (size_t)r.Tc_pad + 2 * (size_t)r.N);
