@@ -34,7 +34,7 @@ constexpr int TILE_M = 128;         // points per MMA tile (tcgen05 M)
 constexpr int TC_MAX = 192;         // max t-columns per MMA (tcgen05 N): two stage slots of
                                     // accumulators (<= 192 columns) plus weights (<= 64 columns)
                                     // fit the 512 tensor-memory columns of an SM
-constexpr int STAT_BLOCK = 256;     // points (threads) per statistics block of the per-request prep
+constexpr int STAT_BLOCK = 128;     // points (threads) per statistics block of the per-request prep
 constexpr int KP_MAX = 64;          // max padded K on the tensor path
 static_assert(STAT_BLOCK % TILE_M == 0, "a statistics block covers whole 128-point tiles");
 

@@ -131,6 +131,23 @@ __device__ __forceinline__ void cp_async4(void *dst, const void *src) {
                  : "memory");
 }
 
+// The block's parameter rows [np][R] (contiguous at src) into shared rows of
+// Rp doubles, one 8-byte cp.async per element in the flat order of the source
+// (coalesced), the (row, column) of each thread stepped without a division.
+__device__ __forceinline__ void copy_rows8(double *dst, int Rp, const double *src, int R, int np) {
+    int row = (int)threadIdx.x / R, col = (int)threadIdx.x - row * R;
+    const int drow = (int)blockDim.x / R, dcol = (int)blockDim.x - drow * R;
+    while (row < np) {
+        cp_async8(dst + (size_t)row * Rp + col, src + (size_t)row * R + col);
+        col += dcol;
+        row += drow;
+        if (col >= R) {
+            col -= R;
+            ++row;
+        }
+    }
+}
+
 // (sh, sl) += (xh, xl) in double-float arithmetic: Knuth's two-sum of the high
 // parts, the low parts added to its error, then renormalised.
 __device__ __forceinline__ void df_add(float &sh, float &sl, float xh, float xl) {
@@ -253,10 +270,7 @@ __global__ void __launch_bounds__(STAT_BLOCK) prep_stats_kernel(const ReqDesc *_
         const int R = N + 4, Rp = padded_row(R);
         double *slab = sh_stats_d + (nw * W + 1) / 2;
         const double *src = r.params + p0 * R;
-        for (int k = threadIdx.x; k < np * R; k += blockDim.x) {
-            const int row = k / R;
-            cp_async8(slab + (size_t)row * Rp + (k - row * R), src + k);
-        }
+        copy_rows8(slab, Rp, src, R, np);
         cp_async_wait_all();
         __syncthreads();
         th = slab + (size_t)(p < r.P ? threadIdx.x : 0) * Rp;
@@ -470,10 +484,7 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_tc_kernel(const ReqDesc *__
         const int np = (int)min((int64_t)TILE_M, r.P - p0);
         const int R = NP + 4, Rp = padded_row(R);
         const double *src = r.params + p0 * R;
-        for (int k = threadIdx.x; k < np * R; k += blockDim.x) {
-            const int row = k / R;
-            cp_async8(slab + (size_t)row * Rp + (k - row * R), src + k);
-        }
+        copy_rows8(slab, Rp, src, R, np);
         prep_finalize(r, fin_sh, gpart, bbar, false);
         cp_async_wait_all();
         __syncthreads();
