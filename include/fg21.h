@@ -232,7 +232,10 @@ int fg21_simulate_data(const fg21_sky *sky, const fg21_obs *obs, const double *t
  * device, evaluates on `stream`, copies logL back and returns when done.
  * Buffers in page-locked memory (cudaMallocHost, cudaHostAlloc,
  * cudaHostRegister) are copied by DMA directly; pageable ones pass through a
- * page-locked staging buffer the model keeps.
+ * page-locked staging buffer the model keeps.  When a call repeats the previous
+ * call's P and precision, the model captures the evaluation as a CUDA graph and
+ * replays it on later calls of that size (one graph kept per model; the
+ * results are the same bit for bit as the direct launches).
  * precision: FG21_PREC_*.  Points with a non-finite parameter, sigma_n <= 0 or
  * sigma21 == 0 get logL = -inf and are counted (fg21_last_invalid_count); the
  * call still succeeds.  Prior bounds are not enforced.  P = 0 is a no-op.

@@ -87,6 +87,8 @@ struct fg21_model {
     fg21_graph *host_graph = nullptr;
     int64_t hg_P = 0;
     int hg_prec = -1, hg_cpg = -1;
+    int64_t last_P = -1;            // the previous host-buffer call's size, precision and split:
+    int last_prec = -1, last_cpg = -1;   // a graph is captured when a call repeats them
     fg21::Workspace ws;
     std::map<std::pair<int, int>, int> tuned_cpg;   // (precision, 128-point tiles) -> channels per group
     std::mutex tune_mu;                              // guards tuned_cpg
