@@ -886,6 +886,9 @@ cudaError_t launch_prep(const ReqDesc *h_reqs, const ReqDesc *d_reqs, int n_reqs
                         int max_stat_blocks, int max_F_chunks, int max_tiles, cudaStream_t stream) {
     int maxNP = 0;
     for (int k = 0; k < n_reqs; ++k) maxNP = maxNP > h_reqs[k].NPF ? maxNP : h_reqs[k].NPF;
+    // the finalise keeps one row of statistics per thread group in FIN_GROUP_SCRATCH
+    // floats (2 NPF + 2 <= 256 within the documented region limits)
+    if (2 * maxNP + 2 > FIN_GROUP_SCRATCH) return cudaErrorInvalidValue;
     dim3 g1(max_stat_blocks, n_reqs);
     // warp partials, then the staged parameter rows when they fit comfortably
     const size_t part = sizeof(double) * (((size_t)(STAT_BLOCK / 32) * (2 * maxNP + 2) + 1) / 2);
