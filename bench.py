@@ -25,7 +25,7 @@ contraction, trough, residual and square (a2-a5), per-point reduction and logL
                the amplitude-mask model, the noise-only likelihood workload,
                log L_max(N), the 64-point latency case and the serving mix
 
-`--impl reference` times the oracle alone (the reference arm of this build).
+`--impl reference` times the FP64 oracle alone (the paper publishes no code to run).
 Multi-GPU: one process per GPU under torchrun, each rank an independent
 replica with its own batch (weak scaling, no collective on the data path).
 """
