@@ -21,6 +21,8 @@ contraction, trough, residual and square (a2-a5), per-point reduction and logL
                dense 16-bit tensor peak
   cpu_baseline the FP64 oracle on the host cores (all of them, and one), on a
                bounded sample
+  near_posterior  the same step on a batch close to one point (the regime
+               of a nested sampler's late iterations)
   alpha_model, noise_q, occam, small_batch, serve
                the amplitude-mask model, the noise-only likelihood workload,
                log L_max(N), the 64-point latency case and the serving mix
@@ -645,6 +647,14 @@ def main():
     e2e_s = max_over_ranks([(time.perf_counter() - t) / e2e_K], dev)[0]
     assert np.all(np.isfinite(out))
 
+    # the nested-sampling regime: the same graph-replayed step on a batch scattered
+    # by 1e-5 in beta about one point (the weights' series takes its short form)
+    near = I.scatter_around(params[0], P, 1e-5, I.BASE_SEED, extra=rank)
+    d_params.copy_(torch.from_numpy(near))
+    nres = timed_graph(max(3, args.steps // 4), 3)
+    near_ms = max_over_ranks([nres["ms_per_step"]], dev)[0]
+    d_params.copy_(torch.from_numpy(params))
+
     pk, pk_kind = peaks()
     alg_flops = 2.0 * N * F * T * P
     achieved = alg_flops / (res["main_ms"] * 1e-3) / 1e12
@@ -682,11 +692,14 @@ def main():
         "direct_call": {"value": P * ws / (call_ms * 1e-3), "unit": "logL evals/s", "ms_per_step": call_ms,
                         "what": "the same step through fg21_loglike_batch_device each time (plan, descriptor "
                                 "upload and four launches per call)"},
+        "near_posterior": {"value": replica_throughput(P, ws, near_ms), "unit": "logL evals/s", "ms_per_step": near_ms,
+                           "what": "the graph-replayed step on 16384 points within 1e-5 in beta of one point, "
+                                   "as a nested sampler's late batches are (L2 flushed between steps)"},
         "e2e": {"value": P * ws / e2e_s, "unit": "logL evals/s", "h2d_bytes_per_step": int(params.nbytes),
                 "d2h_bytes_per_step": int(P * 8), "ms_per_step": e2e_s * 1e3,
                 "path": "fg21_loglike_batch on page-locked host buffers: params H2D, the step (replayed from "
                         "the graph the call keeps for its size), logL and status D2H, synchronise"},
-        "gpu_launches": 4 * args.steps,     # prep_stats, prep_tc, tc_loglike, reduce
+        "gpu_launches": 4 * args.steps,     # prep_stats, prep_tc, tc_loglike, reduce per timed graph replay
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": f"{pk_kind} dense bf16 burst (fp16 same nominal rate)",

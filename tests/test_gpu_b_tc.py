@@ -166,14 +166,10 @@ def test_workload3_benchmark_configuration_sampled(fg21lib):
     every 64th logL (256 points the oracle evaluates one by one) is within the
     derived tolerance."""
     torch = pytest.importorskip("torch")
-    wl = cases.I.workload(3)
-    sky, obs = wl.sky(), wl.obs()
-    m = O.build_model(sky, obs, wl.N, wl.scheme, wl.weighting)
-    data = O.simulate_data(sky, obs, np.array(cases.I.FIDUCIAL_T21), cases.I.NOISE_K, wl.noise())
+    wl, sky, obs, m, data, params = cases.workload_case(3)      # the oracle's model, built once per session
     model = fg21lib.fg21_build_regions(sky, obs, wl.N, wl.scheme, wl.weighting)
     assert np.array_equal(model.labels, m.labels)
     fg21lib.fg21_model_set_data(model, data)
-    params = wl.params()
     P = params.shape[0]
     d_p = torch.from_numpy(params).cuda()
     d_l = torch.empty(P, dtype=torch.float64, device="cuda")
@@ -239,3 +235,35 @@ def test_limits_refused(fg21lib):
     with pytest.raises(fg21lib.Fg21Error) as e:
         fg21lib.fg21_build_regions(sky, obs, 127)
     assert e.value.code == fg21lib.FG21_E_ARG
+
+
+def test_workload3_near_posterior_sampled(fg21lib):
+    """The benchmark's sky, model and launch configuration (graph replay of 16384
+    points) on the nested-sampling regime: data from the 24-region model at a
+    truth plus 25 mK noise, points within 1e-5 in beta of it.  Every 64th logL
+    (256 points the oracle evaluates one by one) meets the absolute 1e-2 nats
+    bound where chi2/(F T) <= 10, and the derived bound everywhere."""
+    torch = pytest.importorskip("torch")
+    wl, sky, obs, m, _, _ = cases.workload_case(3)
+    truth, data, pts = cases.near_posterior(m, obs, 1e-5, wl.P)
+    model = fg21lib.fg21_build_regions(sky, obs, wl.N, wl.scheme, wl.weighting)
+    fg21lib.fg21_model_set_data(model, data)
+    d_p = torch.from_numpy(pts).cuda()
+    d_l = torch.empty(wl.P, dtype=torch.float64, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    g = fg21lib.fg21_graph_create(model, d_p.data_ptr(), wl.P, d_l.data_ptr(), "fp16x3")
+    g.launch(s)
+    assert g.sync_status(s) == 0
+    got = d_l.cpu().numpy()
+    g.close()
+    idx = np.arange(0, wl.P, 64)
+    want, dterm = cases.expected(m, obs, data, pts[idx])
+    err = np.abs(got[idx] - want)
+    red = 2 * dterm / (obs.F * obs.T)
+    near = red <= 10
+    report("w3_near_posterior_sampled", max_abs=err.max(), max_chi2_red=red.max(), n_near=int(near.sum()))
+    assert near.sum() > 0
+    assert np.all(err[near] <= 1e-2), cases.fmt_err("w3 near", got[idx][near], want[near], 1e-2)
+    tol = cases.logl_tolerance("fp16x3", m, obs, data, pts[idx])
+    assert np.all(err <= tol), cases.fmt_err("w3 near", got[idx], want, tol)
+    model.close()
