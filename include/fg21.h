@@ -68,6 +68,13 @@ extern "C" {
 #define FG21_PREC_BF16X3      1  /* as FP16X3 with BF16 operands (wider range, 8-bit significands) */
 #define FG21_PREC_FP32_DELTA  2  /* SIMT FP32, reference-subtracted */
 #define FG21_PREC_FP32_DIRECT 3  /* SIMT FP32, the plain eq. fast_forward_model in FP32 (comparator) */
+/* Accuracy of the reference-subtracted forms: each residual carries a relative
+ * error of about u (2^-22 split FP16, 2^-16 split BF16, 2^-24 FP32) of the
+ * batch's departure from its reference point, sum_i |A_i| |w(beta_p,i) - w(bbar_i)|,
+ * so the logL error grows with the spread of the batch in beta and with the
+ * number of cells F T.  Measured with split FP16 at F T = 30100: 3e-3 nats for a
+ * batch within 1e-6 of one point, 0.03 nats within 1e-5.  The plain FP32 form
+ * carries u of the whole foreground instead. */
 
 /* Limits. */
 #define FG21_MAX_REGIONS_TC  62      /* N <= 62 on the tensor-core path (K = N + 2 padded to <= 64) */
