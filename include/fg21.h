@@ -264,30 +264,34 @@ int fg21_loglike_batch_device(fg21_model *m, const double *d_params, int64_t P, 
 #define FG21_NOALLOC_SCRATCH_BYTES (32u << 20)
 
 /* The paper has no counterpart to this call.  It serves callers that cannot
- * allocate GPU memory while they evaluate the likelihood: code that runs while
- * a CUDA graph is being captured (an allocation there is not allowed), or a
- * host that fixes the library's device memory up front and forbids growth
- * later.  Same arguments and results as fg21_loglike_batch_device, for the
- * tensor-core precisions (FG21_PREC_FP16X3, FG21_PREC_BF16X3), but it calls no
- * cudaMalloc / cudaFree and allocates nothing: all per-call scratch comes from
+ * allocate GPU memory while they evaluate the likelihood: a host application
+ * that gives the library a fixed device-memory budget at start-up and forbids
+ * growth afterwards, or a runtime that owns the GPU's memory pool and refuses
+ * allocations from plug-ins once it is running.  Same arguments and results as
+ * fg21_loglike_batch_device, for the tensor-core precisions (FG21_PREC_FP16X3,
+ * FG21_PREC_BF16X3), but it calls no cudaMalloc / cudaFree and allocates
+ * nothing: all per-call scratch, the request descriptor included, comes from
  * one static device array of FG21_NOALLOC_SCRATCH_BYTES (32 MiB) that every GPU
  * which loads the library keeps until the process exits.  The model itself
- * must already exist (fg21_build_regions allocates it).  A request whose
- * scratch would not fit returns FG21_E_RANGE (the limit is about 105,000
- * points at N = 24, F = 301, T = 100; split larger batches).  The first
- * call on a device looks up the array's device address (cudaGetSymbolAddress)
- * with that device current, so make that first call before any stream capture.
- * All calls share the array and leave its contents behind (the status word is
- * cleared at the start of each call, everything else is rewritten): calls
- * that overlap on the GPU race, so order them, e.g. on one stream.  Invalid
- * points get logL = -inf as in the other calls; the invalid count and the
- * kernels' internal status are not reported by this call. */
+ * must already exist (fg21_build_regions allocates it); the call takes the
+ * model's lock and makes the model's device current, as the regular calls do.
+ * A request whose scratch would not fit returns FG21_E_RANGE (the limit is
+ * about 105,000 points at N = 24, F = 301, T = 100; split larger batches).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current, so make that first call
+ * before any stream capture on that device.  All calls share the array and
+ * leave its contents behind (the status word is cleared at the start of each
+ * call, everything else is rewritten): calls that overlap on the GPU race, so
+ * order them, e.g. on one stream.  Invalid points get logL = -inf as in the
+ * other calls; the invalid count is not reported by this call, and a kernel's
+ * internal failure (a bounded wait that ran out) shows as logL = NaN for every
+ * point of the call. */
 int fg21_loglike_batch_device_noalloc(fg21_model *m, const double *d_params, int64_t P, double *d_logL,
                                       int precision, void *stream);
 
 /* Wait for the model's outstanding work on `stream`, then report the invalid
  * count of its last device call (may be NULL) and FG21_E_DEVICE if a kernel
- * reported an internal failure. */
+ * reported an internal failure (the logL of that call are then NaN). */
 int fg21_model_sync_status(fg21_model *m, void *stream, int64_t *invalid_count);
 
 /* The paper has no counterpart to this call: it checks the library's failure

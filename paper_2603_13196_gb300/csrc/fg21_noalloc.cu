@@ -2,20 +2,27 @@
 // callers that must not allocate GPU memory during a call.
 //
 // Some callers cannot call cudaMalloc at the point where they evaluate the
-// likelihood: code running while a CUDA graph is being captured, hosts that
-// give the library a fixed memory budget up front, or a runtime that forbids
-// allocation after start-up.  The regular entry points grow a per-model
-// workspace with cudaMalloc on first use; this one instead takes all of its
-// per-call scratch (request statistics, reference data, operand tiles, point
-// operands, partial sums, the request descriptor and the status word) from one
-// file-scope device array of FG21_NOALLOC_SCRATCH_BYTES, which every GPU that
-// loads the library holds until the process exits.  It runs the same kernels
-// (prep, tensor-core likelihood, reduction) as fg21_loglike_batch_device.
+// likelihood: a host application that hands the library a fixed device-memory
+// budget at start-up and forbids growth afterwards, or a runtime that owns the
+// GPU's memory pool and rejects allocations from plug-ins once it is running.
+// The regular entry points grow a per-model workspace with cudaMalloc on
+// first use; this one instead takes all of its per-call scratch (request
+// statistics, reference data, operand tiles, point operands, partial sums, the
+// request descriptor and the status word) from one file-scope device array of
+// FG21_NOALLOC_SCRATCH_BYTES, which every GPU that loads the library holds
+// until the process exits.  It runs the same kernels (prep, tensor-core
+// likelihood, reduction) as fg21_loglike_batch_device.
+//
+// The request descriptor reaches the array through the arguments of a
+// one-thread kernel (kernel arguments are copied when the launch is enqueued),
+// so no host buffer has to outlive the call.
 //
 // Every call shares the array and leaves its contents behind: the status word
 // and invalid counter are cleared at the start of each call, everything else
 // is fully rewritten.  Calls that overlap on the GPU (two streams, or two host
-// threads) race on the array; callers must order them.
+// threads) race on the array; callers must order them.  If a kernel reports an
+// internal failure (a bounded wait that ran out), the reduction writes NaN to
+// every logL of the call instead of a value built from stale partial sums.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -53,6 +60,10 @@ int noalloc_base(int device, char **base) {
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Stores the request descriptor, passed by value, into the scratch array.
+static_assert(sizeof(ReqDesc) <= 4096, "the request descriptor travels as a kernel argument");
+__global__ void store_desc_kernel(const ReqDesc r, ReqDesc *dst) { *dst = r; }
+
 }  // namespace
 }  // namespace fg21
 
@@ -67,9 +78,13 @@ extern "C" int fg21_loglike_batch_device_noalloc(fg21_model *m, const double *d_
     if (m->N > FG21_MAX_REGIONS_TC) return set_error(FG21_E_RANGE, "N = %d above the tensor-core limit", m->N);
     if (P == 0) return FG21_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    int dev = 0;
-    FG21_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev != m->device) return set_error(FG21_E_ARG, "model lives on device %d, current device is %d", m->device, dev);
+    // the model's lock keeps its device arrays fixed while the request reads
+    // them; the model's device is made current, as the regular calls do
+    std::lock_guard<std::mutex> lk(m->mu);
+    const int dev = m->device;
+    int cur = -1;
+    FG21_CUDA_TRY(cudaGetDevice(&cur));
+    if (cur != dev) FG21_CUDA_TRY(cudaSetDevice(dev));
     char *base = nullptr;
     int rc = noalloc_base(dev, &base);
     if (rc) return rc;
@@ -112,7 +127,8 @@ extern "C" int fg21_loglike_batch_device_noalloc(fg21_model *m, const double *d_
 
     // the status word and invalid counter start at zero; the rest is rewritten
     FG21_CUDA_TRY(cudaMemsetAsync(status, 0, status_bytes(1), s));
-    FG21_CUDA_TRY(cudaMemcpyAsync(d_req, &r, sizeof r, cudaMemcpyHostToDevice, s));
+    store_desc_kernel<<<1, 1, 0, s>>>(r, d_req);
+    FG21_CUDA_TRY(cudaGetLastError());
     FG21_CUDA_TRY(launch_prep(&r, d_req, 1, precision, r.n_stat_blocks, r.F * r.n_tchunks, r.n_tiles, s));
     TcLaunch T;
     T.d_reqs = d_req;
