@@ -276,7 +276,7 @@ int fg21_loglike_batch_device(fg21_model *m, const double *d_params, int64_t P, 
  * must already exist (fg21_build_regions allocates it); the call takes the
  * model's lock and makes the model's device current, as the regular calls do.
  * A request whose scratch would not fit returns FG21_E_RANGE (the limit is
- * about 105,000 points at N = 24, F = 301, T = 100; split larger batches).
+ * about 73,000 points at N = 24, F = 301, T = 100; split larger batches).
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current, so make that first call
  * before any stream capture on that device.  All calls share the array and
