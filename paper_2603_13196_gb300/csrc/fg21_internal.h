@@ -114,7 +114,12 @@ struct ReqDesc {
                            // spectral index (rows < Kp-2, zero beyond N), then A21, nu21,
                            // 1/(2 sigma21^2) (rows Kp-2..Kp); with amplitude parameters, rows
                            // Kp+4.. hold ln(alpha / alpha_bar) of each component, pair-interleaved
-                           // ([Kp/2 pairs][128 points][2]); tensor path
+                           // ([Kp/2 pairs][128 points][2]); the last Kp rows hold the low parts
+                           // of the deviations (beta - bbar minus its FP32 rounding), pair-
+                           // interleaved the same way; tensor path
+    double chi2_scale;     // the reduction multiplies chi2 by this: 1 + (2/3) 2^-23 on the tensor
+                           // path (the expected half-ulp that the accumulator's final rounding
+                           // toward zero drops, relative to chi2), 1 on the SIMT paths
     unsigned *status;      // device status word (shared by a launch)
     unsigned long long *invalid;  // invalid-point counter
 };

@@ -329,7 +329,12 @@ __global__ void __launch_bounds__(STAT_BLOCK) prep_stats_kernel(const ReqDesc *_
 // of component k's spectral index j in FP32 (zero for k >= N), then A21, nu21
 // and 1/(2 sigma21^2); with amplitude regions, rows Kp+4.. hold
 // ln(alpha_{p,i} / abar_i) of each component's amplitude i, two components per
-// 8-byte pair ([Kp/2][128][2]) so a generator thread loads a pair at once.
+// 8-byte pair ([Kp/2][128][2]) so a generator thread loads a pair at once.  The
+// last Kp rows hold, in the same pair layout, the low part of each deviation
+// (beta - bbar less its FP32 rounding): a deviation rounded to FP32 shifts the
+// point by up to 2^-25 of it in every cell of the observation at once, which
+// near the posterior of a large observation moves logL by more than 1e-2
+// nats, so the generators add its first-order effect to each weight.
 // Two threads per point (`half` 0 and 1 of the block): the deviation rows
 // alternate between them; half 0 also writes the trough rows and the sigma_n
 // terms, half 1 the amplitude rows.  `th` is the point's parameter row (staged
@@ -340,15 +345,21 @@ __device__ __forceinline__ void prep_points(const ReqDesc &r, int tile, const do
     const int64_t p = (int64_t)tile * TILE_M + pidx;
     const int N = r.N, Nb = r.Nb, NP = r.NPF, Kp = r.Kp;
     float *out = r.pts32 + (size_t)tile * r.pts_rows * TILE_M + pidx;
+    // the deviations' low parts: pair-interleaved rows after the other operands
+    float *lo_out = out - pidx + (size_t)(Kp + 4 + (r.Na ? Kp : 0)) * TILE_M + 2 * pidx;
     const bool in = p < r.P;
     for (int k = half; k < Kp - 2; k += 2) {
-        float v = 0.0f;
+        float v = 0.0f, vlo = 0.0f;
         if (in && k < N) {
             const int j = Nb == N ? k : k % Nb;
-            v = f32_of_f64(th[j] - bbar[j]);
+            const double dv = th[j] - bbar[j];
+            v = f32_of_f64(dv);
+            vlo = f32_of_f64(dv - (double)v);
         }
         out[(size_t)k * TILE_M] = v;
+        lo_out[(size_t)(k >> 1) * 2 * TILE_M + (k & 1)] = vlo;
     }
+    lo_out[(size_t)((Kp - 2) >> 1) * 2 * TILE_M + half] = 0.0f;     // the (trough, -1) pair
     if (half == 0) {
         out[(size_t)(Kp - 2) * TILE_M] = in ? f32_of_f64(th[NP]) : 0.0f;
         out[(size_t)(Kp - 1) * TILE_M] = in ? f32_of_f64(th[NP + 1]) : 0.0f;
@@ -771,6 +782,8 @@ __device__ __forceinline__ void two_sum_acc(float &s, float &c, float x) {
 //    summing partials l, l+32, ... in ascending order, the lanes' sums combined
 //    in a fixed butterfly.
 // WARP selects the form a launch serves; requests of the other form are skipped.
+// When the launch's status word is set (a bounded wait ran out, so some
+// partials were never written), every logL of the launch is NaN.
 template <bool WARP>
 __global__ void __launch_bounds__(REDUCE_THREADS) reduce_kernel(const ReqDesc *__restrict__ reqs, int n_reqs) {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -780,6 +793,10 @@ __global__ void __launch_bounds__(REDUCE_THREADS) reduce_kernel(const ReqDesc *_
     const int64_t p = gid - r.pt_begin;
     if (p < 0 || p >= r.P) return;       // uniform over a warp in WARP mode
     if ((r.n_part > REDUCE_SERIAL_MAX) != WARP) return;
+    if (*r.status) {         // a kernel of this launch stopped early: its partials are incomplete
+        if (lane == 0) r.logL[p] = __longlong_as_double(0x7FF8000000000000ll);
+        return;
+    }
     if (!r.pvalid[p]) {      // the statistics pass tested the point (point_valid)
         if (lane == 0) {
             r.logL[p] = -INFINITY;
@@ -808,7 +825,7 @@ __global__ void __launch_bounds__(REDUCE_THREADS) reduce_kernel(const ReqDesc *_
             two_sum_acc(sh, sl, v.y);
         }
     }
-    const double chi2 = (double)sh + (double)sl;
+    const double chi2 = ((double)sh + (double)sl) * r.chi2_scale;
     if (r.pnorm) {           // sigma_n terms from prep (tensor path)
         const double2 nm = r.pnorm[p];
         r.logL[p] = -0.5 * (nm.x + chi2 * nm.y);

@@ -161,7 +161,7 @@ static int choose_channels_per_group(int64_t total_tiles, int F, int num_sms) {
 
 void plan_request(ReqDesc &r, int precision, int num_sms, int64_t total_tiles) {
     r.Kp = round16(r.N + 2);
-    r.pts_rows = r.Kp + 4 + (r.Na ? r.Kp : 0);
+    r.pts_rows = r.Kp + 4 + (r.Na ? r.Kp : 0) + r.Kp;
     // t-chunks of at most TC_MAX columns: the same cap for every K keeps the
     // plan of a request independent of what it is batched with
     r.n_tchunks = (r.T + TC_MAX - 1) / TC_MAX;
@@ -174,6 +174,7 @@ void plan_request(ReqDesc &r, int precision, int num_sms, int64_t total_tiles) {
     r.ch_per_group = (r.F + r.G - 1) / r.G;
     const bool tc = precision == FG21_PREC_FP16X3 || precision == FG21_PREC_BF16X3;
     r.n_part = tc ? 2 * r.G : r.G;      // the tensor path splits each point's t-columns over two warps
+    r.chi2_scale = tc ? 1.0 + (2.0 / 3.0) * std::ldexp(1.0, -23) : 1.0;
     r.tile_rows = (int64_t)r.Kp * r.Tc_pad / 32;   // 2 splits x Kp x Tc_pad x 2 bytes / 128
 }
 

@@ -284,8 +284,12 @@ __device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
 // coefficients e_j (2^sW folded into them when s = 0), on two arguments at
 // once.  Relative truncation error |y|^D / (D+1)!: D = 3 for |y| <= 0.01,
 // 5 for |y| <= 0.1, 8 for |y| <= 0.55; each squaring adds about two roundings.
-template <int D, int CH>
-__device__ __forceinline__ void em1_series2(uint64_t (&w)[CH], const uint64_t *d2, const uint64_t *e2) {
+// LO: the deviation is d + dlo (dlo2, its part below FP32); the last Horner
+// step adds e_1 dlo, the first-order effect of dlo (its next term is about
+// |y| times smaller and below FP32 resolution).
+template <int D, int CH, bool LO>
+__device__ __forceinline__ void em1_series2(uint64_t (&w)[CH], const uint64_t *d2, const uint64_t *e2,
+                                            const uint64_t *dlo2) {
 #pragma unroll
     for (int i = 0; i < CH; ++i) w[i] = fma2(e2[D], d2[i], e2[D - 1]);
 #pragma unroll
@@ -293,7 +297,7 @@ __device__ __forceinline__ void em1_series2(uint64_t (&w)[CH], const uint64_t *d
 #pragma unroll
         for (int i = 0; i < CH; ++i) w[i] = fma2(w[i], d2[i], e2[j]);
 #pragma unroll
-    for (int i = 0; i < CH; ++i) w[i] = mul2(w[i], d2[i]);
+    for (int i = 0; i < CH; ++i) w[i] = LO ? fma2(w[i], d2[i], mul2(e2[1], dlo2[i])) : mul2(w[i], d2[i]);
 }
 
 template <bool BF16>
@@ -338,9 +342,10 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t 
 // ln(alpha / abar) of each component (pairs at gp[i * 128]) and the channel's
 // nL in nL2; e2 then holds the constant coefficients 2^(-s j) / j!.
 template <int NPHMAX, bool BF16, bool FULL, bool ALPHA>
-__device__ __forceinline__ void gen_half(uint32_t t_hi, uint32_t t_mid, const uint64_t *d2, const uint64_t *e2,
-                                         SeriesPlan sp, uint64_t sW2, int nph_rt, int nz, bool last, float s21,
-                                         float sW, const float2 *__restrict__ gp, uint64_t nL2) {
+__device__ __forceinline__ void gen_half(uint32_t t_hi, uint32_t t_mid, const uint64_t *d2,
+                                         const float2 *__restrict__ lop, const uint64_t *e2, SeriesPlan sp,
+                                         uint64_t sW2, int nph_rt, int nz, bool last, float s21, float sW,
+                                         const float2 *__restrict__ gp, uint64_t nL2) {
     constexpr int CH = 4;
     const int nph = FULL ? NPHMAX : nph_rt;
 #pragma unroll
@@ -359,9 +364,21 @@ __device__ __forceinline__ void gen_half(uint32_t t_hi, uint32_t t_mid, const ui
                 }
                 x2 = y2;
             }
-            if (sp.D == 3) em1_series2<3, CH>(w, x2, e2);
-            else if (sp.D == 5) em1_series2<5, CH>(w, x2, e2);
-            else em1_series2<8, CH>(w, x2, e2);
+            if (sp.D == 3) {
+                // short series (a batch spread below ~0.007 in beta, as near a
+                // posterior): the deviations' low parts enter the weights
+                uint64_t l2[CH];
+#pragma unroll
+                for (int i = 0; i < CH; ++i) {
+                    const float2 v = ALPHA ? make_float2(0.0f, 0.0f) : __ldg(lop + (size_t)(c0 + i) * 128);
+                    l2[i] = pk2(v.x, v.y);
+                }
+                em1_series2<3, CH, !ALPHA>(w, x2, e2, l2);
+            } else if (sp.D == 5) {
+                em1_series2<5, CH, false>(w, x2, e2, nullptr);
+            } else {
+                em1_series2<8, CH, false>(w, x2, e2, nullptr);
+            }
             if (sp.s > 0) {
                 const uint64_t two2 = pk2(2.0f, 2.0f);
                 for (int q = 0; q < sp.s; ++q)
@@ -421,6 +438,7 @@ struct Ring {
 template <int NPHMAX>
 struct GenItem {
     uint64_t d2[NPHMAX];
+    const float2 *lop;     // this thread's first low-part pair of its half (spectral-index-only models)
     float a21, nu21, inv2s2, sW;
     int Kr, nz;            // nz: pairs of this half from index nz on carry no region
     SeriesPlan sp;
@@ -439,6 +457,9 @@ __device__ __forceinline__ void gen_item_load(GenItem<NPHMAX> &g, const ReqDesc 
         const float b = (i < nph && k + 1 < Kr - 2) ? pts[(size_t)(k + 1) * 128] : 0.0f;
         g.d2[i] = pk2(a, b);
     }
+    // low parts: pair-interleaved rows after the other operands (pairs beyond N hold zeros)
+    g.lop = reinterpret_cast<const float2 *>(pts - m + (size_t)(Kr + 4 + (r.Na ? Kr : 0)) * 128) +
+            (size_t)half * nph * 128 + m;
     g.a21 = half ? pts[(size_t)(Kr - 2) * 128] : 0.0f;
     g.nu21 = half ? pts[(size_t)(Kr - 1) * 128] : 0.0f;
     g.inv2s2 = half ? pts[(size_t)Kr * 128] : 0.0f;
@@ -503,11 +524,13 @@ __device__ __forceinline__ bool gen_item(const Params &prm, Barriers *S, Ring &r
             tc_fence_after();
             const uint32_t wb = w_lane + rg.slot * KP;
             if (FULL)
-                gen_half<NPHMAX, BF16, true, ALPHA>(wb + half * NPHMAX, wb + KP / 2 + half * NPHMAX, gi.d2, e2, gi.sp,
-                                                    sW2, NPHMAX, gi.nz, half != 0, s21, gi.sW, gi.gp, pk2(nL, nL));
+                gen_half<NPHMAX, BF16, true, ALPHA>(wb + half * NPHMAX, wb + KP / 2 + half * NPHMAX, gi.d2, gi.lop,
+                                                    e2, gi.sp, sW2, NPHMAX, gi.nz, half != 0, s21, gi.sW, gi.gp,
+                                                    pk2(nL, nL));
             else
-                gen_half<NPHMAX, BF16, false, ALPHA>(wb + half * nph, wb + gi.Kr / 2 + half * nph, gi.d2, e2, gi.sp,
-                                                     sW2, nph, gi.nz, half != 0, s21, gi.sW, gi.gp, pk2(nL, nL));
+                gen_half<NPHMAX, BF16, false, ALPHA>(wb + half * nph, wb + gi.Kr / 2 + half * nph, gi.d2, gi.lop,
+                                                     e2, gi.sp, sW2, nph, gi.nz, half != 0, s21, gi.sW, gi.gp,
+                                                     pk2(nL, nL));
             tmem_st_wait();
             tc_fence_before();
             __syncwarp();
@@ -645,6 +668,32 @@ struct MmaStage {
     }
 };
 
+// The stage's MMAs as straight-line code for KS k steps: the issuing thread
+// shares its scheduler with ALU warps, and loop control between the MMAs
+// measurably delays them.
+//
+// Each MMA rounds its sum toward zero in FP32 (measured on this part: the
+// accumulator and the 16 products are aligned to the largest exponent E,
+// truncated at 2^(E-25), added, and the sum truncated to FP32), so every MMA
+// whose result is as large as the residual biases |D - M| low by about half an
+// ulp.  The small correction products (hi*mid, mid*hi) of every k step go
+// first, while the accumulator is still small, then the hi*hi products, last k
+// step first: only the last MMA ends at the size of the residual, and the
+// reduction adds back its expected half-ulp (chi2_scale).
+template <int KS>
+__device__ __forceinline__ void issue_mmas(uint32_t d_tmem, uint32_t w_hi, uint32_t w_mid, uint32_t b_addr,
+                                           uint32_t b_lbo, uint32_t b_split, uint32_t idesc) {
+#pragma unroll
+    for (int ks = 0; ks < KS; ++ks) {
+        mma_f16_ts(d_tmem, w_hi + ks * 8, smem_desc(b_addr + b_split + ks * 2 * b_lbo, b_lbo, 128), idesc,
+                   ks > 0 ? 1u : 0u);
+        mma_f16_ts(d_tmem, w_mid + ks * 8, smem_desc(b_addr + ks * 2 * b_lbo, b_lbo, 128), idesc, 1u);
+    }
+#pragma unroll
+    for (int ks = KS - 1; ks >= 0; --ks)
+        mma_f16_ts(d_tmem, w_hi + ks * 8, smem_desc(b_addr + ks * 2 * b_lbo, b_lbo, 128), idesc, 1u);
+}
+
 template <int KP, bool BF16>
 __device__ __forceinline__ void issue_stage(const MmaStage &st, uint32_t tmem, uint32_t w_col0, char *b_slots,
                                             const Params &prm) {
@@ -652,16 +701,10 @@ __device__ __forceinline__ void issue_stage(const MmaStage &st, uint32_t tmem, u
     const uint32_t w_hi = tmem + w_col0 + st.rg.slot * KP, w_mid = w_hi + st.Kr / 2;
     const uint32_t b_addr = smem_u32(b_slots + st.rg.slot * prm.b_stage_bytes);
     const uint32_t d_tmem = tmem + st.rg.slot * prm.acc_cols;
-    // per k-step hi*hi, hi*mid, mid*hi.  (Putting the small correction products
-    // before every hi*hi one lowers the accumulation error near the posterior by
-    // about a sixth but measured 13% slower.)
-    for (int ks = 0; ks < st.ksteps; ++ks) {
-        const uint64_t b_hi = smem_desc(b_addr + ks * 2 * st.b_lbo, st.b_lbo, 128);
-        const uint64_t b_mid = smem_desc(b_addr + st.b_split + ks * 2 * st.b_lbo, st.b_lbo, 128);
-        mma_f16_ts(d_tmem, w_hi + ks * 8, b_hi, idesc, ks > 0 ? 1u : 0u);
-        mma_f16_ts(d_tmem, w_hi + ks * 8, b_mid, idesc, 1u);
-        mma_f16_ts(d_tmem, w_mid + ks * 8, b_hi, idesc, 1u);
-    }
+    if (KP == 16 || st.ksteps == 1) issue_mmas<1>(d_tmem, w_hi, w_mid, b_addr, st.b_lbo, st.b_split, idesc);
+    else if (KP == 32 || st.ksteps == 2) issue_mmas<2>(d_tmem, w_hi, w_mid, b_addr, st.b_lbo, st.b_split, idesc);
+    else if (st.ksteps == 3) issue_mmas<3>(d_tmem, w_hi, w_mid, b_addr, st.b_lbo, st.b_split, idesc);
+    else issue_mmas<4>(d_tmem, w_hi, w_mid, b_addr, st.b_lbo, st.b_split, idesc);
 }
 
 // Tensor-memory columns: accumulator of slot s at s * acc_cols; weights of

@@ -3,7 +3,7 @@
 Every expected value comes from the FP64 oracle (oracle/); inputs come from
 paper_2603_13196_gb300.inputs.  Nothing here calls the CUDA library.
 
-Tolerances (derived from the arithmetic; see the design notes):
+Tolerances (derived from the arithmetic of each form):
   * logL, any point: |dlogL| <= 1e-2 + C u sum_{f,t} |r| (S + |r|) / sigma_n^2
     (logl_tolerance): each residual r is formed from terms of size S (the
     point's departure from the request reference, or the whole foreground for
@@ -19,6 +19,7 @@ from __future__ import annotations
 
 import functools
 import math
+import os
 
 import numpy as np
 
@@ -131,6 +132,135 @@ def foreground_magnitude(m, obs, params):
     L = np.log(obs.nu / obs.nu0)
     w = np.exp(-params[:, :N, None] * L[None, None, :])
     return np.einsum("pif,ift->pft", w, np.abs(m.A))
+
+
+# Regression ceilings.  The derived bound above is the contract; each family of
+# parity checks also keeps its worst err/tol below a ceiling of 4x the figure
+# measured on a GB300 (kept beside it), so that an accuracy regression well
+# inside the derived bound still fails.  FG21_CEILING_COLLECT=1 reports the
+# ratios without applying the ceilings (to re-measure after a deliberate
+# change of the arithmetic).
+CEILING_FACTOR = 4.0
+# worst err / tol of each family over its GPU tests (one GB300 run of the whole
+# -m gpu suite with FG21_CEILING_COLLECT=1); 0 means the comparison was exact
+MEASURED_ERR_OVER_TOL = {
+    'T_model_near_bf16x3_1e-05': 1.734e-03,
+    'T_model_near_bf16x3_1e-06': 1.895e-03,
+    'T_model_near_fp16x3_1e-05': 4.270e-05,
+    'T_model_near_fp16x3_1e-06': 4.810e-05,
+    'T_model_near_fp32_delta_1e-05': 2.792e-05,
+    'T_model_near_fp32_delta_1e-06': 1.752e-05,
+    'T_model_prior_bf16x3': 3.500e-02,
+    'T_model_prior_fp16x3': 5.606e-02,
+    'T_model_prior_fp32_delta': 1.024e-01,
+    'T_model_prior_fp32_direct': 4.321e-01,
+    'ab_invalid_fp16x3': 1.380e-02,
+    'ab_invalid_fp32_delta': 6.032e-02,
+    'ab_invalid_fp32_direct': 6.738e-02,
+    'ab_multi_fp16x3': 1.748e-02,
+    'ab_near_abs_fp16x3_0.0001_0.001': 1.764e-01,
+    'ab_near_abs_fp16x3_1e-05_0.0001': 3.310e-01,
+    'ab_near_abs_fp16x3_1e-06_1e-06': 7.095e-03,
+    'ab_near_abs_fp32_delta_0.0001_0.001': 6.025e-01,
+    'ab_near_abs_fp32_delta_1e-05_0.0001': 3.744e-01,
+    'ab_near_abs_fp32_delta_1e-06_1e-06': 2.094e-03,
+    'ab_near_bf16x3_0.0001_0.001': 1.404e-03,
+    'ab_near_bf16x3_1e-05_0.0001': 1.450e-03,
+    'ab_near_bf16x3_1e-06_1e-06': 1.341e-03,
+    'ab_near_fp16x3_0.0001_0.001': 2.154e-02,
+    'ab_near_fp16x3_1e-05_0.0001': 1.507e-02,
+    'ab_near_fp16x3_1e-06_1e-06': 4.036e-03,
+    'ab_near_fp32_delta_0.0001_0.001': 9.020e-02,
+    'ab_near_fp32_delta_1e-05_0.0001': 5.313e-02,
+    'ab_near_fp32_delta_1e-06_1e-06': 1.700e-03,
+    'ab_prior_bf16x3': 8.620e-03,
+    'ab_prior_fp16x3': 4.736e-02,
+    'ab_prior_fp32_delta': 9.645e-02,
+    'ab_prior_fp32_direct': 1.538e-01,
+    'ab_serve_noalloc_vs_direct': 0.000e+00,
+    'after_timeout_fp16x3': 1.434e-02,
+    'autotune_fp16x3': 1.282e-02,
+    'graph_fp16x3': 9.261e-03,
+    'graph_fp32_delta': 3.277e-02,
+    'graph_multi_fp16x3': 1.822e-02,
+    'host_call_fp16x3': 9.646e-03,
+    'host_call_fp32_delta': 3.236e-02,
+    'invalid_fp16x3': 1.039e-02,
+    'invalid_fp32_delta': 3.236e-02,
+    'invalid_fp32_direct': 1.450e-01,
+    'limits_fp32_delta': 5.041e-02,
+    'max_shape_bf16x3': 2.067e-03,
+    'max_shape_fp16x3': 3.456e-02,
+    'max_shape_fp32_delta': 5.763e-02,
+    'max_shape_fp32_direct': 9.241e-03,
+    'multi_fp16x3': 1.876e-02,
+    'multi_fp32_delta': 2.970e-02,
+    'multi_fp32_direct': 1.234e-02,
+    'near_abs_fp16x3_0.0001': 2.489e-01,
+    'near_abs_fp16x3_1e-05': 4.268e-02,
+    'near_abs_fp16x3_1e-06': 1.052e-02,
+    'near_abs_fp32_delta_0.0001': 6.929e-01,
+    'near_abs_fp32_delta_1e-05': 5.839e-02,
+    'near_abs_fp32_delta_1e-06': 4.844e-03,
+    'near_bf16x3_0.0001': 3.213e-03,
+    'near_bf16x3_1e-05': 2.011e-03,
+    'near_bf16x3_1e-06': 9.085e-04,
+    'near_fp16x3_0.0001': 4.325e-03,
+    'near_fp16x3_1e-05': 3.881e-03,
+    'near_fp16x3_1e-06': 4.448e-03,
+    'near_fp32_delta_0.0001': 3.151e-02,
+    'near_fp32_delta_1e-05': 1.571e-02,
+    'near_fp32_delta_1e-06': 3.687e-03,
+    'noalloc_fp16x3': 9.475e-03,
+    'noise_1_500': 3.383e-01,
+    'noise_2_500': 5.206e-02,
+    'noise_30100_128': 2.880e-03,
+    'noise_4097_64': 5.209e-04,
+    'noise_51_2000': 3.886e-02,
+    'noise_through_likelihood_fp16x3': 6.235e-04,
+    'noise_through_likelihood_fp32_delta': 1.938e-04,
+    'serve_mixed_fp16x3': 2.098e-02,
+    'simt_small_fp32_delta': 3.475e-02,
+    'simt_small_fp32_direct': 8.179e-02,
+    'simt_w1_fp32_delta': 4.148e-02,
+    'simt_w1_fp32_direct': 5.938e-02,
+    'tc_prior_bf16x3': 8.163e-03,
+    'tc_prior_fp16x3': 2.573e-02,
+    'w1_bf16x3': 2.449e-03,
+    'w1_fp16x3': 6.776e-03,
+    'w1_fp32_delta': 4.148e-02,
+    'w1_fp32_direct': 5.938e-02,
+    'w2_fp16x3': 1.165e-02,
+    'w2_fp32_direct': 3.936e-02,
+    'w3_graph_fp16x3': 1.466e-02,
+    'w3_near_0.0001': 3.439e-03,
+    'w3_near_1e-05': 7.813e-03,
+    'w3_near_1e-06': 6.956e-03,
+    'w3_near_abs_1e-05': 3.493e-01,
+    'w3_near_abs_1e-06': 9.393e-02,
+    'w4_full_multi': 1.652e-02,
+    'w5_served_mix': 1.541e-02,
+}
+
+
+def check_logl(family, got, want, tol, label=""):
+    """Assert |got - want| <= tol element-wise and max(err / tol) under the
+    family's regression ceiling; returns max(err / tol)."""
+    from conftest import report
+    got, want = np.asarray(got, dtype=np.float64), np.asarray(want, dtype=np.float64)
+    err = np.abs(got - want)
+    tol = np.broadcast_to(np.asarray(tol, dtype=np.float64), err.shape)
+    ratio = float(np.max(err / tol)) if err.size else 0.0
+    report("ceiling:" + family, max_err_over_tol=ratio, label=label, max_abs=float(err.max()) if err.size else 0.0)
+    assert np.all(err <= tol), fmt_err(f"{family} {label}", got, want, tol)
+    if os.environ.get("FG21_CEILING_COLLECT"):
+        return ratio
+    assert family in MEASURED_ERR_OVER_TOL, f"no regression ceiling recorded for {family}"
+    measured = MEASURED_ERR_OVER_TOL[family]
+    ceil = CEILING_FACTOR * measured
+    assert ratio <= ceil, (f"{family} {label}: worst err/tol {ratio:.3e} above the regression ceiling {ceil:.3e} "
+                           f"({CEILING_FACTOR:g} x the {measured:.3e} measured)")
+    return ratio
 
 
 def fmt_err(name, got, want, tol):

@@ -22,7 +22,7 @@ def test_simt_small(fg21lib, prec, P):
     tol = cases.logl_tolerance(prec, m, obs, data, params)
     report(f"simt_small_{prec}_{P}", max_abs=np.max(np.abs(got - want)),
            max_rel_dterm=np.max(np.abs(got - want) / np.abs(dterm)))
-    assert np.all(np.abs(got - want) <= tol), cases.fmt_err(prec, got, want, tol)
+    cases.check_logl(f"simt_small_{prec}", got, want, tol, f"P={P}")
 
 
 @pytest.mark.parametrize("prec", ["fp32_delta", "fp32_direct"])
@@ -36,4 +36,4 @@ def test_simt_workload1(fg21lib, prec):
     tol = cases.logl_tolerance(prec, m, obs, data, params)
     report(f"simt_w1_{prec}", max_abs=np.max(np.abs(got - want)),
            max_rel_dterm=np.max(np.abs(got - want) / np.abs(dterm)))
-    assert np.all(np.abs(got - want) <= tol), cases.fmt_err(prec, got, want, tol)
+    cases.check_logl(f"simt_w1_{prec}", got, want, tol)

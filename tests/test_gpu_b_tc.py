@@ -36,7 +36,7 @@ def test_tc_prior_draws(fg21lib, shape, prec):
     tol = cases.logl_tolerance(prec, m, obs, data, params)
     report(f"tc_prior_{prec}_{shape}", max_abs=np.max(np.abs(got - want)),
            max_rel_dterm=np.max(np.abs(got - want) / np.abs(dterm)))
-    assert np.all(np.abs(got - want) <= tol), cases.fmt_err(prec, got, want, tol)
+    cases.check_logl(f"tc_prior_{prec}", got, want, tol, str(shape))
 
 
 @pytest.mark.parametrize("prec", ["fp16x3", "fp32_delta", "fp32_direct", "bf16x3"])
@@ -56,10 +56,10 @@ def test_near_posterior(fg21lib, prec, dbeta):
     report(f"near_post_{prec}_{dbeta}", max_abs=err.max(), max_chi2_red=red.max(), min_chi2_red=red.min())
     if prec in ("fp16x3", "fp32_delta"):
         near = red <= 10
-        assert np.all(err[near] <= 1e-2), cases.fmt_err(prec, got[near], want[near], 1e-2)
+        cases.check_logl(f"near_abs_{prec}_{dbeta}", got[near], want[near], 1e-2)
     tol = cases.logl_tolerance(prec, m, obs, data, pts)
     if prec != "fp32_direct":
-        assert np.all(err <= tol), cases.fmt_err(prec, got, want, tol)
+        cases.check_logl(f"near_{prec}_{dbeta}", got, want, tol)
 
 
 @pytest.mark.parametrize("prec", ["fp16x3", "bf16x3", "fp32_delta", "fp32_direct"])
@@ -76,7 +76,7 @@ def test_model_temperature_prior_draws(fg21lib, prec):
     tol = 1e-3 + cases.REL_T[prec] * scale
     err = np.abs(got - want)
     report(f"T_model_prior_{prec}", max_abs=err.max(), max_rel_scale=np.max(err / scale))
-    assert np.all(err <= tol), cases.fmt_err(prec, got, want, tol)
+    cases.check_logl(f"T_model_prior_{prec}", got, want, tol)
 
 
 @pytest.mark.parametrize("prec", ["fp16x3", "fp32_delta", "fp32_direct", "bf16x3"])
@@ -95,7 +95,7 @@ def test_model_temperature_near_posterior(fg21lib, prec, dbeta):
     err = np.abs(got - want)
     report(f"T_model_near_{prec}_{dbeta}", max_abs=err.max())
     if prec != "fp32_direct":
-        assert err.max() <= 1e-3, f"{prec}: max |dT| = {err.max():.3e} K"
+        cases.check_logl(f"T_model_near_{prec}_{dbeta}", got, want, 1e-3)
 
 
 def test_invalid_points(fg21lib):
@@ -115,7 +115,7 @@ def test_invalid_points(fg21lib):
         assert fg21lib.fg21_last_invalid_count() == 5
         good = [0, 2, 4, 6, 9]
         want, dterm = cases.expected(m, obs, data, params[good])
-        assert np.all(np.abs(got[good] - want) <= cases.logl_tolerance(prec, m, obs, data, params[good]))
+        cases.check_logl(f"invalid_{prec}", got[good], want, cases.logl_tolerance(prec, m, obs, data, params[good]))
 
 
 def test_empty_batch_and_errors(fg21lib):
@@ -142,7 +142,7 @@ def test_workload1_all_precisions(fg21lib):
         tol = cases.logl_tolerance(prec, m, obs, data, params)
         report(f"w1_{prec}", max_abs=np.max(np.abs(got - want)),
                max_rel_dterm=np.max(np.abs(got - want) / np.abs(dterm)))
-        assert np.all(np.abs(got - want) <= tol), cases.fmt_err(prec, got, want, tol)
+        cases.check_logl(f"w1_{prec}", got, want, tol)
 
 
 def test_workload2_full(fg21lib):
@@ -156,7 +156,7 @@ def test_workload2_full(fg21lib):
         tol = cases.logl_tolerance(prec, m, obs, data, params)
         report(f"w2_{prec}", max_abs=np.max(np.abs(got - want)),
                max_rel_dterm=np.max(np.abs(got - want) / np.abs(dterm)))
-        assert np.all(np.abs(got - want) <= tol), cases.fmt_err(prec, got, want, tol)
+        cases.check_logl(f"w2_{prec}", got, want, tol)
 
 
 def test_workload3_benchmark_configuration_sampled(fg21lib):
@@ -186,7 +186,7 @@ def test_workload3_benchmark_configuration_sampled(fg21lib):
     err = np.abs(got[idx] - want)
     report("w3_graph_sampled", max_abs=err.max(), max_rel_dterm=np.max(err / np.abs(dterm)),
            max_err_over_tol=np.max(err / tol))
-    assert np.all(err <= tol), cases.fmt_err("w3", got[idx], want, tol)
+    cases.check_logl("w3_graph_fp16x3", got[idx], want, tol)
     assert np.all(np.isfinite(got))
 
 
@@ -214,7 +214,7 @@ def test_maximum_shapes(fg21lib, shape):
         got = fg21lib.fg21_loglike_batch(model, params, prec)
         tol = cases.logl_tolerance(prec, m, obs, data, params)
         report(f"max_shape_{prec}_N{N}_T{T}", max_err_over_tol=np.max(np.abs(got - want) / tol))
-        assert np.all(np.abs(got - want) <= tol), cases.fmt_err(prec, got, want, tol)
+        cases.check_logl(f"max_shape_{prec}", got, want, tol, f"N{N}_T{T}")
     model.close()
 
 
@@ -230,24 +230,24 @@ def test_limits_refused(fg21lib):
     # the SIMT forms take N = 63
     got = fg21lib.fg21_loglike_batch(model, params, "fp32_delta")
     want, _ = cases.expected(m, obs, data, params)
-    assert np.all(np.abs(got - want) <= cases.logl_tolerance("fp32_delta", m, obs, data, params))
+    cases.check_logl("limits_fp32_delta", got, want, cases.logl_tolerance("fp32_delta", m, obs, data, params))
     model.close()
     with pytest.raises(fg21lib.Fg21Error) as e:
         fg21lib.fg21_build_regions(sky, obs, 127)
     assert e.value.code == fg21lib.FG21_E_ARG
 
 
-@pytest.mark.parametrize("dbeta", [1e-6, 1e-5])
-def test_workload3_near_posterior_sampled(fg21lib, dbeta):
-    """The benchmark's sky, model and launch configuration (graph replay of 16384
-    points) in the nested-sampling regime: data from the 24-region model at a
-    truth plus 25 mK noise, points within dbeta in beta of it; every 64th logL
-    (256 points the oracle evaluates one by one) is checked.  In the posterior
-    bulk (dbeta = 1e-6, chi2/(F T) about 1.06) the absolute 1e-2 nats bound
-    holds.  At dbeta = 1e-5 (chi2/(F T) up to 7, some 1e5 nats below the peak)
-    the split-FP16 error grows with the departure from the batch reference
-    summed over the 30100 cells and is held to the derived bound; its size is
-    recorded."""
+_W3_NEAR = {}
+
+
+def _w3_near(fg21lib, dbeta):
+    """The benchmark's sky, model and launch configuration (graph replay of
+    16384 points) in the nested-sampling regime: data from the 24-region model
+    at a truth plus 25 mK noise, points within dbeta in beta of it; every 64th
+    logL (256 points the oracle evaluates one by one) with the oracle's value,
+    chi2 / (F T) and the derived tolerance.  Computed once per dbeta."""
+    if dbeta in _W3_NEAR:
+        return _W3_NEAR[dbeta]
     torch = pytest.importorskip("torch")
     wl, sky, obs, m, _, _ = cases.workload_case(3)
     truth, data, pts = cases.near_posterior(m, obs, dbeta, wl.P)
@@ -261,14 +261,55 @@ def test_workload3_near_posterior_sampled(fg21lib, dbeta):
     assert g.sync_status(s) == 0
     got = d_l.cpu().numpy()
     g.close()
+    model.close()
     idx = np.arange(0, wl.P, 64)
     want, dterm = cases.expected(m, obs, data, pts[idx])
-    err = np.abs(got[idx] - want)
     red = 2 * dterm / (obs.F * obs.T)
     tol = cases.logl_tolerance("fp16x3", m, obs, data, pts[idx])
+    _W3_NEAR[dbeta] = (got[idx], want, red, tol)
+    return _W3_NEAR[dbeta]
+
+
+@pytest.mark.parametrize("dbeta", [1e-6, 1e-5, 1e-4])
+def test_workload3_near_posterior_sampled(fg21lib, dbeta):
+    """At the benchmark size, near the posterior: the derived tolerance at
+    every sampled point, and the absolute 1e-2 nats bound wherever chi2 / (F T)
+    <= 10 for dbeta = 1e-6 (chi2 / (F T) about 1.06) and 1e-5 (up to 7)."""
+    got, want, red, tol = _w3_near(fg21lib, dbeta)
+    err = np.abs(got - want)
+    near = red <= 10
     report(f"w3_near_posterior_sampled_{dbeta}", max_abs=err.max(), max_chi2_red=red.max(),
-           min_chi2_red=red.min(), max_err_over_tol=np.max(err / tol))
-    assert np.all(err <= tol), cases.fmt_err("w3 near", got[idx], want, tol)
-    if dbeta <= 1e-6:
-        assert np.all(err <= 1e-2), cases.fmt_err("w3 bulk", got[idx], want, 1e-2)
-    model.close()
+           min_chi2_red=red.min(), n_near=near.sum(), max_abs_near=err[near].max() if near.any() else 0.0,
+           max_err_over_tol=np.max(err / tol))
+    cases.check_logl(f"w3_near_{dbeta}", got, want, tol)
+    assert near.any()
+    if dbeta <= 1e-5:
+        cases.check_logl(f"w3_near_abs_{dbeta}", got[near], want[near], 1e-2)
+
+
+@pytest.mark.xfail(strict=True, reason="known gap: at dbeta = 1e-4 the 80 of 256 sampled points whose departures "
+                                       "cancel to chi2/(F T) <= 10 reach |dlogL| = 1.8e-2 (GB300): the FP32 weights "
+                                       "and the accumulator's rounding toward zero of departure-sized partial sums")
+def test_workload3_near_posterior_absolute_bound_dbeta_1e_4(fg21lib):
+    """The absolute 1e-2 nats bound at dbeta = 1e-4 wherever chi2 / (F T) <=
+    10.  Expected to fail (strict: a pass means the gap closed and the mark must
+    go).  There the points' departures from the batch reference are ~10 times
+    their residuals and cancel across the 24 regions; FP32 weights alone
+    (rounded once per point, region and channel, and so coherent over the 100
+    LST bins) leave ~1.1e-2, and the FP32 accumulator's rounding toward zero of
+    departure-sized partial sums adds the rest.  The regression ceiling of this
+    case is held by test_workload3_near_posterior_sampled[0.0001]."""
+    got, want, red, tol = _w3_near(fg21lib, 1e-4)
+    near = red <= 10
+    assert near.any()
+    assert np.all(np.abs(got[near] - want[near]) <= 1e-2)
+
+
+def test_workload3_near_posterior_dbeta_1e_4_recorded(fg21lib):
+    """The absolute error at dbeta = 1e-4 where chi2 / (F T) <= 10 stays below
+    3e-2 nats: a regression ceiling of 1.7x the 1.8e-2 measured on a GB300."""
+    got, want, red, tol = _w3_near(fg21lib, 1e-4)
+    near = red <= 10
+    err = np.abs(got[near] - want[near])
+    report("w3_near_abs_1e-4_recorded", max_abs_near=err.max(), n_near=near.sum())
+    assert err.max() <= 3e-2, f"max |dlogL| {err.max():.3e} at dbeta = 1e-4, chi2/(F T) <= 10"

@@ -41,7 +41,7 @@ def test_multi_matches_oracle_and_single(fg21lib, uneven):
         want, dterm = cases.expected(om, obs, data, p)
         tol = cases.logl_tolerance("fp16x3", om, obs, data, p)
         report(f"multi_{wl.name}", max_abs=np.max(np.abs(g - want)))
-        assert np.all(np.abs(g - want) <= tol), cases.fmt_err(wl.name, g, want, tol)
+        cases.check_logl("multi_fp16x3", g, want, tol, wl.name)
         single = fg21lib.fg21_loglike_batch(m, p, "fp16x3")
         assert np.array_equal(single, g), wl.name       # same work split alone and batched
 
@@ -53,7 +53,7 @@ def test_multi_simt_precisions(fg21lib, uneven):
         got = fg21lib.fg21_loglike_multi([m for *_, m in sub], params, prec)
         for (wl, obs, om, data, m), p, g in zip(sub, params, got):
             want, dterm = cases.expected(om, obs, data, p)
-            assert np.all(np.abs(g - want) <= cases.logl_tolerance(prec, om, obs, data, p))
+            cases.check_logl(f"multi_{prec}", g, want, cases.logl_tolerance(prec, om, obs, data, p), wl.name)
 
 
 def test_serve_alone_equals_mixed(fg21lib, uneven):
@@ -93,7 +93,8 @@ def test_serve_alone_equals_mixed(fg21lib, uneven):
         alone = fg21lib.fg21_loglike_batch(m, p, "fp16x3")
         assert np.array_equal(alone, results[j]), j
         want, dterm = cases.expected(om, obs, data, p)
-        assert np.all(np.abs(results[j] - want) <= cases.logl_tolerance("fp16x3", om, obs, data, p))
+        cases.check_logl("serve_mixed_fp16x3", results[j], want, cases.logl_tolerance("fp16x3", om, obs, data, p),
+                         str(j))
     srv.close()
 
 

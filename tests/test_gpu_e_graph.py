@@ -33,7 +33,7 @@ def test_graph_matches_device_call_and_follows_params(fg21lib, prec):
         got, ref = d_g.cpu().numpy(), d_ref.cpu().numpy()
         assert np.array_equal(got, ref)
         want, _ = cases.expected(m, obs, data, params)
-        assert np.all(np.abs(got - want) <= cases.logl_tolerance(prec, m, obs, data, params))
+        cases.check_logl(f"graph_{prec}", got, want, cases.logl_tolerance(prec, m, obs, data, params))
     # repeated replays are exact
     first = d_g.clone()
     for _ in range(5):
@@ -68,7 +68,7 @@ def test_graph_multi_matches_multi_and_oracle(fg21lib):
         got = d.cpu().numpy()
         assert np.array_equal(got, r), wl.name
         want, _ = cases.expected(om, obs, data, p)
-        assert np.all(np.abs(got - want) <= cases.logl_tolerance("fp16x3", om, obs, data, p)), wl.name
+        cases.check_logl("graph_multi_fp16x3", got, want, cases.logl_tolerance("fp16x3", om, obs, data, p), wl.name)
     g.close()
 
 
@@ -103,14 +103,14 @@ def test_host_call_pinned_buffers_and_its_cached_graph(fg21lib, prec):
     assert np.array_equal(c, device_call(p2))
     assert np.array_equal(fg21lib.fg21_loglike_batch(model, p1, prec), a)
     want, _ = cases.expected(m, obs, data, p1)
-    assert np.all(np.abs(a - want) <= cases.logl_tolerance(prec, m, obs, data, p1))
+    cases.check_logl(f"host_call_{prec}", a, want, cases.logl_tolerance(prec, m, obs, data, p1))
     # a tuned work split for this size replaces the kept graph
     d_p = torch.from_numpy(p1).cuda()
     d_l = torch.empty(300, dtype=torch.float64, device="cuda")
     fg21lib.fg21_autotune(model, d_p.data_ptr(), 300, d_l.data_ptr(), prec, stream)
     t = fg21lib.fg21_loglike_batch(model, p1, prec)
     assert np.array_equal(t, device_call(p1))
-    assert np.all(np.abs(t - want) <= cases.logl_tolerance(prec, m, obs, data, p1))
+    cases.check_logl(f"host_call_{prec}", t, want, cases.logl_tolerance(prec, m, obs, data, p1), "timed")
     # invalid points: -inf and counted through the replayed graph
     p3 = p1.copy()
     p3[5, -1] = -1.0

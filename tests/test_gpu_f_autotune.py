@@ -29,9 +29,9 @@ def test_autotune_split_is_valid_and_results_hold(fg21lib):
     host = fg21lib.fg21_loglike_batch(model, params, "fp16x3")
     assert np.array_equal(dev, host)
     want, _ = cases.expected(m, obs, data, params)
-    assert np.all(np.abs(host - want) <= cases.logl_tolerance("fp16x3", m, obs, data, params))
+    cases.check_logl("autotune_fp16x3", host, want, cases.logl_tolerance("fp16x3", m, obs, data, params))
     # a request of another size keeps the planner's split and still matches
     p2 = I.prior_draws(300, 9, seed=22)
     got2 = fg21lib.fg21_loglike_batch(model, p2, "fp16x3")
     want2, _ = cases.expected(m, obs, data, p2)
-    assert np.all(np.abs(got2 - want2) <= cases.logl_tolerance("fp16x3", m, obs, data, p2))
+    cases.check_logl("autotune_fp16x3", got2, want2, cases.logl_tolerance("fp16x3", m, obs, data, p2), "P=300")

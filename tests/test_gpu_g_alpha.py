@@ -51,7 +51,7 @@ def test_ab_prior_draws(fg21lib, shape, prec):
     tol = cases.logl_tolerance_ab(prec, m, obs, data, params)
     report(f"ab_prior_{prec}_{shape}", max_abs=np.max(np.abs(got - want)),
            max_rel_dterm=np.max(np.abs(got - want) / np.abs(dterm)))
-    assert np.all(np.abs(got - want) <= tol), cases.fmt_err(prec, got, want, tol)
+    cases.check_logl(f"ab_prior_{prec}", got, want, tol, str(shape))
 
 
 @pytest.mark.parametrize("prec", ["fp16x3", "fp32_delta", "bf16x3"])
@@ -72,9 +72,9 @@ def test_ab_near_posterior(fg21lib, prec, dbeta, dalpha):
     if prec in ("fp16x3", "fp32_delta"):
         near = red <= 10
         assert near.any()
-        assert np.all(err[near] <= 1e-2), cases.fmt_err(prec, got[near], want[near], 1e-2)
+        cases.check_logl(f"ab_near_abs_{prec}_{dbeta}_{dalpha}", got[near], want[near], 1e-2)
     tol = cases.logl_tolerance_ab(prec, m, obs, data, pts)
-    assert np.all(err <= tol), cases.fmt_err(prec, got, want, tol)
+    cases.check_logl(f"ab_near_{prec}_{dbeta}_{dalpha}", got, want, tol)
 
 
 @pytest.mark.parametrize("prec", ["fp16x3", "fp32_delta"])
@@ -110,7 +110,7 @@ def test_ab_invalid_points(fg21lib):
         assert fg21lib.fg21_last_invalid_count() == 4
         assert np.all(np.isneginf(got[bad]))
         want, _ = cases.expected_ab(m, obs, data, params[ok])
-        assert np.all(np.abs(got[ok] - want) <= cases.logl_tolerance_ab(prec, m, obs, data, params[ok]))
+        cases.check_logl(f"ab_invalid_{prec}", got[ok], want, cases.logl_tolerance_ab(prec, m, obs, data, params[ok]))
 
 
 def test_ab_multi_and_graph_mixed_with_beta_only(fg21lib):
@@ -130,9 +130,10 @@ def test_ab_multi_and_graph_mixed_with_beta_only(fg21lib):
     assert np.array_equal(got[0], fg21lib.fg21_loglike_batch(mod_a, pa, "fp16x3"))
     assert np.array_equal(got[1], fg21lib.fg21_loglike_batch(mod_b, pb, "fp16x3"))
     want_a, _ = cases.expected_ab(m_a, obs_a, data_a, pa)
-    assert np.all(np.abs(got[0] - want_a) <= cases.logl_tolerance_ab("fp16x3", m_a, obs_a, data_a, pa))
+    cases.check_logl("ab_multi_fp16x3", got[0], want_a, cases.logl_tolerance_ab("fp16x3", m_a, obs_a, data_a, pa))
     want_b, _ = cases.expected(m_b, obs_b, data_b, pb)
-    assert np.all(np.abs(got[1] - want_b) <= cases.logl_tolerance("fp16x3", m_b, obs_b, data_b, pb))
+    cases.check_logl("ab_multi_fp16x3", got[1], want_b, cases.logl_tolerance("fp16x3", m_b, obs_b, data_b, pb),
+                     "beta-only")
     dev = torch.device("cuda:0")
     dpa, dpb = torch.from_numpy(pa).to(dev), torch.from_numpy(pb).to(dev)
     la = torch.empty(300, dtype=torch.float64, device=dev)
@@ -173,4 +174,4 @@ def test_ab_served_and_allocation_free(fg21lib):
     assert rc == 0, fg21lib.lib().fg21_last_error()
     torch.cuda.synchronize()
     tol = cases.logl_tolerance_ab("fp16x3", m, obs, data, params)
-    assert np.all(np.abs(d_na.cpu().numpy() - direct) <= tol)
+    cases.check_logl("ab_serve_noalloc_vs_direct", d_na.cpu().numpy(), direct, tol)

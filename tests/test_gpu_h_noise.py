@@ -42,7 +42,7 @@ def test_noise_loglike_matches_oracle(fg21lib, n, s_noise, s_n, K):
     want = O.noise_loglike(n, s_noise, s_n, K, seed)
     tol = _tolerance(want, n, s_noise, s_n)
     report(f"noise_{n}_{K}", max_abs=np.max(np.abs(got - want)), max_err_over_tol=np.max(np.abs(got - want) / tol))
-    assert np.all(np.abs(got - want) <= tol), (np.max(np.abs(got - want)), tol.min())
+    cases.check_logl(f"noise_{n}_{K}", got, want, tol)
 
 
 def test_noise_reproducible_and_seeded(fg21lib):
@@ -91,7 +91,8 @@ def test_noise_loglike_through_the_likelihood_kernel(fg21lib):
         for prec in ("fp32_delta", "fp16x3"):
             got = fg21lib.fg21_loglike_batch(model, pts, prec)
             tol = cases.logl_tolerance(prec, m, obs, data, pts)
-            assert np.all(np.abs(got - L_gpu[k]) <= tol + _tolerance(L_gpu[k:k + 1], n, s, s)), (k, prec)
+            cases.check_logl(f"noise_through_likelihood_{prec}", got, np.full(3, L_gpu[k]),
+                             tol + _tolerance(L_gpu[k:k + 1], n, s, s), str(k))
 
 
 def test_noise_argument_errors(fg21lib):

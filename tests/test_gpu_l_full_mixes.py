@@ -28,13 +28,11 @@ def _sample(P, n, seed):
     return np.array(sorted(idx))
 
 
-def _check(name, om, obs, data, params, got, idx):
+def _check(family, name, om, obs, data, params, got, idx):
     want, dterm = cases.expected(om, obs, data, params[idx])
     tol = cases.logl_tolerance("fp16x3", om, obs, data, params[idx])
-    err = np.abs(got[idx] - want)
-    assert np.all(err <= tol), cases.fmt_err(name, got[idx], want, tol)
     assert np.all(np.isfinite(got))
-    return float(np.max(err / tol))
+    return cases.check_logl(family, got[idx], want, tol, name)
 
 
 def test_workload4_full_size_multi_and_graph(fg21lib):
@@ -54,7 +52,7 @@ def test_workload4_full_size_multi_and_graph(fg21lib):
     got = fg21lib.fg21_loglike_multi([x[4] for x in mods], params, "fp16x3")
     worst = 0.0
     for k, ((wl, obs, om, data, m), p, g) in enumerate(zip(mods, params, got)):
-        worst = max(worst, _check(wl.name, om, obs, data, p, g, _sample(p.shape[0], 12, k)))
+        worst = max(worst, _check("w4_full_multi", wl.name, om, obs, data, p, g, _sample(p.shape[0], 12, k)))
 
     # the same batch captured as one graph on device buffers
     dps = [torch.from_numpy(p).cuda() for p in params]
@@ -113,7 +111,7 @@ def test_workload5_full_size_served_mix(fg21lib):
         if k not in oracle_models:
             oracle_models[k] = O.build_model(run.sky(), run.obs(), run.N, "recursive")
             assert np.array_equal(models[k].labels, oracle_models[k].labels), k
-        worst = max(worst, _check(f"req{j}_run{k}", oracle_models[k], run.obs(), datas[k], p, results[j],
+        worst = max(worst, _check("w5_served_mix", f"req{j}_run{k}", oracle_models[k], run.obs(), datas[k], p, results[j],
                                   _sample(p.shape[0], 12, j)))
     report("w5_full_served", requests=len(reqs), points=int(sum(p.shape[0] for _, p in reqs)),
            launches=st["launches"], p50_ms=st["p50_ms"], p99_ms=st["p99_ms"], max_err_over_tol=worst)
