@@ -86,6 +86,8 @@ struct ReqDesc {
     int G, ch_per_group;         // channel groups per 128-point tile
     int cpg_hint;                // channels per group chosen by the autotuner for this size (0 = model)
     int n_part;                  // partial sums per point (G on the SIMT forms, 2G on the tensor path)
+    int simt_tc;                 // SIMT forms: t-columns staged per round (128, or 64 / 32 where the
+                                 // double-buffered slabs of a large N would not fit shared memory)
     int n_tiles;                 // ceil(P / 128)
     int n_stat_blocks;           // ceil(P / STAT_BLOCK)
     int64_t item_begin;          // first global work-item id of this request
@@ -144,6 +146,12 @@ cudaError_t launch_prep(const ReqDesc *h_reqs, const ReqDesc *d_reqs, int n_reqs
                         int max_stat_blocks, int max_F_chunks, int max_tiles, cudaStream_t stream);
 cudaError_t launch_simt(const ReqDesc *h_reqs, const ReqDesc *d_reqs, int n_reqs, int precision,
                         cudaStream_t stream);
+// Blocks of the SIMT kernel of `precision` that one SM holds at once for a
+// request shape (the CUDA occupancy calculator, cached per device and shape),
+// and the t-chunk width that shape stages (the widest of 128, 64, 32 whose
+// shared memory fits a block).
+int simt_blocks_per_sm(int N, int Nb, int Na, int tc, int precision);
+int simt_chunk_width(int N, int Nb, int Na);
 cudaError_t launch_reduce(const ReqDesc *h_reqs, const ReqDesc *d_reqs, int n_reqs,
                           cudaStream_t stream);
 cudaError_t launch_model_eval(const ReqDesc *h_req, const ReqDesc *d_req, int precision,

@@ -18,6 +18,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "fg21_internal.h"
 
 namespace fg21 {
@@ -124,6 +128,26 @@ __device__ __forceinline__ void cp_async8(void *dst, const void *src) {
                  : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Packed FP32 pairs for the SIMT kernels' FMAs (fma.rn.f32x2: two lanes of
+// round-to-nearest FMA in one instruction).
+__device__ __forceinline__ uint64_t pk2f(float a, float b) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2f(uint64_t v, float &a, float &b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ uint64_t fma2f(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// All but the most recent committed group have completed.
+__device__ __forceinline__ void cp_async_wait_group1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 __device__ __forceinline__ void cp_async4(void *dst, const void *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
@@ -624,13 +648,28 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_tc_kernel(const ReqDesc *__
 }
 
 // ------------------------------------------------------------- SIMT paths
-// One block = 128 points of one request x one channel group.  Each thread owns
-// a point: its weights for the channel go to a private shared-memory column,
-// the channel's model slice is staged in shared memory (broadcast reads), and
-// the residual of each (f, t) is squared and summed in FP32 per channel, the
-// channels folded into a compensated (hi, lo) FP32 pair.
+// One block = 128 points of one request x one channel group (an item).  The
+// block walks its stages (channel, t-chunk of at most SIMT_TC columns) with
+// the next stage's model slab ([N][SIMT_TC]: A for the plain form, wbar A for
+// the reference-subtracted form) and data columns copied into the other half
+// of a double buffer by cp.async while the current one is used.  Per channel
+// the weights of the block's 128 points ([N][128]) and their troughs are
+// formed in shared memory.  Each thread computes register tiles of 4 points x
+// 8 columns: 32 accumulators, each an FMA chain over the regions in ascending
+// order, with the next region's operands (one 16-byte load of weights, two of
+// the slab row, addresses stepped by pointer) loaded while the current
+// region's FMAs issue, two columns per packed FP32x2 FMA; it squares the
+// residuals into its points' sums.  The per-point sums
+// of a channel are combined in a fixed order and folded over the channels into
+// a compensated (hi, lo) FP32 pair.
 constexpr int SIMT_THREADS = 128;
-constexpr int SIMT_TCH = 64;
+constexpr int SIMT_TC = 128;                      // widest t-chunk staged per round (= SIMT_THREADS)
+constexpr int SIMT_PT = 4, SIMT_CT = 8;           // register tile: points x columns
+constexpr int SIMT_PG = TILE_M / SIMT_PT;         // 32 point groups
+constexpr int SIMT_CS = SIMT_THREADS / SIMT_PG;   // 4 column slots
+static_assert(SIMT_PT % 4 == 0 && SIMT_CT == 8, "weights load as float4, slab rows as two float4");
+static_assert(SIMT_TC == SIMT_THREADS, "the slab is staged one column per thread");
+static_assert(SIMT_TC % SIMT_CT == 0, "column blocks tile the t-chunk");
 
 __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
     float y = x - c;
@@ -657,108 +696,183 @@ __device__ __forceinline__ int find_req_by_point(const ReqDesc *__restrict__ req
     return lo;
 }
 
-template <int TCH, bool DIRECT>
-__device__ __forceinline__ float simt_chunk(const float *__restrict__ As, const float *__restrict__ ds,
-                                            const float *__restrict__ wcol, int N, int nvalid, float s21) {
-    float acc[TCH];
-#pragma unroll
-    for (int j = 0; j < TCH; ++j) acc[j] = 0.0f;
-    for (int i = 0; i < N; ++i) {
-        const float w = wcol[i * SIMT_THREADS];
-        const float4 *a4 = reinterpret_cast<const float4 *>(As + i * SIMT_TCH);
-#pragma unroll
-        for (int j = 0; j < TCH / 4; ++j) {
-            float4 a = a4[j];
-            acc[4 * j] = fmaf(a.x, w, acc[4 * j]);
-            acc[4 * j + 1] = fmaf(a.y, w, acc[4 * j + 1]);
-            acc[4 * j + 2] = fmaf(a.z, w, acc[4 * j + 2]);
-            acc[4 * j + 3] = fmaf(a.w, w, acc[4 * j + 3]);
-        }
-    }
-    float q = 0.0f;
-#pragma unroll
-    for (int j = 0; j < TCH; ++j) {
-        if (j < nvalid) {
-            float rr = (ds[j] - s21) - acc[j];
-            q = fmaf(rr, rr, q);
-        }
-    }
-    return q;
+// Shared-memory floats of a SIMT block with N components, Nb spectral-index
+// and Na amplitude parameters, staging tc columns per round: weights
+// [N+1][128] and two slabs [N+1][tc] (one spare row each, read ahead by the
+// last region's load and never used), two sets of data columns [2][2][128],
+// troughs, per-slot sums, amplitudes and spectral indices [Na + Nb][128].
+__host__ __device__ inline size_t simt_smem_floats(int N, int Nb, int Na, int tc) {
+    return (size_t)(N + 1) * TILE_M + 2 * (size_t)(N + 1) * tc + 2 * 2 * SIMT_TC + TILE_M +
+           (size_t)SIMT_CS * TILE_M + (size_t)(Na + Nb) * TILE_M;
 }
+constexpr size_t SIMT_SMEM_MAX = 226 * 1024;      // bytes a block may take (227 KB less the driver's share)
 
 template <bool DIRECT>
 __global__ void __launch_bounds__(SIMT_THREADS) simt_kernel(const ReqDesc *__restrict__ reqs, int n_reqs) {
-    extern __shared__ float smem_f[];
+    extern __shared__ __align__(16) float smem_f[];
     const int64_t item = blockIdx.x;
     const ReqDesc &r = reqs[find_req_by_item(reqs, n_reqs, item)];
     const int64_t lid = item - r.item_begin;
     const int tile = (int)(lid / r.G), g = (int)(lid % r.G);
     const int N = r.N, Nb = r.Nb, Na = r.Na, NP = r.NPF, F = r.F, T = r.T;
     const int f0 = g * r.ch_per_group, f1 = min(F, f0 + r.ch_per_group);
-    float *wcol_all = smem_f;                          // [N][128]
-    float *As = smem_f + N * SIMT_THREADS;             // [N][64]
-    float *ds = As + N * SIMT_TCH;                     // [64]
-    float *acol = ds + SIMT_TCH + threadIdx.x;         // [Na][128]: alpha (direct) or ln(alpha/abar)
-    const int64_t p = (int64_t)tile * TILE_M + threadIdx.x;
+    const size_t slab = (size_t)(N + 1) * r.simt_tc;
+    float *Wsh = smem_f;                              // [N+1][128] weights
+    float *As = Wsh + (size_t)(N + 1) * TILE_M;       // [2][N+1][tc] model slabs
+    float *dcol = As + 2 * slab;                      // [2][2][SIMT_TC]: data (or dref), B
+    float *s21s = dcol + 4 * SIMT_TC;                 // [128] trough of each point
+    float *qp = s21s + TILE_M;                        // [SIMT_CS][128] per-slot point sums
+    float *acol = qp + SIMT_CS * TILE_M;              // [Na][128] alpha (plain) or ln(alpha/abar)
+    float *bcol = acol + (size_t)Na * TILE_M;         // [Nb][128] beta (plain) or beta - bbar
+    const int tid = threadIdx.x;
+    const int64_t p = (int64_t)tile * TILE_M + tid;   // the point whose weights and sums this thread owns
     const bool inb = p < r.P;
+    const int TCr = r.simt_tc;
+    const int nck = (T + TCr - 1) / TCr, S = (f1 - f0) * nck;
+    const float *src = DIRECT ? r.A32 : r.Bp32;
+    const size_t istride = (size_t)F * T;
+
+    // stage st's slab and data columns into buffer st & 1 (column tid of each row)
+    auto prefetch = [&](int st) {
+        const int f = f0 + st / nck, t0 = (st % nck) * TCr;
+        const int tn = min(TCr, T - t0);
+        float *a = As + (size_t)(st & 1) * slab;
+        float *d = dcol + (size_t)(st & 1) * 2 * SIMT_TC;
+        const size_t ft = (size_t)f * T + t0 + tid;
+        if (tid < tn) {
+            for (int i = 0; i < N; ++i) cp_async4(a + (size_t)i * TCr + tid, src + (size_t)i * istride + ft);
+            cp_async4(d + tid, DIRECT ? r.data32 + ft : r.dref32 + ft);
+            if (DIRECT) cp_async4(d + SIMT_TC + tid, r.B32 + ft);
+        } else if (tid < TCr) {
+            for (int i = 0; i < N; ++i) a[(size_t)i * TCr + tid] = 0.0f;
+            d[tid] = 0.0f;
+            d[SIMT_TC + tid] = 0.0f;
+        }
+        cp_async_commit();
+    };
+    if (S > 0) prefetch(0);
+
     const double *th = r.params + (inb ? p : 0) * (NP + 4);
     const float a21 = (float)th[NP], nu21 = (float)th[NP + 1];
     const float inv2s2 = (float)(1.0 / (2.0 * th[NP + 2] * th[NP + 2]));
     for (int i = 0; i < Na; ++i) {
         const double ab = r.beta_bar[Nb + i];
-        acol[i * SIMT_THREADS] = DIRECT ? (float)th[Nb + i] : log1pf((float)(th[Nb + i] - ab) / (float)ab);
+        acol[i * TILE_M + tid] = DIRECT ? (float)th[Nb + i] : log1pf((float)(th[Nb + i] - ab) / (float)ab);
     }
+    for (int j = 0; j < Nb; ++j) bcol[j * TILE_M + tid] = DIRECT ? (float)th[j] : (float)(th[j] - r.beta_bar[j]);
+    Wsh[(size_t)N * TILE_M + tid] = 0.0f;
+    // this thread's register tiles: points 4 pg .. 4 pg + 3, column blocks cs, cs + 4, ...
+    // (a warp holds all 32 point groups of one column slot: broadcast slab loads)
+    const int pg = tid % SIMT_PG, cs = tid / SIMT_PG;
     float qs = 0.0f, qc = 0.0f;
-    float *wcol = wcol_all + threadIdx.x;
-    for (int f = f0; f < f1; ++f) {
-        const float nuf = (float)r.nu[f];
-        const float dnu = nuf - nu21;
-        const float s21 = a21 * expf(-dnu * dnu * inv2s2);
-        if (DIRECT) {
-            const float l2 = (float)(r.L[f] * 1.4426950408889634);   // log2(nu/nu0)
-            for (int i = 0; i < N; ++i) {
-                const float w = exp2f(-(float)th[i % Nb] * l2);
-                wcol[i * SIMT_THREADS] = Na ? acol[(i / Nb) * SIMT_THREADS] * w : w;
+    float q4[SIMT_PT];
+#pragma unroll
+    for (int a = 0; a < SIMT_PT; ++a) q4[a] = 0.0f;
+    for (int st = 0; st < S; ++st) {
+        const int f = f0 + st / nck, ck = st % nck, t0 = ck * TCr;
+        const int tn = min(TCr, T - t0);
+        if (ck == 0) {
+            // the channel's weights and troughs (the previous stage's readers
+            // passed the barrier that ended it)
+            const float nuf = (float)r.nu[f];
+            const float dnu = nuf - nu21;
+            s21s[tid] = a21 * expf(-dnu * dnu * inv2s2);
+            if (DIRECT) {
+                const float l2 = (float)(r.L[f] * 1.4426950408889634);   // log2(nu/nu0)
+                for (int i = 0; i < N; ++i) {
+                    const float w = exp2f(-bcol[(i % Nb) * TILE_M + tid] * l2);
+                    Wsh[i * TILE_M + tid] = Na ? acol[(i / Nb) * TILE_M + tid] * w : w;
+                }
+            } else {
+                const float nL = (float)(-r.L[f]);
+                for (int i = 0; i < N; ++i) {
+                    float y = bcol[(i % Nb) * TILE_M + tid] * nL;
+                    if (Na) y += acol[(i / Nb) * TILE_M + tid];
+                    Wsh[i * TILE_M + tid] = expm1f(y);
+                }
             }
+        }
+        if (st + 1 < S) {
+            prefetch(st + 1);           // buffer (st + 1) & 1 was last read by stage st - 1
+            cp_async_wait_group1();
         } else {
-            const float nL = (float)(-r.L[f]);
+            cp_async_wait_all();
+        }
+        __syncthreads();
+        const float *a_st = As + (size_t)(st & 1) * slab;
+        const float *d_st = dcol + (size_t)(st & 1) * 2 * SIMT_TC;
+        const float tcmb = (float)r.t_cmb;
+        const int ncb = (tn + SIMT_CT - 1) / SIMT_CT;
+        for (int cb = cs; cb < ncb; cb += SIMT_CS) {
+            // accumulator pairs (columns 2k, 2k+1 of one point): packed FP32x2
+            // FMAs, each lane the same round-to-nearest FMA as a scalar one
+            uint64_t acc2[SIMT_PT][SIMT_CT / 2];
+#pragma unroll
+            for (int a = 0; a < SIMT_PT; ++a)
+#pragma unroll
+                for (int c = 0; c < SIMT_CT / 2; ++c) acc2[a][c] = 0ull;
+            const float4 *wp = reinterpret_cast<const float4 *>(Wsh + SIMT_PT * pg);
+            const float4 *ap = reinterpret_cast<const float4 *>(a_st + SIMT_CT * cb);
+            const int wstep = TILE_M / 4, astep = TCr / 4;      // one region, in float4
+            float4 wq[SIMT_PT / 4];
+#pragma unroll
+            for (int k = 0; k < SIMT_PT / 4; ++k) wq[k] = wp[k];
+            float4 a0 = ap[0], a1 = ap[1];
             for (int i = 0; i < N; ++i) {
-                const int j = i % Nb;
-                float y = (float)(th[j] - r.beta_bar[j]) * nL;
-                if (Na) y += acol[(i / Nb) * SIMT_THREADS];
-                wcol[i * SIMT_THREADS] = expm1f(y);
+                // region i + 1's operands (row N is a spare row) while region i's FMAs issue
+                wp += wstep;
+                ap += astep;
+                float4 wn[SIMT_PT / 4];
+#pragma unroll
+                for (int k = 0; k < SIMT_PT / 4; ++k) wn[k] = wp[k];
+                const float4 a0n = ap[0], a1n = ap[1];
+                const uint64_t av[SIMT_CT / 2] = {pk2f(a0.x, a0.y), pk2f(a0.z, a0.w), pk2f(a1.x, a1.y),
+                                                  pk2f(a1.z, a1.w)};
+#pragma unroll
+                for (int a = 0; a < SIMT_PT; ++a) {
+                    const float4 &q = wq[a / 4];
+                    const float wa = (a & 3) == 0 ? q.x : (a & 3) == 1 ? q.y : (a & 3) == 2 ? q.z : q.w;
+                    const uint64_t ww = pk2f(wa, wa);
+#pragma unroll
+                    for (int c = 0; c < SIMT_CT / 2; ++c) acc2[a][c] = fma2f(av[c], ww, acc2[a][c]);
+                }
+#pragma unroll
+                for (int k = 0; k < SIMT_PT / 4; ++k) wq[k] = wn[k];
+                a0 = a0n;
+                a1 = a1n;
+            }
+            float acc[SIMT_PT][SIMT_CT];
+#pragma unroll
+            for (int a = 0; a < SIMT_PT; ++a)
+#pragma unroll
+                for (int c = 0; c < SIMT_CT / 2; ++c) upk2f(acc2[a][c], acc[a][2 * c], acc[a][2 * c + 1]);
+#pragma unroll
+            for (int c = 0; c < SIMT_CT; ++c) {
+                const int t = SIMT_CT * cb + c;
+                if (t < tn) {
+                    const float dv = DIRECT ? d_st[t] - tcmb * d_st[SIMT_TC + t] : d_st[t];
+#pragma unroll
+                    for (int a = 0; a < SIMT_PT; ++a) {
+                        const float rr = (dv - s21s[SIMT_PT * pg + a]) - acc[a][c];
+                        q4[a] = fmaf(rr, rr, q4[a]);
+                    }
+                }
             }
         }
-        float qf = 0.0f;
-        for (int tb = 0; tb < T; tb += SIMT_TCH) {
-            const int nvalid = min(SIMT_TCH, T - tb);
-            __syncthreads();
-            for (int k = threadIdx.x; k < N * SIMT_TCH; k += SIMT_THREADS) {
-                const int i = k / SIMT_TCH, j = k % SIMT_TCH;
-                float v = 0.0f;
-                if (j < nvalid) {
-                    const size_t idx = ((size_t)i * F + f) * T + tb + j;
-                    v = DIRECT ? r.A32[idx] : r.Bp32[idx];
-                }
-                As[k] = v;
-            }
-            for (int j = threadIdx.x; j < SIMT_TCH; j += SIMT_THREADS) {
-                float v = 0.0f;
-                if (j < nvalid) {
-                    const size_t ft = (size_t)f * T + tb + j;
-                    v = DIRECT ? r.data32[ft] - (float)r.t_cmb * r.B32[ft] : r.dref32[ft];
-                }
-                ds[j] = v;
+        if (ck == nck - 1) {
+            // the channel is complete: its per-point sums, combined in slot order
+#pragma unroll
+            for (int a = 0; a < SIMT_PT; ++a) {
+                qp[cs * TILE_M + SIMT_PT * pg + a] = q4[a];
+                q4[a] = 0.0f;
             }
             __syncthreads();
-            if (nvalid > 32)
-                qf += simt_chunk<64, DIRECT>(As, ds, wcol, N, nvalid, s21);
-            else if (nvalid > 16)
-                qf += simt_chunk<32, DIRECT>(As, ds, wcol, N, nvalid, s21);
-            else
-                qf += simt_chunk<16, DIRECT>(As, ds, wcol, N, nvalid, s21);
+            float qf = qp[tid];
+#pragma unroll
+            for (int k = 1; k < SIMT_CS; ++k) qf += qp[k * TILE_M + tid];
+            kahan_add(qs, qc, qf);
         }
-        kahan_add(qs, qc, qf);
+        __syncthreads();                // every read of this stage's buffers is done
     }
     if (inb) r.partials[(size_t)p * r.n_part + g] = make_float2(qs, -qc);
 }
@@ -947,26 +1061,71 @@ cudaError_t launch_prep(const ReqDesc *h_reqs, const ReqDesc *d_reqs, int n_reqs
     return cudaGetLastError();
 }
 
+// The SIMT kernels may use up to the largest dynamic shared memory a block can
+// hold; set once per process (the occupancy query and the launches both use
+// the limit).
+static cudaError_t simt_smem_limit() {
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    std::call_once(once, [] {
+        err = cudaFuncSetAttribute(simt_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        if (err == cudaSuccess)
+            err = cudaFuncSetAttribute(simt_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    });
+    return err;
+}
+
+int simt_chunk_width(int N, int Nb, int Na) {
+    for (int tc = SIMT_TC; tc > 32; tc >>= 1)
+        if (sizeof(float) * simt_smem_floats(N, Nb, Na, tc) <= SIMT_SMEM_MAX) return tc;
+    return 32;
+}
+
+int simt_blocks_per_sm(int N, int Nb, int Na, int tc, int precision) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int, int, int>, int> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    const bool direct = precision == FG21_PREC_FP32_DIRECT;
+    const auto key = std::make_tuple(dev, N, Nb, Na, tc * 2 + (int)direct);
+    std::lock_guard<std::mutex> lk(mu);
+    const auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    const size_t sm = sizeof(float) * simt_smem_floats(N, Nb, Na, tc);
+    int n = 0;
+    cudaError_t e = simt_smem_limit();
+    if (e == cudaSuccess)
+        e = direct ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, simt_kernel<true>, SIMT_THREADS, sm)
+                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, simt_kernel<false>, SIMT_THREADS, sm);
+    if (e != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        n = 1;
+    }
+    cache[key] = n;
+    return n;
+}
+
 cudaError_t launch_simt(const ReqDesc *h_reqs, const ReqDesc *d_reqs, int n_reqs, int precision,
                         cudaStream_t stream) {
     int64_t items = 0;
-    int maxN = 0, maxNa = 0;
+    size_t sm = 0;
     for (int k = 0; k < n_reqs; ++k) {
-        items += (int64_t)h_reqs[k].n_tiles * h_reqs[k].G;
-        maxN = maxN > h_reqs[k].N ? maxN : h_reqs[k].N;
-        maxNa = maxNa > h_reqs[k].Na ? maxNa : h_reqs[k].Na;
+        const ReqDesc &r = h_reqs[k];
+        items += (int64_t)r.n_tiles * r.G;
+        const size_t need = sizeof(float) * simt_smem_floats(r.N, r.Nb, r.Na, r.simt_tc);
+        sm = sm > need ? sm : need;
     }
     if (items == 0) return cudaSuccess;
-    const size_t sm = sizeof(float) * ((size_t)maxN * (SIMT_THREADS + SIMT_TCH) + SIMT_TCH + (size_t)maxNa * SIMT_THREADS);
-    static bool attr_done[2] = {false, false};
-    const bool direct = precision == FG21_PREC_FP32_DIRECT;
-    if (!attr_done[direct]) {
-        cudaError_t e = direct ? cudaFuncSetAttribute(simt_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)
-                               : cudaFuncSetAttribute(simt_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        if (e != cudaSuccess) return e;
-        attr_done[direct] = true;
-    }
-    if (direct)
+    for (int k = 0; k < n_reqs; ++k)
+        if (h_reqs[k].P > 0 && (h_reqs[k].simt_tc < 32 || h_reqs[k].simt_tc > SIMT_TC || h_reqs[k].simt_tc % 32))
+            return cudaErrorInvalidValue;
+    if (sm > SIMT_SMEM_MAX) return cudaErrorInvalidValue;
+    cudaError_t e = simt_smem_limit();
+    if (e != cudaSuccess) return e;
+    if (precision == FG21_PREC_FP32_DIRECT)
         simt_kernel<true><<<(unsigned)items, SIMT_THREADS, sm, stream>>>(d_reqs, n_reqs);
     else
         simt_kernel<false><<<(unsigned)items, SIMT_THREADS, sm, stream>>>(d_reqs, n_reqs);

@@ -141,15 +141,17 @@ static int g_cpg_override() {
     return v;
 }
 
-// Channels per work item: minimise (waves of items over the SMs) x (channels
-// per item + a per-item overhead of about one channel).
-static int choose_channels_per_group(int64_t total_tiles, int F, int num_sms) {
+// Channels per work item: minimise (waves of items over the `slots` items
+// the GPU runs at once) x (channels per item + a per-item overhead of about
+// one channel), with at most max_groups groups.
+static int choose_channels_per_group(int64_t total_tiles, int F, int slots, int max_groups = 1 << 30) {
     if (g_cpg_override() > 0) return std::min(F, g_cpg_override());
     double best = 1e300;
     int best_cpg = F;
     for (int cpg = 1; cpg <= F; ++cpg) {
         int G = (F + cpg - 1) / cpg;
-        double waves = std::ceil((double)total_tiles * G / num_sms);
+        if (G > max_groups) continue;
+        double waves = std::ceil((double)total_tiles * G / slots);
         double cost = waves * (cpg + 1.0);
         if (cost < best - 1e-9) {
             best = cost;
@@ -169,10 +171,21 @@ void plan_request(ReqDesc &r, int precision, int num_sms, int64_t total_tiles) {
     r.Tc_pad = round16(r.Tc);
     r.n_tiles = (int)((r.P + TILE_M - 1) / TILE_M);
     r.n_stat_blocks = (int)((r.P + STAT_BLOCK - 1) / STAT_BLOCK);
-    int cpg = r.cpg_hint > 0 ? std::min(r.F, r.cpg_hint) : choose_channels_per_group(total_tiles, r.F, num_sms);
+    const bool tc = precision == FG21_PREC_FP16X3 || precision == FG21_PREC_BF16X3;
+    r.simt_tc = tc ? 0 : simt_chunk_width(r.N, r.Nb, r.Na);
+    int cpg;
+    if (r.cpg_hint > 0) {
+        cpg = std::min(r.F, r.cpg_hint);
+    } else if (tc) {
+        cpg = choose_channels_per_group(total_tiles, r.F, num_sms);
+    } else {
+        // SIMT blocks are not persistent: the waves are counted in the blocks
+        // the GPU holds at once (at most 32 groups, the reduction's serial row)
+        const int slots = num_sms * simt_blocks_per_sm(r.N, r.Nb, r.Na, r.simt_tc, precision);
+        cpg = choose_channels_per_group(total_tiles, r.F, slots, 32);
+    }
     r.G = (r.F + cpg - 1) / cpg;
     r.ch_per_group = (r.F + r.G - 1) / r.G;
-    const bool tc = precision == FG21_PREC_FP16X3 || precision == FG21_PREC_BF16X3;
     r.n_part = tc ? 2 * r.G : r.G;      // the tensor path splits each point's t-columns over two warps
     r.chi2_scale = tc ? 1.0 + (2.0 / 3.0) * std::ldexp(1.0, -23) : 1.0;
     r.tile_rows = (int64_t)r.Kp * r.Tc_pad / 32;   // 2 splits x Kp x Tc_pad x 2 bytes / 128
