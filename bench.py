@@ -15,7 +15,13 @@ contraction, trough, residual and square (a2-a5), per-point reduction and logL
   direct_call  the same step through fg21_loglike_batch_device every time
   e2e          the same through the host-buffer C-ABI call on page-locked
                buffers (params H2D and logL D2H inside the timed region)
-  fp32_direct  the plain FP32 SIMT kernel on the same device and protocol
+  fp32_direct  the plain FP32 SIMT kernel on the same device and protocol, with
+               its kernel's fraction of the FP32 FMA rate
+  c2, c4       workload 2 (split FP16 against plain FP32 at N = 9, T = 20) and
+               workload 4 (32 uneven models, autotuned, one graph-replayed launch)
+  serve        workload 5: 64 concurrent nested slice-sampling runs feeding the
+               serving loop (p50 / p99 latency, throughput); serve_pool is the
+               loop's capacity and latency on a pool of prior-draw requests
   roofline     dominant kernel (tcgen05 likelihood kernel): algorithmic flops
                (2 N F T per point) / its mean launch time, against the measured
                dense 16-bit tensor peak
@@ -23,9 +29,9 @@ contraction, trough, residual and square (a2-a5), per-point reduction and logL
                bounded sample
   near_posterior  the same step on a batch close to one point (the regime
                of a nested sampler's late iterations)
-  alpha_model, noise_q, occam, small_batch, serve
+  alpha_model, noise_q, occam, small_batch
                the amplitude-mask model, the noise-only likelihood workload,
-               log L_max(N), the 64-point latency case and the serving mix
+               log L_max(N) and the 64-point latency case
 
 `--impl reference` times the FP64 oracle alone (the paper publishes no code to run).
 Multi-GPU: one process per GPU under torchrun, each rank an independent
@@ -65,6 +71,10 @@ def parse():
     ap.add_argument("--no-noise", action="store_true", help="skip the accuracy-criterion (L_noise) line")
     ap.add_argument("--no-occam", action="store_true", help="skip the log L_max(N) line")
     ap.add_argument("--no-small", action="store_true", help="skip the 64-point latency line")
+    ap.add_argument("--no-c2", action="store_true", help="skip the workload-2 line")
+    ap.add_argument("--no-c4", action="store_true", help="skip the workload-4 line")
+    ap.add_argument("--no-ns", action="store_true", help="skip the nested-sampling-driven serving line")
+    ap.add_argument("--ns-seconds", type=float, default=20.0, help="wall time of the nested-sampling serve line")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample budget")
     return ap.parse_args()
 
@@ -322,6 +332,185 @@ def serve_phase(fg21, I, seconds=3.0, n_runs=64):
             "mean_ms_at_half_load": st["mean_ms"], "launches_at_half_load": st["launches"],
             "closed_loop_p50_ms": st_cap["p50_ms"], "closed_loop_p99_ms": st_cap["p99_ms"],
             "build_s": build_s}
+
+
+def c2_phase(fg21, I, flush, stream, K):
+    """Workload 2 (12288-pixel sky, N = 9, F = 151, T = 20 over 6 h, P = 4096
+    prior draws): the split-FP16 tensor-core form and the plain FP32 form on the
+    same device, each with its autotuned work split and replayed from a CUDA
+    graph (L2 flushed between steps), plus each form's kernel time from direct
+    calls."""
+    import torch
+    wl = I.workload(2)
+    sky, obs = wl.sky(), wl.obs()
+    m = fg21.fg21_build_regions(sky, obs, wl.N, wl.scheme, wl.weighting)
+    fg21.fg21_model_set_data(m, fg21.fg21_simulate_data(sky, obs, I.FIDUCIAL_T21, I.NOISE_K, wl.noise()))
+    params = wl.params()
+    P = params.shape[0]
+    d_p = torch.from_numpy(params).cuda()
+    d_l = torch.empty(P, dtype=torch.float64, device="cuda")
+    sptr = stream.cuda_stream
+    out = {"workload": wl.name, "unit": "logL evals/s"}
+    for prec in ("fp16x3", "fp32_direct"):
+        fg21.fg21_autotune(m, d_p.data_ptr(), P, d_l.data_ptr(), prec, sptr)
+        g = fg21.fg21_graph_create(m, d_p.data_ptr(), P, d_l.data_ptr(), prec)
+        for _ in range(3):
+            flush.zero_()
+            g.launch(sptr)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        torch.cuda.synchronize()
+        for a, b in evs:
+            flush.zero_()
+            a.record(stream)
+            g.launch(sptr)
+            b.record(stream)
+        torch.cuda.synchronize()
+        inv = g.sync_status(sptr)
+        g.close()
+        ms = sum(a.elapsed_time(b) for a, b in evs) / K
+        fg21.fg21_model_timing(m, True)
+        for _ in range(max(3, K // 4)):
+            flush.zero_()
+            fg21.fg21_loglike_batch_device(m, d_p.data_ptr(), P, d_l.data_ptr(), prec, sptr)
+        calls, prep_ms, main_ms, red_ms = fg21.fg21_model_timing_totals(m)
+        fg21.fg21_model_timing(m, False)
+        assert inv == 0 and bool(torch.isfinite(d_l).all())
+        out[prec] = {"value": P / (ms * 1e-3), "ms_per_step": ms, "kernel_ms": main_ms / calls,
+                     "alg_tflops": 2.0 * wl.N * wl.F * wl.T * P / (main_ms / calls * 1e-3) / 1e12}
+    out["speedup_fp16x3_over_fp32_direct"] = out["fp16x3"]["value"] / out["fp32_direct"]["value"]
+    m.close()
+    return out
+
+
+def c4_phase(fg21, I, flush, stream, K, pk):
+    """Workload 4: 32 model instances (N ~ U{4..30}, T ~ U{1..60}, P ~
+    U{256..8192}, F = 151, each with its own sky partition and data), every
+    model's work split tuned by fg21_autotune for its batch size, then all 32
+    batches in one persistent launch replayed from a CUDA graph
+    (fg21_graph_create_multi; L2 flushed between steps)."""
+    import torch
+    wls = I.uneven_batch(32)
+    models, dps, dls, Ps = [], [], [], []
+    macs = 0
+    sptr = stream.cuda_stream
+    t0 = time.time()
+    for wl in wls:
+        sky, obs = wl.sky(), wl.obs()
+        m = fg21.fg21_build_regions(sky, obs, wl.N, wl.scheme, wl.weighting)
+        fg21.fg21_model_set_data(m, fg21.fg21_simulate_data(sky, obs, I.FIDUCIAL_T21, I.NOISE_K, wl.noise()))
+        p = wl.params()
+        d_p = torch.from_numpy(p).cuda()
+        d_l = torch.empty(p.shape[0], dtype=torch.float64, device="cuda")
+        models.append(m)
+        dps.append(d_p)
+        dls.append(d_l)
+        Ps.append(p.shape[0])
+        macs += wl.N * wl.F * wl.T * p.shape[0]
+    build_s = time.time() - t0
+    t0 = time.time()
+    for m, d_p, d_l, P in zip(models, dps, dls, Ps):
+        fg21.fg21_autotune(m, d_p.data_ptr(), P, d_l.data_ptr(), "fp16x3", sptr)
+    tune_s = time.time() - t0
+    g = fg21.fg21_graph_create_multi(models, [d.data_ptr() for d in dps], Ps, [d.data_ptr() for d in dls], "fp16x3")
+    for _ in range(3):
+        flush.zero_()
+        g.launch(sptr)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    torch.cuda.synchronize()
+    for a, b in evs:
+        flush.zero_()
+        a.record(stream)
+        g.launch(sptr)
+        b.record(stream)
+    torch.cuda.synchronize()
+    inv = g.sync_status(sptr)
+    g.close()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / K
+    assert inv == 0 and all(bool(torch.isfinite(d).all()) for d in dls)
+    for m in models:
+        m.close()
+    pts = sum(Ps)
+    alg = 2.0 * macs / (ms * 1e-3) / 1e12
+    return {"workload": f"32 models, N 4-30, T 1-60, P 256-8192, F 151 ({pts} points)", "points": pts,
+            "value": pts / (ms * 1e-3), "unit": "logL evals/s", "ms_per_step": ms, "steps": K,
+            "macs_per_s": macs / (ms * 1e-3), "build_regions_s": round(build_s, 3), "autotune_s": round(tune_s, 3),
+            "roofline": {"bound": "tensor", "achieved": alg, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+                         "frac": alg / pk["bf16_tflops"],
+                         "what": "algorithmic 2 N F T P over the whole graph-replayed step (prep and reduction "
+                                 "included), so a lower bound on the tensor kernel's own fraction"},
+            "path": "fg21_graph_create_multi / fg21_graph_launch: one prep, one persistent tensor-core launch "
+                    "and one reduction over all 32 requests; work splits from fg21_autotune per model"}
+
+
+class _StopRun(Exception):
+    pass
+
+
+def ns_serve_phase(fg21, I, seconds=20.0, n_runs=64):
+    """Workload 5 as stated: n_runs concurrent batched nested slice-sampling runs
+    (n_live 500, 128 deletions per iteration, 5 D inner steps; N cycling
+    through 5, 9, 14, 20, 30 and T through 1, 10, 50, each run with its own
+    3072-pixel sky, LST window and simulated data, F = 151) feed the serving
+    loop, one client thread per run.  Every slice round of a run is one
+    request; the runs go on for `seconds` of wall time.  Reports the serving
+    loop's latency percentiles, throughput and launch batching under that load."""
+    from paper_2603_13196_gb300 import ns
+    runs, _ = I.serving_mix(n_runs)
+    srv = fg21.Server(mem_budget_bytes=60 << 30, max_batch_points=65536, max_wait_us=200, max_inflight=2)
+    models, likes = [], []
+    t0 = time.time()
+    for run in runs:
+        sky, obs = run.sky(), run.obs()
+        m = fg21.fg21_build_regions(sky, obs, run.N, "recursive")
+        fg21.fg21_model_set_data(m, fg21.fg21_simulate_data(sky, obs, I.FIDUCIAL_T21, I.NOISE_K, run.noise()))
+        models.append(m)
+        likes.append(ns.ServeLikelihood(fg21, srv, m))
+    build_s = time.time() - t0
+    stop = threading.Event()
+    rounds = [0] * n_runs
+    iters = [0] * n_runs
+    errors = []
+
+    def client(k):
+        prior = ns.region_model_prior(runs[k].N)
+
+        def like(theta):
+            if stop.is_set():
+                raise _StopRun()
+            rounds[k] += 1
+            return likes[k](theta)
+        sampler = ns.NestedSlice(prior, like, n_live=500, num_delete=128, num_inner_steps=5 * prior.dim,
+                                 seed=I.BASE_SEED + k)
+        try:
+            r = sampler.run()
+            iters[k] = r.iterations
+        except _StopRun:
+            pass
+        except Exception as e:          # reported, not hidden
+            errors.append(repr(e))
+
+    ths = [threading.Thread(target=client, args=(k,), daemon=True) for k in range(n_runs)]
+    t_start = time.time()
+    [t.start() for t in ths]
+    time.sleep(seconds)
+    stop.set()
+    [t.join(timeout=60) for t in ths]
+    wall = time.time() - t_start
+    st = fg21.fg21_serve_stats(srv)
+    for lk in likes:
+        lk.close()
+    srv.close()
+    for m in models:
+        m.close()
+    return {"workload": f"{n_runs} concurrent nested slice-sampling runs (n_live 500, 128 deletions, 5 D inner "
+                        "steps), N in {5,9,14,20,30}, T in {1,10,50}, F 151, 3072-pixel skies",
+            "wall_s": round(wall, 2), "requests": st["requests_done"], "points": st["points_done"],
+            "evals_per_s": st["points_done"] / wall, "macs_per_s_server": st["macs_per_s"],
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"], "launches": st["launches"],
+            "mean_points_per_launch": st["points_done"] / max(1, st["launches"]),
+            "rounds_per_run_mean": float(sum(rounds)) / n_runs, "runs_finished": sum(1 for x in iters if x),
+            "client_errors": errors[:3], "build_s": round(build_s, 3),
+            "path": "ns.NestedSlice per run -> ns.ServeLikelihood -> fg21_serve_submit / fg21_serve_wait"}
 
 
 def run_reference(args):
@@ -657,6 +846,8 @@ def main():
 
     pk, pk_kind = peaks()
     alg_flops = 2.0 * N * F * T * P
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = sm_count * 128 * 2 * (clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
     achieved = alg_flops / (res["main_ms"] * 1e-3) / 1e12
     peak = pk["bf16_tflops"]
     kp, tcp = ((N + 2 + 15) // 16) * 16, ((T + 15) // 16) * 16
@@ -687,7 +878,13 @@ def main():
                    "l2": "flushed by a 256 MiB write between timed steps (not timed)",
                    "build_regions_s": round(build_s, 3)},
         "fp32_direct": {"value": P * ws / (direct_ms * 1e-3), "unit": "logL evals/s", "ms_per_step": direct_ms,
-                        "speedup_of_value": (P * ws / (step_ms * 1e-3)) / (P * ws / (direct_ms * 1e-3))},
+                        "speedup_of_value": (P * ws / (step_ms * 1e-3)) / (P * ws / (direct_ms * 1e-3)),
+                        "kernel_ms": direct["main_ms"],
+                        "fp32_pipe": {"bound": "alu", "achieved": alg_flops / (direct["main_ms"] * 1e-3) / 1e12,
+                                      "peak": fp32_peak, "unit": "TFLOP/s",
+                                      "frac": alg_flops / (direct["main_ms"] * 1e-3) / 1e12 / fp32_peak,
+                                      "peak_kind": "derived: SMs x 128 FP32 lanes x 2 flop (one FMA) x the "
+                                                   "median SM clock sampled during the timed region"}},
         "kernels_ms": {"prep": res["prep_ms"], "tc_loglike": res["main_ms"], "reduce": res["reduce_ms"]},
         "direct_call": {"value": P * ws / (call_ms * 1e-3), "unit": "logL evals/s", "ms_per_step": call_ms,
                         "what": "the same step through fg21_loglike_batch_device each time (plan, descriptor "
@@ -717,11 +914,17 @@ def main():
         line["occam"] = occam_phase(fg21, I)
     if rank == 0 and not args.no_small:
         line["small_batch"] = small_batch_phase(fg21, I, stream)
+    if rank == 0 and not args.no_c2:
+        line["c2"] = c2_phase(fg21, I, flush, stream, max(3, args.steps // 4))
+    if rank == 0 and not args.no_c4:
+        line["c4"] = c4_phase(fg21, I, flush, stream, max(3, args.steps // 4), pk)
     if rank == 0 and not args.no_serve:
-        sv = serve_phase(fg21, I)
+        line["serve_pool"] = serve_phase(fg21, I)
+    if rank == 0 and not args.no_ns:
+        sv = ns_serve_phase(fg21, I, seconds=args.ns_seconds)
         line["serve"] = sv
-        line["serve_p50_ms"] = sv["p50_ms_at_half_load"]
-        line["serve_p99_ms"] = sv["p99_ms_at_half_load"]
+        line["serve_p50_ms"] = sv["p50_ms"]
+        line["serve_p99_ms"] = sv["p99_ms"]
     if rank == 0 and not args.no_cpu_baseline:
         cb, _, _ = cpu_baseline(sky, obs, N, params, args.cpu_seconds)
         line["cpu_baseline"] = cb
