@@ -12,7 +12,7 @@
  * runs sequentially in a fixed order, so results do not depend on the thread
  * count.
  *
- * Readings of points the paper leaves open (all listed in the design notes):
+ * Readings of points the paper leaves open (each stated here in full):
  *  - template map: T230 with nu0 = 230 MHz (Sec. 2.1, eq. of the sky
  *    extrapolation), although eqs. forward_model / chromatic_function print
  *    T408;
