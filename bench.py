@@ -456,7 +456,10 @@ def ns_serve_phase(fg21, I, seconds=20.0, n_runs=64):
     loop's latency percentiles, throughput and launch batching under that load."""
     from paper_2603_13196_gb300 import ns
     runs, _ = I.serving_mix(n_runs)
-    srv = fg21.Server(mem_budget_bytes=60 << 30, max_batch_points=65536, max_wait_us=200, max_inflight=2)
+    # the clients block on every round, so the loop launches whatever is pending at
+    # once (no fill window); requests that arrive while launches are in flight
+    # share the next launch
+    srv = fg21.Server(mem_budget_bytes=60 << 30, max_batch_points=65536, max_wait_us=0, max_inflight=2)
     models, likes = [], []
     t0 = time.time()
     for run in runs:
@@ -509,7 +512,7 @@ def ns_serve_phase(fg21, I, seconds=20.0, n_runs=64):
             "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"], "launches": st["launches"],
             "mean_points_per_launch": st["points_done"] / max(1, st["launches"]),
             "rounds_per_run_mean": float(sum(rounds)) / n_runs, "runs_finished": sum(1 for x in iters if x),
-            "client_errors": errors[:3], "build_s": round(build_s, 3),
+            "client_errors": errors[:3], "build_s": round(build_s, 3), "max_wait_us": 0,
             "path": "ns.NestedSlice per run -> ns.ServeLikelihood -> fg21_serve_submit / fg21_serve_wait"}
 
 

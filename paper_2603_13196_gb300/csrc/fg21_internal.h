@@ -178,6 +178,10 @@ cudaError_t launch_tc(const TcLaunch &L, int num_sms, cudaStream_t stream);
 // One CTA whose waits expire by design (status + 4 per-warp waiting times).
 cudaError_t launch_wait_selftest(unsigned *status, unsigned long long *elapsed, cudaStream_t stream);
 constexpr int WAIT_SELFTEST_WARPS = 4;
+// One tcgen05.mma (kind::f16, M = 128, N = 16, K = 16) on device buffers:
+// d = c + a b (a [128][16], b [16][16] F16 bits, c, d [128][16] FP32).
+cudaError_t launch_mma_probe(const uint16_t *a, const uint16_t *b, const float *c, float *d, unsigned *status,
+                             cudaStream_t stream);
 // Largest multiple of 8 (<= 256 rows of 128 bytes) dividing every tile height.
 int tc_box_rows(const int64_t *tile_rows, int n);
 int tc_map_init();  // resolves cuTensorMapEncodeTiled; FG21_OK or error

@@ -736,6 +736,35 @@ int fg21_selftest_bounded_wait(uint32_t *status_word, double *elapsed_s, void *s
     return FG21_OK;
 }
 
+int fg21_selftest_mma_rounding(const uint16_t *a, const uint16_t *b, const float *c, float *d, void *stream) {
+    if (!a || !b || !c || !d) return set_error(FG21_E_ARG, "NULL operand");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t na = 128 * 16 * 2, nb = 16 * 16 * 2, nc = 128 * 16 * 4;
+    char *p = nullptr;
+    if (cudaMalloc((void **)&p, 256 + na + nb + 2 * nc) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(FG21_E_NOMEM, "cudaMalloc of the probe buffers failed");
+    }
+    unsigned *d_status = (unsigned *)p;
+    uint16_t *d_a = (uint16_t *)(p + 256);
+    uint16_t *d_b = (uint16_t *)(p + 256 + na);
+    float *d_c = (float *)(p + 256 + na + nb);
+    float *d_d = d_c + 128 * 16;
+    unsigned st = 0;
+    cudaError_t e = cudaMemsetAsync(d_status, 0, 4, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_a, a, na, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_b, b, nb, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_c, c, nc, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_mma_probe(d_a, d_b, d_c, d_d, d_status, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d, d_d, nc, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&st, d_status, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(p);
+    if (e != cudaSuccess) return cuda_error(e, "MMA rounding self-test");
+    if (st) return set_error(FG21_E_DEVICE, "MMA probe reported status 0x%x", st);
+    return FG21_OK;
+}
+
 int fg21_model_timing(fg21_model *m, int enable) {
     if (!m) return set_error(FG21_E_ARG, "NULL model");
     std::lock_guard<std::mutex> lk(m->mu);

@@ -957,7 +957,88 @@ __global__ void __launch_bounds__(128) wait_selftest_kernel(unsigned *status, un
     if ((threadIdx.x & 31) == 0) elapsed[warp] = ok ? ~0ull : dt;
 }
 
+// One MMA exactly as the likelihood kernel issues it (kind::f16, F16
+// operands, F32 accumulator, M = 128, N = 16, K = 16, A in tensor memory, B
+// from shared memory by descriptor): d = c + a b for caller-given operands, so
+// that a host can check the accumulator's rounding.  a [128][16] and b
+// [16 n][16 k] are F16 bit patterns, c and d [128][16] FP32.  One CTA of 128
+// threads; the completion wait is bounded (status bit STATUS_TIMEOUT_MMA).
+__global__ void __launch_bounds__(128, 1) mma_probe_kernel(const uint16_t *__restrict__ a,
+                                                            const uint16_t *__restrict__ b,
+                                                            const float *__restrict__ c, float *__restrict__ d,
+                                                            unsigned *status) {
+    __shared__ __align__(1024) uint16_t sb[2][16][8];      // [k chunk][n][8 values of k]
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tbase;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tbase)),
+                     "r"(32)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    for (int i = tid; i < 256; i += 128) sb[(i & 15) >> 3][i >> 4][i & 7] = b[i];
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tm = tbase, lane_base = tm + ((uint32_t)(warp * 32) << 16);
+    uint32_t v[16];
+#pragma unroll
+    for (int n = 0; n < 16; ++n) v[n] = __float_as_uint(c[tid * 16 + n]);
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+            lane_base),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
+    uint32_t w[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) w[j] = (uint32_t)a[tid * 16 + 2 * j] | ((uint32_t)a[tid * 16 + 2 * j + 1] << 16);
+    tmem_st4(lane_base + 16, w);
+    tmem_st4(lane_base + 20, w + 4);
+    tmem_st_wait();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0) {
+        mma_f16_ts(tm, tm + 16, smem_desc(smem_u32(&sb[0][0][0]), 16 * 16, 128), instr_desc(128, 16, false), 1u);
+        mma_commit(&bar);
+    }
+    const uint64_t t0 = globaltimer();
+    bool ok = true;
+    while (!mbar_try_wait(&bar, 0)) {
+        if (globaltimer() - t0 > WAIT_LIMIT_NS) {
+            if (tid == 0) atomicOr(status, STATUS_TIMEOUT_MMA);
+            ok = false;
+            break;
+        }
+    }
+    tc_fence_after();
+    float r[16];
+    tmem_ld16(lane_base, r);
+    tmem_ld_wait();
+#pragma unroll
+    for (int n = 0; n < 16; ++n) d[tid * 16 + n] = ok ? r[n] : __int_as_float(0x7FC00000);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(32) : "memory");
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_mma_probe(const uint16_t *a, const uint16_t *b, const float *c, float *d, unsigned *status,
+                             cudaStream_t stream) {
+    mma_probe_kernel<<<1, 128, 0, stream>>>(a, b, c, d, status);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_wait_selftest(unsigned *status, unsigned long long *elapsed, cudaStream_t stream) {
     wait_selftest_kernel<<<1, 128, 0, stream>>>(status, elapsed);

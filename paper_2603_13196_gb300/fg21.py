@@ -90,6 +90,7 @@ _SIGS = {
     "fg21_loglike_batch_device_noalloc": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int, _P]),
     "fg21_model_sync_status": (C.c_int, [_P, _P, _P]),
     "fg21_selftest_bounded_wait": (C.c_int, [_P, _P, _P]),
+    "fg21_selftest_mma_rounding": (C.c_int, [_P, _P, _P, _P, _P]),
     "fg21_autotune": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int, _P, _P, _P]),
     "fg21_model_eval": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int, _P]),
     "fg21_model_timing": (C.c_int, [_P, C.c_int]),
@@ -344,6 +345,19 @@ def fg21_model_sync_status(m: Model, stream: int = 0) -> int:
     n = C.c_int64()
     _check(lib().fg21_model_sync_status(m.handle, stream or None, C.byref(n)), "fg21_model_sync_status")
     return n.value
+
+
+def fg21_selftest_mma_rounding(a16: np.ndarray, b16: np.ndarray, c: np.ndarray, stream: int = 0) -> np.ndarray:
+    """d = c + a b by one tcgen05.mma (a [128,16], b [16 n, 16 k] float16; c [128,16] float32)."""
+    a = np.ascontiguousarray(a16, dtype=np.float16)
+    b = np.ascontiguousarray(b16, dtype=np.float16)
+    cc = np.ascontiguousarray(c, dtype=np.float32)
+    if a.shape != (128, 16) or b.shape != (16, 16) or cc.shape != (128, 16):
+        raise ValueError("shapes: a [128, 16], b [16, 16], c [128, 16]")
+    d = np.empty((128, 16), dtype=np.float32)
+    _check(lib().fg21_selftest_mma_rounding(a.ctypes.data, b.ctypes.data, cc.ctypes.data, d.ctypes.data,
+                                            stream or None), "fg21_selftest_mma_rounding")
+    return d
 
 
 def fg21_selftest_bounded_wait(stream: int = 0):

@@ -61,6 +61,7 @@ def test_argument_errors_without_device(L):
     assert L.fg21_build_regions_ab(nul, nul, nul, nul, nul, nul, nul, nul, nul) == fg21.FG21_E_ARG
     assert L.fg21_build_regions_ab_host(nul, nul, nul, nul, nul, nul, nul, nul, nul, nul) == fg21.FG21_E_ARG
     assert L.fg21_selftest_bounded_wait(nul, nul, nul) == fg21.FG21_E_ARG
+    assert L.fg21_selftest_mma_rounding(nul, nul, nul, nul, nul) == fg21.FG21_E_ARG
     assert L.fg21_model_sync_status(nul, nul, nul) == fg21.FG21_E_ARG
     assert "NULL" in L.fg21_last_error().decode()
 
