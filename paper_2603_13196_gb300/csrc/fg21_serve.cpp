@@ -10,6 +10,9 @@
 // waits on each launch's event, copies results to the callers' buffers and
 // wakes their tickets.  Runs are admitted while their resident bytes fit the
 // memory budget; the others wait in arrival order.
+#include <cstdio>
+#include <nvtx3/nvToolsExt.h>
+#include <nvtx3/nvToolsExtCudaRt.h>
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -150,6 +153,11 @@ bool launch_batch(fg21_server *s, int k, std::unique_lock<std::mutex> &lk) {
     std::vector<std::pair<Ticket *, fg21_model *>> work;
     for (Ticket *t : sl.batch) work.emplace_back(t, s->runs.at(t->run).m);
     lk.unlock();   // staging and launch without the server lock
+    // profiler range (NVTX; near free when no tool is attached)
+    char label[96];
+    std::snprintf(label, sizeof label, "fg21 serve launch: slot %d, %zu requests, %lld points", k, work.size(),
+                  (long long)pts);
+    nvtxRangePushA(label);
     int rc = FG21_OK;
     do {
         if (off > sl.io_cap) {
@@ -190,6 +198,7 @@ bool launch_batch(fg21_server *s, int k, std::unique_lock<std::mutex> &lk) {
             break;
         }
     } while (0);
+    nvtxRangePop();
     lk.lock();
     sl.launch_rc = rc;
     s->inflight.push_back(k);
@@ -245,6 +254,7 @@ void completer_main(fg21_server *s) {
         s->inflight.pop_front();
         Slot &sl = s->slots[k];
         lk.unlock();
+        nvtxRangePushA("fg21 serve completion: wait for the launch, copy results");
         int rc = sl.launch_rc;
         if (rc == FG21_OK) {
             if (cudaEventSynchronize(sl.done) != cudaSuccess) {
@@ -260,6 +270,7 @@ void completer_main(fg21_server *s) {
             for (size_t j = 0; j < sl.batch.size(); ++j)
                 std::memcpy(sl.batch[j]->out, sl.h_io + sl.loff[j], sizeof(double) * sl.batch[j]->P);
         const auto now = Clock::now();
+        nvtxRangePop();
         lk.lock();
         for (Ticket *t : sl.batch) {
             t->state = TState::Done;
@@ -321,6 +332,9 @@ int fg21_serve_create(const fg21_serve_opts *opts, fg21_server **out) {
             fg21_serve_destroy(s);
             return set_error(FG21_E_CUDA, "stream/event creation failed");
         }
+        char name[48];
+        std::snprintf(name, sizeof name, "fg21 serve slot %d", (int)(&sl - s->slots.data()));
+        nvtxNameCudaStreamA(sl.stream, name);      // labels the slot's stream in a profiler trace
     }
     cudaSetDevice(prev);
     s->batcher = std::thread(batcher_main, s);

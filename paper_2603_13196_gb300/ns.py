@@ -169,39 +169,67 @@ class NestedSlice:
             hi[rej] = np.where(tr >= 0, tr, hi[rej])
         return new_x, new_l
 
-    def run(self, max_iter: int = 100000, tol_logz: float = -3.0) -> NSResult:
+    # ------------------------------------------------------------ state
+    def _start(self):
         u = self.rng.uniform(size=(self.n, self.D))
-        lu = self._eval(u)
-        logX = 0.0
-        dead_l, dead_w, dead_t = [], [], []
-        logZ = -np.inf
-        it = 0
-        while it < max_iter:
-            it += 1
-            order = np.argsort(lu, kind="stable")
-            kill = order[:self.b]
-            keep = order[self.b:]
-            Lmin = lu[kill[-1]]
-            for i, j in enumerate(kill):
-                logX_new = logX - 1.0 / (self.n - i)
-                logw = logX + math.log1p(-math.exp(logX_new - logX))
-                dead_l.append(lu[j])
-                dead_w.append(logw)
-                dead_t.append(u[j].copy())
-                logZ = np.logaddexp(logZ, lu[j] + logw)
-                logX = logX_new
-            # replacements: chains from random survivors, whitened directions
-            start = keep[self.rng.integers(0, keep.size, size=self.b)]
-            x = u[start].copy()
-            lx = lu[start].copy()
-            for _ in range(self.steps):
-                d = self._directions(u[keep], self.b)
-                x, lx = self._slice_step(x, lx, Lmin, d)
-            u[kill] = x
-            lu[kill] = lx
-            live_logZ = logX + _logsumexp(lu) - math.log(self.n)
-            if live_logZ - logZ < tol_logz:
-                break
+        self._st = dict(u=u, lu=self._eval(u), logX=0.0, logZ=-np.inf, it=0, dead_l=[], dead_w=[], dead_t=[])
+
+    def state_dict(self) -> dict:
+        """A checkpoint of the run: live points, their likelihoods, the prior
+        volume, the evidence so far, the dead points, the counters and the
+        random generator's state.  `load_state` on a sampler built with the same
+        prior, likelihood and settings continues the run exactly."""
+        st = self._st
+        return {"u": st["u"].copy(), "lu": st["lu"].copy(), "logX": st["logX"], "logZ": float(st["logZ"]),
+                "it": st["it"], "dead_l": list(st["dead_l"]), "dead_w": list(st["dead_w"]),
+                "dead_t": [t.copy() for t in st["dead_t"]], "n_like": self.n_like, "n_rounds": self.n_rounds,
+                "rng": self.rng.bit_generator.state, "settings": (self.n, self.b, self.steps, self.D)}
+
+    def load_state(self, state: dict):
+        if tuple(state["settings"]) != (self.n, self.b, self.steps, self.D):
+            raise ValueError("checkpoint of a run with other settings")
+        self._st = {"u": state["u"].copy(), "lu": state["lu"].copy(), "logX": state["logX"],
+                    "logZ": state["logZ"], "it": state["it"], "dead_l": list(state["dead_l"]),
+                    "dead_w": list(state["dead_w"]), "dead_t": [t.copy() for t in state["dead_t"]]}
+        self.n_like = state["n_like"]
+        self.n_rounds = state["n_rounds"]
+        self.rng.bit_generator.state = state["rng"]
+
+    def _iterate(self, tol_logz: float) -> bool:
+        """One batched deletion and replacement; True when the run has converged."""
+        st = self._st
+        u, lu = st["u"], st["lu"]
+        st["it"] += 1
+        order = np.argsort(lu, kind="stable")
+        kill = order[:self.b]
+        keep = order[self.b:]
+        Lmin = lu[kill[-1]]
+        logX, logZ = st["logX"], st["logZ"]
+        for i, j in enumerate(kill):
+            logX_new = logX - 1.0 / (self.n - i)
+            logw = logX + math.log1p(-math.exp(logX_new - logX))
+            st["dead_l"].append(lu[j])
+            st["dead_w"].append(logw)
+            st["dead_t"].append(u[j].copy())
+            logZ = np.logaddexp(logZ, lu[j] + logw)
+            logX = logX_new
+        st["logX"], st["logZ"] = logX, logZ
+        # replacements: chains from random survivors, whitened directions
+        start = keep[self.rng.integers(0, keep.size, size=self.b)]
+        x = u[start].copy()
+        lx = lu[start].copy()
+        for _ in range(self.steps):
+            d = self._directions(u[keep], self.b)
+            x, lx = self._slice_step(x, lx, Lmin, d)
+        u[kill] = x
+        lu[kill] = lx
+        live_logZ = logX + _logsumexp(lu) - math.log(self.n)
+        return live_logZ - logZ < tol_logz
+
+    def _finish(self) -> NSResult:
+        st = self._st
+        u, lu, logX, logZ = st["u"], st["lu"], st["logX"], st["logZ"]
+        dead_l, dead_w, dead_t = list(st["dead_l"]), list(st["dead_w"]), list(st["dead_t"])
         # remaining live points share the final volume equally
         for j in np.argsort(lu):
             logw = logX - math.log(self.n)
@@ -213,8 +241,26 @@ class NestedSlice:
         post = np.exp(dl + dw - logZ)
         H = float(np.sum(post * (dl - logZ)))
         return NSResult(logZ=float(logZ), logZ_err=math.sqrt(max(H, 0.0) / self.n), H=H, n_like=self.n_like,
-                        n_rounds=self.n_rounds, iterations=it, logL_max=float(np.max(dl)), dead_logL=dl,
+                        n_rounds=self.n_rounds, iterations=st["it"], logL_max=float(np.max(dl)), dead_logL=dl,
                         dead_logw=dw, dead_theta=self.prior.transform(np.array(dead_t)))
+
+    def run(self, max_iter: int = 100000, tol_logz: float = -3.0, stop_after: Optional[int] = None,
+            resume: Optional[dict] = None) -> Optional[NSResult]:
+        """Run to convergence (or max_iter iterations).  resume: a state_dict to
+        continue from.  stop_after: return None after that many more iterations
+        without finishing (take state_dict() then, to checkpoint)."""
+        if resume is not None:
+            self.load_state(resume)
+        else:
+            self._start()
+        done = 0
+        while self._st["it"] < max_iter:
+            if stop_after is not None and done >= stop_after:
+                return None
+            done += 1
+            if self._iterate(tol_logz):
+                break
+        return self._finish()
 
 
 def expected_log_shrinkage(n: int, b: int) -> float:
