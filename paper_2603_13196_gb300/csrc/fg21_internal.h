@@ -173,7 +173,10 @@ struct TcLaunch {
     void *arena;             // operand tile arena (device), 128-byte rows
     int64_t arena_rows;
     unsigned *status;
+    bool lean;               // every request: no amplitude regions and Kp equal to the launch's padded K
 };
+// The padded K of a tensor-core launch whose largest request K is kp_max.
+inline int tc_launch_kp(int kp_max) { return kp_max <= 16 ? 16 : kp_max <= 32 ? 32 : 64; }
 cudaError_t launch_tc(const TcLaunch &L, int num_sms, cudaStream_t stream);
 // One CTA whose waits expire by design (status + 4 per-warp waiting times).
 cudaError_t launch_wait_selftest(unsigned *status, unsigned long long *elapsed, cudaStream_t stream);

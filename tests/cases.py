@@ -336,3 +336,27 @@ def near_posterior_ab(m, obs, dbeta: float, dalpha: float, P: int, seed: int = 6
     pts[:, :Nb] += g.uniform(-dbeta, dbeta, size=(P, Nb))
     pts[:, Nb:Nb + Na] *= 1.0 + g.uniform(-dalpha, dalpha, size=(P, Na))
     return truth, data, pts
+
+
+# ------------------------------------------------ nested sampling, serving size
+# A run of the serving workload's size (N = 9 regions, F = 151, T = 10 LST bins
+# over 6 h, 3072-pixel sky, n_live = 500, 128 deletions per iteration, 5 D inner
+# slice steps): data from the 9-region model at the regions' mean spectral
+# indices plus 25 mK noise.  The prior on beta is [2.35, 2.75]: the sky's two
+# lowest regions have mean indices of 2.418 and 2.438, below the workloads'
+# prior bound of 2.45, where no sampler could reach the likelihood's peak.
+NS_SERVING = dict(npix=3072, sky_seed=41, N=9, F=151, T=10, window_h=6.0, lst0_h=5.0, noise_seed=41,
+                  n_live=500, num_delete=128, beta_prior=(2.35, 2.75))
+
+
+def ns_serving_problem():
+    """(sky, obs, oracle model, data, truth, prior) of the serving-size run."""
+    from paper_2603_13196_gb300 import ns
+    c = NS_SERVING
+    sky = I.make_sky(c["npix"], c["sky_seed"])
+    obs = I.make_obs(c["F"], c["T"], c["window_h"], lst0_h=c["lst0_h"])
+    m = O.build_model(sky, obs, c["N"], "recursive")
+    truth = np.concatenate([O.region_truth(sky, m.labels, c["N"], m.w), [0.155, 85.0, 15.0, I.NOISE_K]])
+    data = O.fast_model(m.A, m.B, obs, truth)[0] + I.NOISE_K * I.noise_draws(obs.F, obs.T, c["noise_seed"])
+    prior = ns.region_model_prior(c["N"], beta=c["beta_prior"])
+    return sky, obs, m, data, truth, prior

@@ -44,3 +44,36 @@ def test_evidence_gpu_serve_vs_oracle(fg21lib):
     # the best-fit likelihood is the noise floor of the exact model: chi2 ~ F T
     floor = -0.5 * obs.F * obs.T * math.log(2 * math.pi * 0.025 ** 2) - 0.5 * obs.F * obs.T
     assert abs(gpu.logL_max - floor) < 4 * math.sqrt(obs.F * obs.T)
+
+
+def test_evidence_serving_size(fg21lib):
+    """A run of the serving workload's size (9 regions, F = 151, T = 10, n_live
+    500, 128 deletions per iteration, 5 D inner steps) fed by the serving loop
+    reaches the log-evidence of the same sampler fed by the FP64 oracle
+    (tests/golden/ns_serving_reference.json, written by
+    make_ns_serving_reference.py, an independent seed) within twice their
+    combined sampling error sqrt(H / n_live); its best likelihood is near the
+    likelihood of the truth."""
+    import json
+    import os
+    import cases
+    ref = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                      "ns_serving_reference.json")))
+    sky, obs, om, data, truth, prior = cases.ns_serving_problem()
+    c = cases.NS_SERVING
+    model = fg21lib.fg21_build_regions(sky, obs, c["N"], "recursive")
+    assert np.array_equal(model.labels, om.labels)
+    fg21lib.fg21_model_set_data(model, data)
+    srv = fg21lib.Server(mem_budget_bytes=1 << 30, max_batch_points=8192, max_wait_us=0, max_inflight=2)
+    like = ns.ServeLikelihood(fg21lib, srv, model)
+    r = ns.NestedSlice(prior, like, n_live=c["n_live"], num_delete=c["num_delete"],
+                       num_inner_steps=5 * prior.dim, seed=2002).run()
+    like.close()
+    st = fg21lib.fg21_serve_stats(srv)
+    srv.close()
+    err = math.sqrt(r.logZ_err ** 2 + ref["logZ_err"] ** 2)
+    report("ns_evidence_serving_size", logZ_gpu=r.logZ, logZ_oracle=ref["logZ"], err=err, H=r.H,
+           n_like=r.n_like, rounds=r.n_rounds, p50_ms=st["p50_ms"], p99_ms=st["p99_ms"], logLmax_gpu=r.logL_max,
+           logL_truth=ref["logL_truth"])
+    assert abs(r.logZ - ref["logZ"]) < 2.0 * err, (r.logZ, ref["logZ"], err)
+    assert r.logL_max > ref["logL_truth"] - 3.0 * prior.dim, (r.logL_max, ref["logL_truth"])
