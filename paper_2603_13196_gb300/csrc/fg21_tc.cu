@@ -340,8 +340,10 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t 
 // Horner chains of a chunk of CH pairs advance together.
 // ALPHA (amplitude regions): the series runs on y = d nL + g with g =
 // ln(alpha / abar) of each component (pairs at gp[i * 128]) and the channel's
-// nL in nL2; e2 then holds the constant coefficients 2^(-s j) / j!.
-template <int NPHMAX, bool BF16, bool FULL, bool ALPHA>
+// nL in nL2; e2 then holds the constant coefficients 2^(-s j) / j!.  DF: the
+// series degree fixed at compile time (3, 5 or 8; 0 = the request's sp.D at
+// run time); the lean kernel dispatches on it once per work item.
+template <int NPHMAX, bool BF16, bool FULL, bool ALPHA, int DF = 0>
 __device__ __forceinline__ void gen_half(uint32_t t_hi, uint32_t t_mid, const uint64_t *d2,
                                          const float2 *__restrict__ lop, const uint64_t *e2, SeriesPlan sp,
                                          uint64_t sW2, int nph_rt, int nz, bool last, float s21, float sW,
@@ -364,7 +366,7 @@ __device__ __forceinline__ void gen_half(uint32_t t_hi, uint32_t t_mid, const ui
                 }
                 x2 = y2;
             }
-            if (sp.D == 3) {
+            if (DF == 3 || (DF == 0 && sp.D == 3)) {
                 // short series (a batch spread below ~0.007 in beta, as near a
                 // posterior): the deviations' low parts enter the weights
                 uint64_t l2[CH];
@@ -374,12 +376,12 @@ __device__ __forceinline__ void gen_half(uint32_t t_hi, uint32_t t_mid, const ui
                     l2[i] = pk2(v.x, v.y);
                 }
                 em1_series2<3, CH, !ALPHA>(w, x2, e2, l2);
-            } else if (sp.D == 5) {
+            } else if (DF == 5 || (DF == 0 && sp.D == 5)) {
                 em1_series2<5, CH, false>(w, x2, e2, nullptr);
             } else {
                 em1_series2<8, CH, false>(w, x2, e2, nullptr);
             }
-            if (sp.s > 0) {
+            if (DF != 3 && DF != 5 && sp.s > 0) {
                 const uint64_t two2 = pk2(2.0f, 2.0f);
                 for (int q = 0; q < sp.s; ++q)
 #pragma unroll
@@ -475,7 +477,7 @@ __device__ __forceinline__ void gen_item_load(GenItem<NPHMAX> &g, const ReqDesc 
 // request's Kr equals the kernel's KP).  Per stage: wait until the weight slot
 // is free (the MMAs of stage - ring are done), evaluate and store the weights,
 // then one arrival on full[slot].  Returns false on a wait timeout.
-template <int KP, bool BF16, bool FULL, bool ALPHA>
+template <int KP, bool BF16, bool FULL, bool ALPHA, int DF = 0>
 __device__ __forceinline__ bool gen_item(const Params &prm, Barriers *S, Ring &rg, const ReqDesc &r, const Item &it,
                                          const GenItem<KP / 4> &gi, uint32_t w_lane, int half) {
     constexpr int NPHMAX = KP / 4;
@@ -524,11 +526,11 @@ __device__ __forceinline__ bool gen_item(const Params &prm, Barriers *S, Ring &r
             tc_fence_after();
             const uint32_t wb = w_lane + rg.slot * KP;
             if (FULL)
-                gen_half<NPHMAX, BF16, true, ALPHA>(wb + half * NPHMAX, wb + KP / 2 + half * NPHMAX, gi.d2, gi.lop,
+                gen_half<NPHMAX, BF16, true, ALPHA, DF>(wb + half * NPHMAX, wb + KP / 2 + half * NPHMAX, gi.d2, gi.lop,
                                                     e2, gi.sp, sW2, NPHMAX, gi.nz, half != 0, s21, gi.sW, gi.gp,
                                                     pk2(nL, nL));
             else
-                gen_half<NPHMAX, BF16, false, ALPHA>(wb + half * nph, wb + gi.Kr / 2 + half * nph, gi.d2, gi.lop,
+                gen_half<NPHMAX, BF16, false, ALPHA, DF>(wb + half * nph, wb + gi.Kr / 2 + half * nph, gi.d2, gi.lop,
                                                      e2, gi.sp, sW2, nph, gi.nz, half != 0, s21, gi.sW, gi.gp,
                                                      pk2(nL, nL));
             tmem_st_wait();
@@ -759,7 +761,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             const ReqDesc &r = reqs[it.req];
             gen_item_load(gi, r, it, half, m);
             // a request's Kr fixes the column count of each half; it must match its operand tiles
-            if (LEAN) ok = gen_item<KP, BF16, true, false>(prm, S, rg, r, it, gi, w_lane, half);
+            if (LEAN) ok = gi.sp.D == 3 ? gen_item<KP, BF16, true, false, 3>(prm, S, rg, r, it, gi, w_lane, half)
+                         : gi.sp.D == 5 ? gen_item<KP, BF16, true, false, 5>(prm, S, rg, r, it, gi, w_lane, half)
+                                        : gen_item<KP, BF16, true, false, 8>(prm, S, rg, r, it, gi, w_lane, half);
             else if (r.Na) ok = gi.Kr == KP ? gen_item<KP, BF16, true, true>(prm, S, rg, r, it, gi, w_lane, half)
                                             : gen_item<KP, BF16, false, true>(prm, S, rg, r, it, gi, w_lane, half);
             else if (gi.Kr == KP) ok = gen_item<KP, BF16, true, false>(prm, S, rg, r, it, gi, w_lane, half);
