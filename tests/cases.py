@@ -219,7 +219,21 @@ MEASURED_ERR_OVER_TOL = {
     'noise_51_2000': 3.886e-02,
     'noise_through_likelihood_fp16x3': 6.235e-04,
     'noise_through_likelihood_fp32_delta': 1.938e-04,
+    'series_ab_degree3': 5.062e-02,
+    'series_ab_degree5': 3.691e-02,
+    'series_ab_degree8': 1.663e-02,
+    'series_ab_squarings': 1.348e-02,
+    'series_degree3_bf16x3': 1.131e-03,
+    'series_degree3_fp16x3': 4.149e-02,
+    'series_degree5_bf16x3': 1.429e-03,
+    'series_degree5_fp16x3': 3.567e-02,
+    'series_degree8_bf16x3': 1.669e-03,
+    'series_degree8_fp16x3': 1.836e-02,
+    'series_squarings_bf16x3': 2.396e-03,
+    'series_squarings_fp16x3': 1.174e-02,
     'serve_mixed_fp16x3': 2.098e-02,
+    'simt_chunks_fp32_delta': 7.330e-02,
+    'simt_chunks_fp32_direct': 1.579e-01,
     'simt_small_fp32_delta': 3.475e-02,
     'simt_small_fp32_direct': 8.179e-02,
     'simt_w1_fp32_delta': 4.148e-02,

@@ -313,3 +313,62 @@ def test_workload3_near_posterior_dbeta_1e_4_recorded(fg21lib):
     err = np.abs(got[near] - want[near])
     report("w3_near_abs_1e-4_recorded", max_abs_near=err.max(), n_near=near.sum())
     assert err.max() <= 3e-2, f"max |dlogL| {err.max():.3e} at dbeta = 1e-4, chi2/(F T) <= 10"
+
+
+# Batch spreads that select each form of the weight series (the kernel derives
+# it from the spread: max |beta - bbar| * max |ln(nu/nu0)|, about 1.53 here):
+# degree 3 (spread 1e-3), degree 5 (3e-2), degree 8 (the prior box, 0.35) and
+# degree 8 after two halvings undone by squarings (beta in [1.8, 3.6]).
+SERIES_CASES = [("degree3", 1e-3), ("degree5", 3e-2), ("degree8", None), ("squarings", (1.8, 3.6))]
+
+
+@pytest.mark.parametrize("case,spread", SERIES_CASES, ids=[c[0] for c in SERIES_CASES])
+@pytest.mark.parametrize("prec", ["fp16x3", "bf16x3"])
+def test_weight_series_forms(fg21lib, case, spread, prec):
+    """Every form of the weights' expm1 series (degree 3, 5, 8 and squarings)
+    against eq. fast_forward_model / eq. likelihood in the oracle, through the
+    lean kernel (spectral-index regions, K = 32)."""
+    sky, obs, m, data = cases.small_case(npix=2048, N=24, F=41, T=12, window=4.0)
+    model = fg21lib.fg21_build_regions(sky, obs, 24)
+    fg21lib.fg21_model_set_data(model, data)
+    g = np.random.default_rng(17)
+    P = 300
+    if spread is None:
+        params = cases.I.prior_draws(P, 24, seed=23)
+    elif isinstance(spread, tuple):
+        params = cases.I.prior_draws(P, 24, seed=23)
+        params[:, :24] = g.uniform(spread[0], spread[1], size=(P, 24))
+    else:
+        centre = cases.I.prior_draws(1, 24, seed=24)[0]
+        params = cases.I.scatter_around(centre, P, spread, 25)
+    got = fg21lib.fg21_loglike_batch(model, params, prec)
+    want, _ = cases.expected(m, obs, data, params)
+    tol = cases.logl_tolerance(prec, m, obs, data, params)
+    cases.check_logl(f"series_{case}_{prec}", got, want, tol)
+    model.close()
+
+
+@pytest.mark.parametrize("case,spread", SERIES_CASES, ids=[c[0] for c in SERIES_CASES])
+def test_weight_series_forms_amplitude_regions(fg21lib, case, spread):
+    """The same series forms through the generic kernel (amplitude regions:
+    the series runs in y = d nL + ln(alpha / abar), degree chosen at run time)."""
+    Nb, Na = 6, 3
+    sky, obs, m, data = cases.small_case_ab(npix=2048, Nb=Nb, Na=Na, F=31, T=8)
+    model = fg21lib.fg21_build_regions_ab(sky, obs, Nb, "recursive", "beam", Na, cases.I.amplitude_field(sky),
+                                          "hierarchical", "beam")
+    fg21lib.fg21_model_set_data(model, data)
+    g = np.random.default_rng(19)
+    P = 200
+    params = cases.I.prior_draws_ab(P, Nb, Na, seed=29)
+    if isinstance(spread, tuple):
+        params[:, :Nb] = g.uniform(spread[0], spread[1], size=(P, Nb))
+    elif spread is not None:
+        centre = params[0].copy()
+        params = np.repeat(centre[None], P, axis=0)
+        params[:, :Nb] += g.uniform(-spread, spread, size=(P, Nb))
+        params[:, Nb:Nb + Na] *= 1.0 + g.uniform(-spread, spread, size=(P, Na))
+    got = fg21lib.fg21_loglike_batch(model, params, "fp16x3")
+    want, _ = cases.expected_ab(m, obs, data, params)
+    tol = cases.logl_tolerance_ab("fp16x3", m, obs, data, params)
+    cases.check_logl(f"series_ab_{case}", got, want, tol)
+    model.close()
