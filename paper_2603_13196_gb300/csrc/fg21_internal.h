@@ -173,7 +173,8 @@ struct TcLaunch {
     void *arena;             // operand tile arena (device), 128-byte rows
     int64_t arena_rows;
     unsigned *status;
-    bool lean;               // every request: no amplitude regions and Kp equal to the launch's padded K
+    int lean;                // 1: every request has no amplitude regions and Kp equal to the launch's padded
+                             // K; 2: no amplitude regions, Kp of any size; 0: otherwise
 };
 // The padded K of a tensor-core launch whose largest request K is kp_max.
 inline int tc_launch_kp(int kp_max) { return kp_max <= 16 ? 16 : kp_max <= 32 ? 32 : 64; }

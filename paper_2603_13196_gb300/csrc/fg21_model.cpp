@@ -289,8 +289,12 @@ int prepare_requests(Workspace &ws, std::vector<ReqDesc> &reqs, int precision, P
         L.arena = ws.arena;
         L.arena_rows = row;
         L.status = ws.d_status;
-        L.lean = true;
-        for (int k = 0; k < n; ++k) L.lean = L.lean && reqs[k].Na == 0 && reqs[k].Kp == tc_launch_kp(kp_max);
+        bool no_alpha = true, full = true;
+        for (int k = 0; k < n; ++k) {
+            no_alpha = no_alpha && reqs[k].Na == 0;
+            full = full && reqs[k].Kp == tc_launch_kp(kp_max);
+        }
+        L.lean = !no_alpha ? 0 : full ? 1 : 2;
     }
     std::memcpy(ws.pinned, reqs.data(), sizeof(ReqDesc) * n);
     return FG21_OK;

@@ -141,7 +141,7 @@ extern "C" int fg21_loglike_batch_device_noalloc(fg21_model *m, const double *d_
     T.arena = arena;
     T.arena_rows = (int64_t)(L.tiles / 128);
     T.status = status;
-    T.lean = r.Na == 0 && r.Kp == tc_launch_kp(r.Kp);
+    T.lean = r.Na != 0 ? 0 : r.Kp == tc_launch_kp(r.Kp) ? 1 : 2;
     cudaError_t e = launch_tc(T, num_sms_of(dev), s);
     if (e != cudaSuccess) return cuda_error(e, "tensor-core likelihood launch");
     FG21_CUDA_TRY(launch_reduce(&r, d_req, 1, s));
