@@ -87,7 +87,8 @@ struct ReqDesc {
     int cpg_hint;                // channels per group chosen by the autotuner for this size (0 = model)
     int n_part;                  // partial sums per point (G on the SIMT forms, 2G on the tensor path)
     int simt_tc;                 // SIMT forms: t-columns staged per round (128, or 64 / 32 where the
-                                 // double-buffered slabs of a large N would not fit shared memory)
+                                 // double-buffered slabs of a large N would not fit shared memory;
+                                 // never more than T rounded up to a multiple of 8)
     int n_tiles;                 // ceil(P / 128)
     int n_stat_blocks;           // ceil(P / STAT_BLOCK)
     int64_t item_begin;          // first global work-item id of this request
@@ -118,7 +119,9 @@ struct ReqDesc {
                            // Kp+4.. hold ln(alpha / alpha_bar) of each component, pair-interleaved
                            // ([Kp/2 pairs][128 points][2]); the last Kp rows hold the low parts
                            // of the deviations (beta - bbar minus its FP32 rounding), pair-
-                           // interleaved the same way; tensor path
+                           // interleaved the same way; tensor path.  SIMT forms: [n_tiles]
+                           // [Nb + Na][128] beta (direct) or beta - bbar (delta) of each spectral
+                           // index, then alpha (direct) or ln(alpha / abar) (delta)
     double chi2_scale;     // the reduction multiplies chi2 by this: 1 + (2/3) 2^-23 on the tensor
                            // path (the expected half-ulp that the accumulator's final rounding
                            // toward zero drops, relative to chi2), 1 on the SIMT paths
@@ -150,8 +153,8 @@ cudaError_t launch_simt(const ReqDesc *h_reqs, const ReqDesc *d_reqs, int n_reqs
 // request shape (the CUDA occupancy calculator, cached per device and shape),
 // and the t-chunk width that shape stages (the widest of 128, 64, 32 whose
 // shared memory fits a block).
-int simt_blocks_per_sm(int N, int Nb, int Na, int tc, int precision);
-int simt_chunk_width(int N, int Nb, int Na);
+int simt_blocks_per_sm(int N, int tc, int precision);
+int simt_chunk_width(int N, int T);
 cudaError_t launch_reduce(const ReqDesc *h_reqs, const ReqDesc *d_reqs, int n_reqs,
                           cudaStream_t stream);
 cudaError_t launch_model_eval(const ReqDesc *h_req, const ReqDesc *d_req, int precision,

@@ -426,20 +426,39 @@ __device__ __forceinline__ void prep_points(const ReqDesc &r, int tile, const do
 // channel's reference -- wbar_c (FP64), dref[t] = D - sum_c wbar_c A_c - T_CMB B
 // summed in ascending c (FP64: the foreground cancels here) -- and writes the
 // FP32 arrays of the delta form (wbar_c A_c and dref); the direct form only
-// needs the per-channel tables.
+// needs the per-channel tables.  The blocks after them write the FP32 parameter
+// rows of one 128-point tile each (pts32): the spectral indices (direct form)
+// or their deviations beta - bbar (delta form), then the amplitudes (direct) or
+// ln(alpha / abar) (delta).
 template <int MODE>  // 2 = SIMT delta, 3 = SIMT direct
 __global__ void __launch_bounds__(PREP_THREADS) prep_tiles_kernel(const ReqDesc *__restrict__ reqs) {
     extern __shared__ double smem_d[];
     const ReqDesc &r = reqs[blockIdx.y];
     const int nfc = r.F * r.n_tchunks;
     const int N = r.N, NP = r.NPF, Nb = r.Nb, T = r.T;
-    if ((int)blockIdx.x >= nfc) return;
+    if ((int)blockIdx.x >= nfc + r.n_tiles) return;
     // shared memory: the head (bbar, finalise scratch and group results), then wbar [N] FP64
     double *bbar = smem_d;
     float *fin_sh = reinterpret_cast<float *>(bbar + NP);
     float *gpart = reinterpret_cast<float *>(bbar + NP + (2 * NP + 2 + 16 + 1) / 2);
     double *wbar = bbar + prep_head_doubles(NP);
     prep_finalize(r, fin_sh, gpart, bbar, blockIdx.x == 0);
+    if ((int)blockIdx.x >= nfc) {
+        const int tile = blockIdx.x - nfc, Na = r.Na;
+        float *rows = r.pts32 + (size_t)tile * r.pts_rows * TILE_M;
+        for (int q = threadIdx.x; q < (Nb + Na) * TILE_M; q += blockDim.x) {
+            const int j = q / TILE_M, m = q - j * TILE_M;
+            const int64_t pt = (int64_t)tile * TILE_M + m;
+            float v = 0.0f;
+            if (pt < r.P) {
+                const double th = r.params[pt * (NP + 4) + j];
+                if (j < Nb) v = MODE == 3 ? (float)th : (float)(th - bbar[j]);
+                else v = MODE == 3 ? (float)th : log1pf((float)(th - bbar[j]) / (float)bbar[j]);
+            }
+            rows[q] = v;
+        }
+        return;
+    }
     const int fc = blockIdx.x;
     const int f = fc / r.n_tchunks, c = fc % r.n_tchunks;
     const int t0 = c * r.Tc, tn = min(r.Tc, T - t0);
@@ -659,9 +678,12 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_tc_kernel(const ReqDesc *__
 // order, with the next region's operands (one 16-byte load of weights, two of
 // the slab row, addresses stepped by pointer) loaded while the current
 // region's FMAs issue, two columns per packed FP32x2 FMA; it squares the
-// residuals into its points' sums.  The per-point sums
-// of a channel are combined in a fixed order and folded over the channels into
-// a compensated (hi, lo) FP32 pair.
+// residuals into its points' sums (packed too: even and odd columns in two
+// chains).  The column blocks that do not fill a round of the four column
+// slots are shared out by point instead (thread i: point i x 8 columns), so
+// every warp carries the same work into the stage's barrier.  The per-point
+// sums of a channel are combined in a fixed order and folded over the channels
+// into a compensated (hi, lo) FP32 pair.
 constexpr int SIMT_THREADS = 128;
 constexpr int SIMT_TC = 128;                      // widest t-chunk staged per round (= SIMT_THREADS)
 constexpr int SIMT_PT = 4, SIMT_CT = 8;           // register tile: points x columns
@@ -696,14 +718,15 @@ __device__ __forceinline__ int find_req_by_point(const ReqDesc *__restrict__ req
     return lo;
 }
 
-// Shared-memory floats of a SIMT block with N components, Nb spectral-index
-// and Na amplitude parameters, staging tc columns per round: weights
-// [N+1][128] and two slabs [N+1][tc] (one spare row each, read ahead by the
-// last region's load and never used), two sets of data columns [2][2][128],
-// troughs, per-slot sums, amplitudes and spectral indices [Na + Nb][128].
-__host__ __device__ inline size_t simt_smem_floats(int N, int Nb, int Na, int tc) {
+// Shared-memory floats of a SIMT block with N components staging tc columns
+// per round: weights [N+1][128] and two slabs [N+1][tc] (one spare row each,
+// read ahead by the last region's load and never used), two sets of data
+// columns [2][2][128], troughs and per-slot sums.  The points' parameters are
+// read from their FP32 rows in global memory (pts32) when a channel's weights
+// are formed, which keeps a block small enough for five to share an SM.
+__host__ __device__ inline size_t simt_smem_floats(int N, int tc) {
     return (size_t)(N + 1) * TILE_M + 2 * (size_t)(N + 1) * tc + 2 * 2 * SIMT_TC + TILE_M +
-           (size_t)SIMT_CS * TILE_M + (size_t)(Na + Nb) * TILE_M;
+           (size_t)(SIMT_CS + 1) * TILE_M;
 }
 constexpr size_t SIMT_SMEM_MAX = 226 * 1024;      // bytes a block may take (227 KB less the driver's share)
 
@@ -721,10 +744,10 @@ __global__ void __launch_bounds__(SIMT_THREADS) simt_kernel(const ReqDesc *__res
     float *As = Wsh + (size_t)(N + 1) * TILE_M;       // [2][N+1][tc] model slabs
     float *dcol = As + 2 * slab;                      // [2][2][SIMT_TC]: data (or dref), B
     float *s21s = dcol + 4 * SIMT_TC;                 // [128] trough of each point
-    float *qp = s21s + TILE_M;                        // [SIMT_CS][128] per-slot point sums
-    float *acol = qp + SIMT_CS * TILE_M;              // [Na][128] alpha (plain) or ln(alpha/abar)
-    float *bcol = acol + (size_t)Na * TILE_M;         // [Nb][128] beta (plain) or beta - bbar
+    float *qp = s21s + TILE_M;                        // [SIMT_CS + 1][128] per-slot point sums
     const int tid = threadIdx.x;
+    // this point's parameter rows: [Nb] beta (plain) or beta - bbar, then [Na] alpha or ln(alpha/abar)
+    const float *__restrict__ prow = r.pts32 + (size_t)tile * r.pts_rows * TILE_M + tid;
     const int64_t p = (int64_t)tile * TILE_M + tid;   // the point whose weights and sums this thread owns
     const bool inb = p < r.P;
     const int TCr = r.simt_tc;
@@ -755,19 +778,20 @@ __global__ void __launch_bounds__(SIMT_THREADS) simt_kernel(const ReqDesc *__res
     const double *th = r.params + (inb ? p : 0) * (NP + 4);
     const float a21 = (float)th[NP], nu21 = (float)th[NP + 1];
     const float inv2s2 = (float)(1.0 / (2.0 * th[NP + 2] * th[NP + 2]));
-    for (int i = 0; i < Na; ++i) {
-        const double ab = r.beta_bar[Nb + i];
-        acol[i * TILE_M + tid] = DIRECT ? (float)th[Nb + i] : log1pf((float)(th[Nb + i] - ab) / (float)ab);
-    }
-    for (int j = 0; j < Nb; ++j) bcol[j * TILE_M + tid] = DIRECT ? (float)th[j] : (float)(th[j] - r.beta_bar[j]);
     Wsh[(size_t)N * TILE_M + tid] = 0.0f;
     // this thread's register tiles: points 4 pg .. 4 pg + 3, column blocks cs, cs + 4, ...
     // (a warp holds all 32 point groups of one column slot: broadcast slab loads)
     const int pg = tid % SIMT_PG, cs = tid / SIMT_PG;
     float qs = 0.0f, qc = 0.0f;
-    float q4[SIMT_PT];
+    float q4[SIMT_PT];                // masked (partial-block) sums of this thread's tile points
+    uint64_t q2[SIMT_PT];             // packed sums: even and odd columns of full blocks
+    float qr = 0.0f;                  // point tid's sum over the shared-out blocks
 #pragma unroll
-    for (int a = 0; a < SIMT_PT; ++a) q4[a] = 0.0f;
+    for (int a = 0; a < SIMT_PT; ++a) {
+        q4[a] = 0.0f;
+        q2[a] = 0ull;
+    }
+    const uint64_t m1 = pk2f(-1.0f, -1.0f);
     for (int st = 0; st < S; ++st) {
         const int f = f0 + st / nck, ck = st % nck, t0 = ck * TCr;
         const int tn = min(TCr, T - t0);
@@ -780,14 +804,14 @@ __global__ void __launch_bounds__(SIMT_THREADS) simt_kernel(const ReqDesc *__res
             if (DIRECT) {
                 const float l2 = (float)(r.L[f] * 1.4426950408889634);   // log2(nu/nu0)
                 for (int i = 0; i < N; ++i) {
-                    const float w = exp2f(-bcol[(i % Nb) * TILE_M + tid] * l2);
-                    Wsh[i * TILE_M + tid] = Na ? acol[(i / Nb) * TILE_M + tid] * w : w;
+                    const float w = exp2f(-__ldg(prow + (i % Nb) * TILE_M) * l2);
+                    Wsh[i * TILE_M + tid] = Na ? __ldg(prow + (Nb + i / Nb) * TILE_M) * w : w;
                 }
             } else {
                 const float nL = (float)(-r.L[f]);
                 for (int i = 0; i < N; ++i) {
-                    float y = bcol[(i % Nb) * TILE_M + tid] * nL;
-                    if (Na) y += acol[(i / Nb) * TILE_M + tid];
+                    float y = __ldg(prow + (i % Nb) * TILE_M) * nL;
+                    if (Na) y += __ldg(prow + (Nb + i / Nb) * TILE_M);
                     Wsh[i * TILE_M + tid] = expm1f(y);
                 }
             }
@@ -803,7 +827,8 @@ __global__ void __launch_bounds__(SIMT_THREADS) simt_kernel(const ReqDesc *__res
         const float *d_st = dcol + (size_t)(st & 1) * 2 * SIMT_TC;
         const float tcmb = (float)r.t_cmb;
         const int ncb = (tn + SIMT_CT - 1) / SIMT_CT;
-        for (int cb = cs; cb < ncb; cb += SIMT_CS) {
+        const int nfull = ncb - ncb % SIMT_CS;     // blocks taken as 4 x 8 tiles, one per column slot per round
+        for (int cb = cs; cb < nfull; cb += SIMT_CS) {
             // accumulator pairs (columns 2k, 2k+1 of one point): packed FP32x2
             // FMAs, each lane the same round-to-nearest FMA as a scalar one
             uint64_t acc2[SIMT_PT][SIMT_CT / 2];
@@ -841,21 +866,80 @@ __global__ void __launch_bounds__(SIMT_THREADS) simt_kernel(const ReqDesc *__res
                 a0 = a0n;
                 a1 = a1n;
             }
-            float acc[SIMT_PT][SIMT_CT];
+            if (SIMT_CT * cb + SIMT_CT <= tn) {
+                // a full block: r = (dv - s21) - acc and r^2 summed in packed FP32x2,
+                // the same roundings per column as the scalar form below
+                uint64_t dv2[SIMT_CT / 2];
 #pragma unroll
-            for (int a = 0; a < SIMT_PT; ++a)
+                for (int c = 0; c < SIMT_CT / 2; ++c) {
+                    const int t = SIMT_CT * cb + 2 * c;
+                    dv2[c] = DIRECT ? fma2f(pk2f(-tcmb, -tcmb), pk2f(d_st[SIMT_TC + t], d_st[SIMT_TC + t + 1]),
+                                            pk2f(d_st[t], d_st[t + 1]))
+                                    : pk2f(d_st[t], d_st[t + 1]);
+                }
 #pragma unroll
-                for (int c = 0; c < SIMT_CT / 2; ++c) upk2f(acc2[a][c], acc[a][2 * c], acc[a][2 * c + 1]);
+                for (int a = 0; a < SIMT_PT; ++a) {
+                    const float sa = s21s[SIMT_PT * pg + a];
+                    const uint64_t s2 = pk2f(sa, sa);
+#pragma unroll
+                    for (int c = 0; c < SIMT_CT / 2; ++c) {
+                        const uint64_t rr2 = fma2f(acc2[a][c], m1, fma2f(s2, m1, dv2[c]));
+                        q2[a] = fma2f(rr2, rr2, q2[a]);
+                    }
+                }
+            } else {
+                float acc[SIMT_PT][SIMT_CT];
+#pragma unroll
+                for (int a = 0; a < SIMT_PT; ++a)
+#pragma unroll
+                    for (int c = 0; c < SIMT_CT / 2; ++c) upk2f(acc2[a][c], acc[a][2 * c], acc[a][2 * c + 1]);
+#pragma unroll
+                for (int c = 0; c < SIMT_CT; ++c) {
+                    const int t = SIMT_CT * cb + c;
+                    if (t < tn) {
+                        const float dv = DIRECT ? d_st[t] - tcmb * d_st[SIMT_TC + t] : d_st[t];
+#pragma unroll
+                        for (int a = 0; a < SIMT_PT; ++a) {
+                            const float rr = (dv - s21s[SIMT_PT * pg + a]) - acc[a][c];
+                            q4[a] = fmaf(rr, rr, q4[a]);
+                        }
+                    }
+                }
+            }
+        }
+        // the blocks left over from the rounds: thread tid takes point tid x 8 columns
+        for (int cb = nfull; cb < ncb; ++cb) {
+            uint64_t acc2[SIMT_CT / 2] = {0ull, 0ull, 0ull, 0ull};
+            const float *wp = Wsh + tid;
+            const float4 *ap = reinterpret_cast<const float4 *>(a_st + SIMT_CT * cb);
+            const int astep = TCr / 4;
+            float wa = wp[0];
+            float4 a0 = ap[0], a1 = ap[1];
+            for (int i = 0; i < N; ++i) {
+                wp += TILE_M;
+                ap += astep;
+                const float wn = wp[0];
+                const float4 a0n = ap[0], a1n = ap[1];
+                const uint64_t ww = pk2f(wa, wa);
+                acc2[0] = fma2f(pk2f(a0.x, a0.y), ww, acc2[0]);
+                acc2[1] = fma2f(pk2f(a0.z, a0.w), ww, acc2[1]);
+                acc2[2] = fma2f(pk2f(a1.x, a1.y), ww, acc2[2]);
+                acc2[3] = fma2f(pk2f(a1.z, a1.w), ww, acc2[3]);
+                wa = wn;
+                a0 = a0n;
+                a1 = a1n;
+            }
+            float acc[SIMT_CT];
+#pragma unroll
+            for (int c = 0; c < SIMT_CT / 2; ++c) upk2f(acc2[c], acc[2 * c], acc[2 * c + 1]);
+            const float st21 = s21s[tid];
 #pragma unroll
             for (int c = 0; c < SIMT_CT; ++c) {
                 const int t = SIMT_CT * cb + c;
                 if (t < tn) {
                     const float dv = DIRECT ? d_st[t] - tcmb * d_st[SIMT_TC + t] : d_st[t];
-#pragma unroll
-                    for (int a = 0; a < SIMT_PT; ++a) {
-                        const float rr = (dv - s21s[SIMT_PT * pg + a]) - acc[a][c];
-                        q4[a] = fmaf(rr, rr, q4[a]);
-                    }
+                    const float rr = (dv - st21) - acc[c];
+                    qr = fmaf(rr, rr, qr);
                 }
             }
         }
@@ -863,13 +947,18 @@ __global__ void __launch_bounds__(SIMT_THREADS) simt_kernel(const ReqDesc *__res
             // the channel is complete: its per-point sums, combined in slot order
 #pragma unroll
             for (int a = 0; a < SIMT_PT; ++a) {
-                qp[cs * TILE_M + SIMT_PT * pg + a] = q4[a];
+                float lo, hi;
+                upk2f(q2[a], lo, hi);
+                qp[cs * TILE_M + SIMT_PT * pg + a] = (lo + hi) + q4[a];
                 q4[a] = 0.0f;
+                q2[a] = 0ull;
             }
+            qp[SIMT_CS * TILE_M + tid] = qr;
+            qr = 0.0f;
             __syncthreads();
             float qf = qp[tid];
 #pragma unroll
-            for (int k = 1; k < SIMT_CS; ++k) qf += qp[k * TILE_M + tid];
+            for (int k = 1; k <= SIMT_CS; ++k) qf += qp[k * TILE_M + tid];
             kahan_add(qs, qc, qf);
         }
         __syncthreads();                // every read of this stage's buffers is done
@@ -1047,7 +1136,7 @@ cudaError_t launch_prep(const ReqDesc *h_reqs, const ReqDesc *d_reqs, int n_reqs
         }
         sm = sm > need ? sm : need;
     }
-    dim3 g2(max_F_chunks + (tc ? max_tiles : 0), n_reqs);
+    dim3 g2(max_F_chunks + max_tiles, n_reqs);
     static size_t tc_opt_in[2] = {48 * 1024, 48 * 1024};
     if (precision == FG21_PREC_FP16X3) e = opt_in_smem(prep_tc_kernel<false>, sm, tc_opt_in[0]);
     if (precision == FG21_PREC_BF16X3) e = opt_in_smem(prep_tc_kernel<true>, sm, tc_opt_in[1]);
@@ -1075,26 +1164,29 @@ static cudaError_t simt_smem_limit() {
     return err;
 }
 
-int simt_chunk_width(int N, int Nb, int Na) {
+int simt_chunk_width(int N, int T) {
+    // columns staged per round: the widest power of two that fits shared
+    // memory, but no wider than T rounded up to a column block
+    const int t8 = (T + SIMT_CT - 1) / SIMT_CT * SIMT_CT;
     for (int tc = SIMT_TC; tc > 32; tc >>= 1)
-        if (sizeof(float) * simt_smem_floats(N, Nb, Na, tc) <= SIMT_SMEM_MAX) return tc;
-    return 32;
+        if (sizeof(float) * simt_smem_floats(N, std::min(tc, t8)) <= SIMT_SMEM_MAX) return std::min(tc, t8);
+    return std::min(32, t8);
 }
 
-int simt_blocks_per_sm(int N, int Nb, int Na, int tc, int precision) {
+int simt_blocks_per_sm(int N, int tc, int precision) {
     static std::mutex mu;
-    static std::map<std::tuple<int, int, int, int, int>, int> cache;
+    static std::map<std::tuple<int, int, int, int>, int> cache;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }
     const bool direct = precision == FG21_PREC_FP32_DIRECT;
-    const auto key = std::make_tuple(dev, N, Nb, Na, tc * 2 + (int)direct);
+    const auto key = std::make_tuple(dev, N, tc, (int)direct);
     std::lock_guard<std::mutex> lk(mu);
     const auto it = cache.find(key);
     if (it != cache.end()) return it->second;
-    const size_t sm = sizeof(float) * simt_smem_floats(N, Nb, Na, tc);
+    const size_t sm = sizeof(float) * simt_smem_floats(N, tc);
     int n = 0;
     cudaError_t e = simt_smem_limit();
     if (e == cudaSuccess)
@@ -1115,12 +1207,13 @@ cudaError_t launch_simt(const ReqDesc *h_reqs, const ReqDesc *d_reqs, int n_reqs
     for (int k = 0; k < n_reqs; ++k) {
         const ReqDesc &r = h_reqs[k];
         items += (int64_t)r.n_tiles * r.G;
-        const size_t need = sizeof(float) * simt_smem_floats(r.N, r.Nb, r.Na, r.simt_tc);
+        const size_t need = sizeof(float) * simt_smem_floats(r.N, r.simt_tc);
         sm = sm > need ? sm : need;
     }
     if (items == 0) return cudaSuccess;
     for (int k = 0; k < n_reqs; ++k)
-        if (h_reqs[k].P > 0 && (h_reqs[k].simt_tc < 32 || h_reqs[k].simt_tc > SIMT_TC || h_reqs[k].simt_tc % 32))
+        if (h_reqs[k].P > 0 && (h_reqs[k].simt_tc < SIMT_CT || h_reqs[k].simt_tc > SIMT_TC ||
+                                h_reqs[k].simt_tc % SIMT_CT || h_reqs[k].pts32 == nullptr))
             return cudaErrorInvalidValue;
     if (sm > SIMT_SMEM_MAX) return cudaErrorInvalidValue;
     cudaError_t e = simt_smem_limit();

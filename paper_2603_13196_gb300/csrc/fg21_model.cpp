@@ -163,7 +163,8 @@ static int choose_channels_per_group(int64_t total_tiles, int F, int slots, int 
 
 void plan_request(ReqDesc &r, int precision, int num_sms, int64_t total_tiles) {
     r.Kp = round16(r.N + 2);
-    r.pts_rows = r.Kp + 4 + (r.Na ? r.Kp : 0) + r.Kp;
+    r.pts_rows = precision == FG21_PREC_FP16X3 || precision == FG21_PREC_BF16X3 ? r.Kp + 4 + (r.Na ? r.Kp : 0) + r.Kp
+                                                                             : r.Nb + r.Na;
     // t-chunks of at most TC_MAX columns: the same cap for every K keeps the
     // plan of a request independent of what it is batched with
     r.n_tchunks = (r.T + TC_MAX - 1) / TC_MAX;
@@ -172,7 +173,7 @@ void plan_request(ReqDesc &r, int precision, int num_sms, int64_t total_tiles) {
     r.n_tiles = (int)((r.P + TILE_M - 1) / TILE_M);
     r.n_stat_blocks = (int)((r.P + STAT_BLOCK - 1) / STAT_BLOCK);
     const bool tc = precision == FG21_PREC_FP16X3 || precision == FG21_PREC_BF16X3;
-    r.simt_tc = tc ? 0 : simt_chunk_width(r.N, r.Nb, r.Na);
+    r.simt_tc = tc ? 0 : simt_chunk_width(r.N, r.T);
     int cpg;
     if (r.cpg_hint > 0) {
         cpg = std::min(r.F, r.cpg_hint);
@@ -181,7 +182,7 @@ void plan_request(ReqDesc &r, int precision, int num_sms, int64_t total_tiles) {
     } else {
         // SIMT blocks are not persistent: the waves are counted in the blocks
         // the GPU holds at once (at most 32 groups, the reduction's serial row)
-        const int slots = num_sms * simt_blocks_per_sm(r.N, r.Nb, r.Na, r.simt_tc, precision);
+        const int slots = num_sms * simt_blocks_per_sm(r.N, r.simt_tc, precision);
         cpg = choose_channels_per_group(total_tiles, r.F, slots, 32);
     }
     r.G = (r.F + cpg - 1) / cpg;
@@ -208,7 +209,7 @@ ReqLayout request_layout(const ReqDesc &r, int precision) {
     L.partials = align256(sizeof(float2) * (size_t)r.P * r.n_part);
     L.pvalid = align256((size_t)r.P);
     L.pnorm = tc ? align256(sizeof(double2) * (size_t)r.P) : 0;
-    L.pts32 = tc ? align256(sizeof(float) * (size_t)r.n_tiles * r.pts_rows * TILE_M) : 0;
+    L.pts32 = align256(sizeof(float) * (size_t)r.n_tiles * r.pts_rows * TILE_M);
     L.tiles = tc ? (size_t)r.F * r.n_tchunks * r.tile_rows * 128 : 0;
     return L;
 }
