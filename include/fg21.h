@@ -431,7 +431,8 @@ int fg21_noise_q(const double *d_L_noise, int64_t K, const double *L_bar, int64_
 typedef struct {
     size_t mem_budget_bytes;   /* admission budget over registered runs' resident bytes */
     int64_t max_batch_points;  /* points per launch (>= the largest single request) */
-    int32_t max_wait_us;       /* how long the batcher waits to fill a launch once work is pending */
+    int32_t max_wait_us;       /* how long the batcher may wait to fill a launch while earlier launches
+                                  are still running; with every slot idle, pending work goes at once */
     int32_t max_inflight;      /* launches in flight (1..8) */
     int32_t precision;         /* FG21_PREC_FP16X3 or FG21_PREC_BF16X3 */
     int32_t device;            /* CUDA device ordinal */

@@ -219,15 +219,23 @@ void batcher_main(fg21_server *s) {
             return any;
         });
         if (s->stop) break;
-        // give the batch a moment to fill unless it is already full
+        // give the batch a moment to fill, but only while earlier launches keep
+        // the GPU busy: with every slot free, what is pending goes at once
+        // (waiting then would only add latency), and the wait ends early when
+        // the batch is full or the GPU falls idle
+        auto gpu_busy = [s] {
+            for (const Slot &sl : s->slots)
+                if (sl.busy) return true;
+            return false;
+        };
         int64_t pts = 0;
         for (Ticket *t : s->pending) pts += t->P;
-        if (pts < s->opts.max_batch_points && s->opts.max_wait_us > 0) {
-            s->cv_work.wait_for(lk, std::chrono::microseconds(s->opts.max_wait_us), [s] {
+        if (pts < s->opts.max_batch_points && s->opts.max_wait_us > 0 && gpu_busy()) {
+            s->cv_work.wait_for(lk, std::chrono::microseconds(s->opts.max_wait_us), [s, &gpu_busy] {
                 if (s->stop) return true;
                 int64_t q = 0;
                 for (Ticket *t : s->pending) q += t->P;
-                return q >= s->opts.max_batch_points;
+                return q >= s->opts.max_batch_points || !gpu_busy();
             });
             if (s->stop) break;
         }
@@ -289,6 +297,7 @@ void completer_main(fg21_server *s) {
         sl.busy = false;
         s->cv_done.notify_all();
         s->cv_slot.notify_all();
+        s->cv_work.notify_all();   // a batcher filling a launch stops waiting once the GPU is idle
     }
 }
 
