@@ -23,6 +23,7 @@
 #include <tuple>
 
 #include "fg21_internal.h"
+#include "fg21_pdl.cuh"
 
 namespace fg21 {
 
@@ -433,6 +434,7 @@ __device__ __forceinline__ void prep_points(const ReqDesc &r, int tile, const do
 template <int MODE>  // 2 = SIMT delta, 3 = SIMT direct
 __global__ void __launch_bounds__(PREP_THREADS) prep_tiles_kernel(const ReqDesc *__restrict__ reqs) {
     extern __shared__ double smem_d[];
+    pdl_wait();
     const ReqDesc &r = reqs[blockIdx.y];
     const int nfc = r.F * r.n_tchunks;
     const int N = r.N, NP = r.NPF, Nb = r.Nb, T = r.T;
@@ -523,6 +525,7 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_tc_kernel(const ReqDesc *__
     extern __shared__ double smem_d[];
     __shared__ float sh_red[PREP_THREADS / 32];
     __shared__ int s_scaleB;
+    pdl_wait();
     const ReqDesc &r = reqs[blockIdx.y];
     const int nfc = r.F * r.n_tchunks;
     if ((int)blockIdx.x >= nfc + r.n_tiles) return;
@@ -733,6 +736,7 @@ constexpr size_t SIMT_SMEM_MAX = 226 * 1024;      // bytes a block may take (227
 template <bool DIRECT>
 __global__ void __launch_bounds__(SIMT_THREADS) simt_kernel(const ReqDesc *__restrict__ reqs, int n_reqs) {
     extern __shared__ __align__(16) float smem_f[];
+    pdl_wait();
     const int64_t item = blockIdx.x;
     const ReqDesc &r = reqs[find_req_by_item(reqs, n_reqs, item)];
     const int64_t lid = item - r.item_begin;
@@ -989,6 +993,7 @@ __device__ __forceinline__ void two_sum_acc(float &s, float &c, float x) {
 // partials were never written), every logL of the launch is NaN.
 template <bool WARP>
 __global__ void __launch_bounds__(REDUCE_THREADS) reduce_kernel(const ReqDesc *__restrict__ reqs, int n_reqs) {
+    pdl_wait();
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t gid = WARP ? tid >> 5 : tid;
     const int lane = WARP ? (int)(threadIdx.x & 31) : 0;
@@ -1142,11 +1147,14 @@ cudaError_t launch_prep(const ReqDesc *h_reqs, const ReqDesc *d_reqs, int n_reqs
     if (precision == FG21_PREC_BF16X3) e = opt_in_smem(prep_tc_kernel<true>, sm, tc_opt_in[1]);
     if (e != cudaSuccess) return e;
     switch (precision) {
-        case FG21_PREC_FP16X3: prep_tc_kernel<false><<<g2, PREP_THREADS, sm, stream>>>(d_reqs); break;
-        case FG21_PREC_BF16X3: prep_tc_kernel<true><<<g2, PREP_THREADS, sm, stream>>>(d_reqs); break;
-        case FG21_PREC_FP32_DELTA: prep_tiles_kernel<2><<<g2, PREP_THREADS, sm, stream>>>(d_reqs); break;
-        default: prep_tiles_kernel<3><<<g2, PREP_THREADS, sm, stream>>>(d_reqs); break;
+        case FG21_PREC_FP16X3: e = launch_dependent(prep_tc_kernel<false>, g2, PREP_THREADS, sm, stream, d_reqs); break;
+        case FG21_PREC_BF16X3: e = launch_dependent(prep_tc_kernel<true>, g2, PREP_THREADS, sm, stream, d_reqs); break;
+        case FG21_PREC_FP32_DELTA:
+            e = launch_dependent(prep_tiles_kernel<2>, g2, PREP_THREADS, sm, stream, d_reqs);
+            break;
+        default: e = launch_dependent(prep_tiles_kernel<3>, g2, PREP_THREADS, sm, stream, d_reqs); break;
     }
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -1218,10 +1226,10 @@ cudaError_t launch_simt(const ReqDesc *h_reqs, const ReqDesc *d_reqs, int n_reqs
     if (sm > SIMT_SMEM_MAX) return cudaErrorInvalidValue;
     cudaError_t e = simt_smem_limit();
     if (e != cudaSuccess) return e;
-    if (precision == FG21_PREC_FP32_DIRECT)
-        simt_kernel<true><<<(unsigned)items, SIMT_THREADS, sm, stream>>>(d_reqs, n_reqs);
-    else
-        simt_kernel<false><<<(unsigned)items, SIMT_THREADS, sm, stream>>>(d_reqs, n_reqs);
+    e = precision == FG21_PREC_FP32_DIRECT
+            ? launch_dependent(simt_kernel<true>, dim3((unsigned)items), SIMT_THREADS, sm, stream, d_reqs, n_reqs)
+            : launch_dependent(simt_kernel<false>, dim3((unsigned)items), SIMT_THREADS, sm, stream, d_reqs, n_reqs);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -1235,9 +1243,17 @@ cudaError_t launch_reduce(const ReqDesc *h_reqs, const ReqDesc *d_reqs, int n_re
         (h_reqs[k].n_part > REDUCE_SERIAL_MAX ? warp : serial) = true;
     }
     const int th = REDUCE_THREADS;
-    if (serial) reduce_kernel<false><<<(unsigned)((pts + th - 1) / th), th, 0, stream>>>(d_reqs, n_reqs);
+    cudaError_t e = cudaSuccess;
+    if (serial) e = launch_dependent(reduce_kernel<false>, dim3((unsigned)((pts + th - 1) / th)), th, 0, stream, d_reqs,
+                                     n_reqs);
+    if (e != cudaSuccess) return e;
     const int64_t per_block = th / 32;
-    if (warp) reduce_kernel<true><<<(unsigned)((pts + per_block - 1) / per_block), th, 0, stream>>>(d_reqs, n_reqs);
+    if (warp) {
+        const dim3 g((unsigned)((pts + per_block - 1) / per_block));
+        if (serial) reduce_kernel<true><<<g, th, 0, stream>>>(d_reqs, n_reqs);   // after the first reduction
+        else e = launch_dependent(reduce_kernel<true>, g, th, 0, stream, d_reqs, n_reqs);
+    }
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

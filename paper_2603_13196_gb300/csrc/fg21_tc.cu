@@ -52,6 +52,7 @@
 #include <mutex>
 
 #include "fg21_internal.h"
+#include "fg21_pdl.cuh"
 
 namespace fg21 {
 
@@ -745,6 +746,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
     __syncthreads();
     tc_fence_after();
+    // the set-up above touches only this CTA's shared and tensor memory; from
+    // here on the kernel reads what the operand pass wrote
+    pdl_wait();
     const uint32_t tmem = S->tmem_base;
     const uint32_t w_col0 = (uint32_t)(ring * prm.acc_cols);
     const ReqDesc *__restrict__ reqs = prm.reqs;
@@ -888,7 +892,9 @@ cudaError_t launch_kpr(const CUtensorMap &map, const Params &prm, int grid, size
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    tc_loglike_kernel<KP, BF16, RESID, LEAN><<<grid, NUM_THREADS, sm, stream>>>(map, prm);
+    cudaError_t e = launch_dependent(tc_loglike_kernel<KP, BF16, RESID, LEAN>, dim3(grid), dim3(NUM_THREADS), sm,
+                                     stream, map, prm);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
