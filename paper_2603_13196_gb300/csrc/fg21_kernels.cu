@@ -1174,7 +1174,9 @@ static cudaError_t simt_smem_limit() {
 
 int simt_chunk_width(int N, int T) {
     // columns staged per round: the widest power of two that fits shared
-    // memory, but no wider than T rounded up to a column block
+    // memory, but no wider than T rounded up to a column block (128 columns
+    // fit for every N up to 146, beyond the region cap of 126; the narrower
+    // widths guard the shared-memory limit should that cap grow)
     const int t8 = (T + SIMT_CT - 1) / SIMT_CT * SIMT_CT;
     for (int tc = SIMT_TC; tc > 32; tc >>= 1)
         if (sizeof(float) * simt_smem_floats(N, std::min(tc, t8)) <= SIMT_SMEM_MAX) return std::min(tc, t8);

@@ -234,6 +234,8 @@ MEASURED_ERR_OVER_TOL = {
     'serve_mixed_fp16x3': 2.098e-02,
     'simt_chunks_fp32_delta': 7.330e-02,
     'simt_chunks_fp32_direct': 1.579e-01,
+    'simt_remainder_fp32_delta': 7.865e-02,
+    'simt_remainder_fp32_direct': 1.042e-01,
     'simt_small_fp32_delta': 3.475e-02,
     'simt_small_fp32_direct': 8.179e-02,
     'simt_w1_fp32_delta': 4.148e-02,

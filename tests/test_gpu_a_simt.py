@@ -39,9 +39,9 @@ def test_simt_workload1(fg21lib, prec):
     cases.check_logl(f"simt_w1_{prec}", got, want, tol)
 
 
-# t-chunks: T = 300 is three rounds of 128 staged columns; N = 120 stages 64
-# columns per round (two 128-column slabs of 121 rows would not fit shared
-# memory; the threshold is N = 110), so T = 150 is three rounds of 64.
+# t-chunks: T = 300 is three rounds of 128 staged columns (128, 128, 44), and
+# N = 120, T = 150 two rounds (128, 22) of 121-row slabs, near the largest
+# block the region cap (N <= 126) allows.
 SIMT_CHUNK_SHAPES = [(1024, 4, 5, 300, 130), (4096, 120, 5, 150, 129)]
 
 
@@ -57,4 +57,28 @@ def test_simt_t_chunks(fg21lib, shape, prec):
     want, _ = cases.expected(m, obs, data, params)
     tol = cases.logl_tolerance(prec, m, obs, data, params)
     cases.check_logl(f"simt_chunks_{prec}", got, want, tol, f"N{N}_T{T}")
+    model.close()
+
+
+# The column blocks of 8 that do not fill a round of the four column slots go
+# one point per thread: T sets how many are left (ceil(T / 8) mod 4) and whether
+# the last block is partial.  T = 5, 8: one leftover block and no rounds; 17:
+# three leftovers, the last partial; 32: four full rounds' worth, no leftover;
+# 40, 48, 56: one round and 1, 2, 3 leftovers; 100: three rounds and one
+# partial leftover (the benchmark's T).
+SIMT_REMAINDER_T = [5, 8, 17, 32, 40, 48, 56, 100]
+
+
+@pytest.mark.parametrize("T", SIMT_REMAINDER_T)
+@pytest.mark.parametrize("prec", ["fp32_delta", "fp32_direct"])
+def test_simt_column_remainders(fg21lib, prec, T):
+    sky, obs, m, data = cases.small_case(npix=1024, N=6, F=7, T=T, window=8.0, seed=T)
+    model = fg21lib.fg21_build_regions(sky, obs, 6)
+    assert np.array_equal(model.labels, m.labels)
+    fg21lib.fg21_model_set_data(model, data)
+    params = cases.I.prior_draws(133, 6, seed=200 + T)
+    got = fg21lib.fg21_loglike_batch(model, params, prec)
+    want, _ = cases.expected(m, obs, data, params)
+    tol = cases.logl_tolerance(prec, m, obs, data, params)
+    cases.check_logl(f"simt_remainder_{prec}", got, want, tol, f"T{T}")
     model.close()
