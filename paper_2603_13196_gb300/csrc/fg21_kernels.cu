@@ -682,9 +682,9 @@ __global__ void __launch_bounds__(PREP_THREADS) prep_tc_kernel(const ReqDesc *__
 // the slab row, addresses stepped by pointer) loaded while the current
 // region's FMAs issue, two columns per packed FP32x2 FMA; it squares the
 // residuals into its points' sums (packed too: even and odd columns in two
-// chains).  The column blocks that do not fill a round of the four column
-// slots are shared out by point instead (thread i: point i x 8 columns), so
-// every warp carries the same work into the stage's barrier.  The per-point
+// chains).  Past the first round, the column blocks that do not fill a round
+// of the four column slots are shared out by point instead (thread i: point i
+// x 8 columns), so every warp carries the same work into the stage's barrier.  The per-point
 // sums of a channel are combined in a fixed order and folded over the channels
 // into a compensated (hi, lo) FP32 pair.
 constexpr int SIMT_THREADS = 128;
@@ -831,7 +831,10 @@ __global__ void __launch_bounds__(SIMT_THREADS) simt_kernel(const ReqDesc *__res
         const float *d_st = dcol + (size_t)(st & 1) * 2 * SIMT_TC;
         const float tcmb = (float)r.t_cmb;
         const int ncb = (tn + SIMT_CT - 1) / SIMT_CT;
-        const int nfull = ncb - ncb % SIMT_CS;     // blocks taken as 4 x 8 tiles, one per column slot per round
+        // blocks taken as 4 x 8 tiles, one per column slot per round; fewer
+        // blocks than slots go as whole tiles too (one round, some warps idle),
+        // which beats sharing them out point by point there
+        const int nfull = ncb < SIMT_CS ? ncb : ncb - ncb % SIMT_CS;
         for (int cb = cs; cb < nfull; cb += SIMT_CS) {
             // accumulator pairs (columns 2k, 2k+1 of one point): packed FP32x2
             // FMAs, each lane the same round-to-nearest FMA as a scalar one

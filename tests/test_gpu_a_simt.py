@@ -60,12 +60,12 @@ def test_simt_t_chunks(fg21lib, shape, prec):
     model.close()
 
 
-# The column blocks of 8 that do not fill a round of the four column slots go
-# one point per thread: T sets how many are left (ceil(T / 8) mod 4) and whether
-# the last block is partial.  T = 5, 8: one leftover block and no rounds; 17:
-# three leftovers, the last partial; 32: four full rounds' worth, no leftover;
-# 40, 48, 56: one round and 1, 2, 3 leftovers; 100: three rounds and one
-# partial leftover (the benchmark's T).
+# Past the first round, the column blocks of 8 that do not fill a round of the
+# four column slots go one point per thread: T sets how many are left
+# (ceil(T / 8) mod 4) and whether the last block is partial.  T = 5, 8, 17:
+# fewer blocks than slots, whole tiles in one round (17: the third block
+# partial); 32: one full round, no leftover; 40, 48, 56: one round and 1, 2, 3
+# leftovers; 100: three rounds and one partial leftover (the benchmark's T).
 SIMT_REMAINDER_T = [5, 8, 17, 32, 40, 48, 56, 100]
 
 
