@@ -4,6 +4,7 @@
 // in the CUDA kernels of fg21_kernels.cu / fg21_tc.cu; nothing here evaluates
 // a likelihood on the CPU.
 #include <algorithm>
+#include <queue>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -172,54 +173,79 @@ void make_cdf(int64_t n, const double *beta, const std::vector<double> &w, Cdf &
 
 struct Region {
     double a, b, ca, cb;
-    bool flag;   // recursive: closed below; hierarchical: unsplit base region
+    bool closed;   // recursive: the lowest region, closed below
 };
 
-// Algorithm 2 / Algorithm 1 / Sec. 4.1 splits -> ascending edges[N+1].
+// Algorithm 2 (recursive): repeatedly halve, at the beta midpoint, the region
+// of largest importance mass; ties go to the lowest lower edge, then to the
+// region created first.  A max-priority queue holds every region keyed by that
+// rule, with each region's mass summed once when the region is made.
+void split_recursive(const Cdf &c, int N, double bmin, double bmax, std::vector<Region> &R) {
+    struct Key {
+        double m, a;
+        int idx;
+    };
+    // true when x is split after y
+    auto later = [](const Key &x, const Key &y) {
+        if (x.m != y.m) return x.m < y.m;
+        if (x.a != y.a) return x.a > y.a;
+        return x.idx > y.idx;
+    };
+    std::priority_queue<Key, std::vector<Key>, decltype(later)> q(later);
+    R.assign(1, Region{bmin, bmax, 0.0, 0.0, true});
+    q.push(Key{c.mass(bmin, bmax, true), bmin, 0});
+    while ((int)R.size() < N) {
+        const Key k = q.top();
+        q.pop();
+        Region &lo = R[k.idx];
+        const double mid = 0.5 * (lo.a + lo.b);
+        const Region up{mid, lo.b, 0.0, 0.0, false};
+        lo.b = mid;
+        q.push(Key{c.mass(lo.a, lo.b, lo.closed), lo.a, k.idx});
+        R.push_back(up);
+        q.push(Key{c.mass(up.a, up.b, false), up.a, (int)R.size() - 1});
+    }
+}
+
+// Algorithm 1 (hierarchical): 2^floor(log2 N) base regions of equal target
+// mass, then the widest base regions not yet bisected are bisected at their
+// importance midpoints.  Unsplit base regions keep their widths, so the
+// regions bisected are the first N - nb of the base regions in order of width
+// (descending; ties to the lowest lower edge, then to the lower index).
+void split_hierarchical(const Cdf &c, int N, double bmin, double bmax, std::vector<Region> &R) {
+    int nb = 1;
+    while (nb * 2 <= N) nb *= 2;
+    R.clear();
+    for (int j = 1; j <= nb; ++j) {
+        const double cj = (double)j / nb;
+        const double a = R.empty() ? bmin : R.back().b, ca = R.empty() ? 0.0 : R.back().cb;
+        R.push_back(Region{a, j == nb ? bmax : c.inverse(cj), ca, cj, false});
+    }
+    std::vector<int> by_width(nb);
+    for (int j = 0; j < nb; ++j) by_width[j] = j;
+    std::stable_sort(by_width.begin(), by_width.end(), [&R](int x, int y) {
+        const double wx = R[x].b - R[x].a, wy = R[y].b - R[y].a;
+        return wx > wy || (wx == wy && R[x].a < R[y].a);
+    });
+    for (int k = 0; k < N - nb; ++k) {
+        const Region r = R[by_width[k]];
+        const double cm = 0.5 * (r.ca + r.cb), bm = c.inverse(cm);
+        R[by_width[k]].b = bm;
+        R[by_width[k]].cb = cm;
+        R.push_back(Region{bm, r.b, cm, r.cb, false});
+    }
+}
+
+// Algorithm 2 / Algorithm 1 / Sec. 4.1 splits -> ascending edges[N+1]: the
+// regions tile [beta_min, beta_max], so the edges are beta_min and the sorted
+// upper ends of the regions.
 void split(const Cdf &c, int N, int scheme, std::vector<double> &edges) {
     const double bmin = c.sorted_beta.front(), bmax = c.sorted_beta.back();
     std::vector<Region> R;
     if (scheme == FG21_SCHEME_RECURSIVE) {
-        R.push_back({bmin, bmax, 0.0, 1.0, true});
-        std::vector<double> m;
-        while ((int)R.size() < N) {
-            m.resize(R.size());
-            for (size_t r = 0; r < R.size(); ++r) m[r] = c.mass(R[r].a, R[r].b, R[r].flag);
-            size_t best = 0;
-            for (size_t r = 1; r < R.size(); ++r)
-                if (m[r] > m[best] || (m[r] == m[best] && R[r].a < R[best].a)) best = r;
-            double mid = 0.5 * (R[best].a + R[best].b);
-            Region hi{mid, R[best].b, 0.0, 0.0, false};
-            R[best].b = mid;
-            R.push_back(hi);
-        }
+        split_recursive(c, N, bmin, bmax, R);
     } else if (scheme == FG21_SCHEME_HIERARCHICAL) {
-        int nb = 1;
-        while (nb * 2 <= N) nb *= 2;
-        double pb = bmin, pc = 0.0;
-        for (int j = 1; j <= nb; ++j) {
-            double cj = (double)j / nb;
-            double e = j == nb ? bmax : c.inverse(cj);
-            R.push_back({pb, e, pc, cj, true});
-            pb = e;
-            pc = cj;
-        }
-        while ((int)R.size() < N) {
-            int best = -1;
-            for (int r = 0; r < (int)R.size(); ++r) {
-                if (!R[r].flag) continue;
-                if (best < 0) { best = r; continue; }
-                double wr = R[r].b - R[r].a, wb = R[best].b - R[best].a;
-                if (wr > wb || (wr == wb && R[r].a < R[best].a)) best = r;
-            }
-            double cm = 0.5 * (R[best].ca + R[best].cb);
-            double bm = c.inverse(cm);
-            Region hi{bm, R[best].b, cm, R[best].cb, false};
-            R[best].b = bm;
-            R[best].cb = cm;
-            R[best].flag = false;
-            R.push_back(hi);
-        }
+        split_hierarchical(c, N, bmin, bmax, R);
     } else if (scheme == FG21_SCHEME_LINEAR) {
         for (int j = 0; j < N; ++j)
             R.push_back({j == 0 ? bmin : bmin + (bmax - bmin) * j / N,
@@ -234,12 +260,10 @@ void split(const Cdf &c, int N, int scheme, std::vector<double> &edges) {
             prev = e;
         }
     }
-    std::sort(R.begin(), R.end(), [](const Region &x, const Region &y) {
-        return x.a < y.a || (x.a == y.a && x.b < y.b);
-    });
     edges.resize(N + 1);
     edges[0] = bmin;
     for (int j = 0; j < N; ++j) edges[j + 1] = R[j].b;
+    std::sort(edges.begin() + 1, edges.end());
 }
 
 // Chromatic response functions (Sec. 2.2 eq. chromatic_function with
