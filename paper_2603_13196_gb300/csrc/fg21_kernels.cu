@@ -834,7 +834,7 @@ __global__ void __launch_bounds__(SIMT_THREADS) simt_kernel(const ReqDesc *__res
         // blocks taken as 4 x 8 tiles, one per column slot per round; fewer
         // blocks than slots go as whole tiles too (one round, some warps idle),
         // which beats sharing them out point by point there
-        const int nfull = ncb < SIMT_CS ? ncb : ncb - ncb % SIMT_CS;
+        const int nfull = ncb - (ncb >= SIMT_CS ? ncb % SIMT_CS : 0);
         for (int cb = cs; cb < nfull; cb += SIMT_CS) {
             // accumulator pairs (columns 2k, 2k+1 of one point): packed FP32x2
             // FMAs, each lane the same round-to-nearest FMA as a scalar one
