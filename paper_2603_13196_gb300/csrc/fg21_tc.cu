@@ -687,14 +687,20 @@ template <int KS>
 __device__ __forceinline__ void issue_mmas(uint32_t d_tmem, uint32_t w_hi, uint32_t w_mid, uint32_t b_addr,
                                            uint32_t b_lbo, uint32_t b_split, uint32_t idesc) {
 #pragma unroll
+    // one descriptor for the stage's tile; each MMA adds its offset (16-byte
+    // units) to the start-address field, which shared-memory addresses below
+    // 256 KB never carry out of (the issuing thread is busy about half the
+    // kernel's time in this sequence: building every descriptor afresh cost 3%)
+    const uint64_t d0 = smem_desc(b_addr, b_lbo, 128);
+    const uint32_t step = (2 * b_lbo) >> 4, split = b_split >> 4;
+#pragma unroll
     for (int ks = 0; ks < KS; ++ks) {
-        mma_f16_ts(d_tmem, w_hi + ks * 8, smem_desc(b_addr + b_split + ks * 2 * b_lbo, b_lbo, 128), idesc,
-                   ks > 0 ? 1u : 0u);
-        mma_f16_ts(d_tmem, w_mid + ks * 8, smem_desc(b_addr + ks * 2 * b_lbo, b_lbo, 128), idesc, 1u);
+        mma_f16_ts(d_tmem, w_hi + ks * 8, d0 + split + ks * step, idesc, ks > 0 ? 1u : 0u);
+        mma_f16_ts(d_tmem, w_mid + ks * 8, d0 + ks * step, idesc, 1u);
     }
 #pragma unroll
     for (int ks = KS - 1; ks >= 0; --ks)
-        mma_f16_ts(d_tmem, w_hi + ks * 8, smem_desc(b_addr + ks * 2 * b_lbo, b_lbo, 128), idesc, 1u);
+        mma_f16_ts(d_tmem, w_hi + ks * 8, d0 + ks * step, idesc, 1u);
 }
 
 template <int KP, bool BF16>
